@@ -1,0 +1,259 @@
+/*
+ * fsb_oracle.c -- plain single-threaded CPU oracle of the Fish School
+ * Behaviour per-step update.  TEST INFRASTRUCTURE ONLY (see fsb_oracle.h).
+ *
+ * Compiled twice: with FSBO_REAL=float / FSBO_SFX=f32 and with
+ * FSBO_REAL=double / FSBO_SFX=f64.  Build flags must keep IEEE semantics:
+ * -O2 -ffp-contract=off -fno-fast-math (no fused multiply-add contraction,
+ * no reassociation, subnormals kept).
+ *
+ * The method, fish by fish in index order, as the paper describes it and
+ * with the readings taken where the paper is silent:
+ *
+ *   state  (Sec. 2.1.1)  Fish {x, y, weight, prevObjective, currentObjective}
+ *   pond   (Sec. 2.1.2)  200 x 200 plane, read as [-P, P]^2 centred on the
+ *                        origin, P = 100.
+ *   init   (Sec. 2.1.1)  position from the random number generator, uniform
+ *                        over the pond; currentObjective = Euclidean distance
+ *                        to the pond centre; prevObjective = the same value;
+ *                        weight = the Config's initial weight (Sec. 2.1.3),
+ *                        or optionally w0 * (0.5 + u) (reading: the paper
+ *                        says the weight also comes from the generator).
+ *   step t (Sec. 2.1.2, Sec. 2.2.1 "fish movement and feeding"), in order
+ *     swim        random move: x += (2u0 - 1) s, y += (2u1 - 1) s, then each
+ *                 coordinate clamped to [-P, P] (reading: uniform step of
+ *                 half-width s, independent of weight; clamp at the bank)
+ *     objective   prevObjective <- currentObjective;
+ *                 currentObjective <- sqrt(x*x + y*y)
+ *     delta       delta_i = currentObjective - prevObjective
+ *     max         M_t = max_i |delta_i|; the paper's eat() reduction
+ *                 (Sec. 2.3.2) max_i (prevObjective - currentObjective) is
+ *                 reported beside it
+ *     eat         if M_t > 0: weight <- clamp(weight + delta_i / M_t,
+ *                 w_min, w_max) (reading: feeding normalised by the max,
+ *                 capped); if M_t == 0 no fish eats
+ *     barycentre  S_w = sum w, S_x = sum w x, S_y = sum w y over the
+ *                 positions after this step's swim and the weights after
+ *                 this step's eat (reading: weighted centre of the school)
+ *
+ * Draws: u(r) = (r >> 8) * 2^-24 from Philox4x32-10 words (philox.c), so
+ * 2u - 1 is exact in binary32.  Each arithmetic operation rounds once to
+ * nearest-even in FSBO_REAL.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "fsb_oracle.h"
+
+#ifndef FSBO_REAL
+#error "compile with -DFSBO_REAL=float -DFSBO_SFX=f32 (or double / f64)"
+#endif
+
+typedef FSBO_REAL real;
+
+#define FSBO_CAT2(a, b) a##_##b
+#define FSBO_CAT(a, b) FSBO_CAT2(a, b)
+#define FN(name) FSBO_CAT(name, FSBO_SFX)
+#define FISH FSBO_CAT(fsbo_fish, FSBO_SFX)
+
+/* sqrt in the state precision: both are correctly rounded (IEEE 754). */
+static real sqrt_r(real v)
+{
+    if (sizeof(real) == sizeof(float)) return (real)sqrtf((float)v);
+    return (real)sqrt((double)v);
+}
+
+static real clamp_r(real v, real lo, real hi)
+{
+    return v < lo ? lo : (v > hi ? hi : v);
+}
+
+/* 2u - 1 for the draw word r, u = (r >> 8) * 2^-24.  Exact in binary32. */
+static real centred_uniform(uint32_t r)
+{
+    real u = (real)(r >> 8) * (real)0x1p-24;
+    return (real)2 * u - (real)1;
+}
+
+static real objective(real x, real y)
+{
+    return sqrt_r(x * x + y * y);
+}
+
+/* Neumaier-compensated binary64 sum; the products are split exactly with
+ * fma so sum_w, sum_wx, sum_wy are the exact sums up to a relative error of
+ * a few units in 2^-53 plus n * 2^-106 of the sum of magnitudes. */
+typedef struct { double s, c; } csum;
+
+static void csum_add(csum* a, double v)
+{
+    double t = a->s + v;
+    if (fabs(a->s) >= fabs(v)) a->c += (a->s - t) + v;
+    else                      a->c += (v - t) + a->s;
+    a->s = t;
+}
+
+static void csum_add_product(csum* a, double p, double q)
+{
+    double hi = p * q;
+    double lo = fma(p, q, -hi);
+    csum_add(a, hi);
+    csum_add(a, lo);
+}
+
+/* Swim of one fish at step t with draw words r0, r1; updates the objective
+ * fields and returns delta = currentObjective - prevObjective. */
+static real swim_one(FISH* f, uint32_t r0, uint32_t r1, real P, real s)
+{
+    real nx = f->x + centred_uniform(r0) * s;
+    real ny = f->y + centred_uniform(r1) * s;
+    f->x = clamp_r(nx, -P, P);
+    f->y = clamp_r(ny, -P, P);
+    f->prevObjective = f->currentObjective;
+    f->currentObjective = objective(f->x, f->y);
+    return f->currentObjective - f->prevObjective;
+}
+
+static real eat_one(real w, real delta, real M, real wmin, real wmax)
+{
+    return clamp_r(w + delta / M, wmin, wmax);
+}
+
+static int config_ok(const fsbo_config* cfg)
+{
+    if (!cfg || cfg->n_fish == 0) return 0;
+    if (!(cfg->pond_half > 0.0) || !(cfg->step >= 0.0)) return 0;
+    if (!(cfg->w_min <= cfg->w_max)) return 0;
+    if (cfg->init_weight_mode != 0 && cfg->init_weight_mode != 1) return 0;
+    return 1;
+}
+
+int FN(fsbo_init)(const fsbo_config* cfg, FISH* school)
+{
+    if (!config_ok(cfg) || !school) return -1;
+    const real P = (real)cfg->pond_half;
+    const real w0 = (real)cfg->w0;
+    for (uint64_t i = 0; i < cfg->n_fish; ++i) {
+        uint32_t r[3];
+        fsbo_init_words(cfg, i, r);
+        FISH* f = &school[i];
+        f->x = centred_uniform(r[0]) * P;
+        f->y = centred_uniform(r[1]) * P;
+        if (cfg->init_weight_mode == 0) {
+            f->weight = w0;
+        } else {
+            real u2 = (real)(r[2] >> 8) * (real)0x1p-24;
+            f->weight = w0 * ((real)0.5 + u2);
+        }
+        f->currentObjective = objective(f->x, f->y);
+        f->prevObjective = f->currentObjective;
+    }
+    return 0;
+}
+
+int FN(fsbo_run)(const fsbo_config* cfg, uint64_t t0, uint32_t n_steps,
+                 FISH* school, fsbo_stats* stats, const uint32_t* draws)
+{
+    if (!config_ok(cfg) || !school) return -1;
+    if (t0 + (uint64_t)n_steps > 0xFFFFFFFFull) return -1;
+    const uint64_t N = cfg->n_fish;
+    const real P = (real)cfg->pond_half;
+    const real s = (real)cfg->step;
+    const real wmin = (real)cfg->w_min;
+    const real wmax = (real)cfg->w_max;
+
+    real* delta = (real*)malloc(sizeof(real) * N);
+    if (!delta) return -1;
+
+    for (uint32_t k = 0; k < n_steps; ++k) {
+        const uint32_t t = (uint32_t)(t0 + k + 1);
+
+        /* swim, objective, delta */
+        for (uint64_t i = 0; i < N; ++i) {
+            uint32_t r[2];
+            if (draws) {
+                r[0] = draws[((uint64_t)k * N + i) * 2 + 0];
+                r[1] = draws[((uint64_t)k * N + i) * 2 + 1];
+            } else {
+                fsbo_swim_words(cfg, i, t, r);
+            }
+            delta[i] = swim_one(&school[i], r[0], r[1], P, s);
+        }
+
+        /* max |delta| and the paper's eat() statistic, initialised to
+         * -infinity as in Sec. 2.3.2 */
+        double M = 0.0;
+        double eat_max = -INFINITY;
+        for (uint64_t i = 0; i < N; ++i) {
+            double a = fabs((double)delta[i]);
+            if (a > M) M = a;
+            double diff = (double)(school[i].prevObjective -
+                                   school[i].currentObjective);
+            if (diff > eat_max) eat_max = diff;
+        }
+
+        /* eat */
+        if (M > 0.0) {
+            const real Mr = (real)M;   /* exact: M is one of the deltas */
+            for (uint64_t i = 0; i < N; ++i)
+                school[i].weight = eat_one(school[i].weight, delta[i], Mr,
+                                           wmin, wmax);
+        }
+
+        /* barycentre sums */
+        if (stats) {
+            csum sw = {0, 0}, sx = {0, 0}, sy = {0, 0};
+            csum ax = {0, 0}, ay = {0, 0};
+            for (uint64_t i = 0; i < N; ++i) {
+                double w = (double)school[i].weight;
+                double x = (double)school[i].x;
+                double y = (double)school[i].y;
+                csum_add(&sw, w);
+                csum_add_product(&sx, w, x);
+                csum_add_product(&sy, w, y);
+                csum_add_product(&ax, w, fabs(x));
+                csum_add_product(&ay, w, fabs(y));
+            }
+            stats[k].max_abs_delta = M;
+            stats[k].eat_max_diff = eat_max;
+            stats[k].sum_w = sw.s + sw.c;
+            stats[k].sum_wx = sx.s + sx.c;
+            stats[k].sum_wy = sy.s + sy.c;
+            stats[k].sum_abs_wx = ax.s + ax.c;
+            stats[k].sum_abs_wy = ay.s + ay.c;
+        }
+    }
+    free(delta);
+    return 0;
+}
+
+void FN(fsbo_track_fish)(const fsbo_config* cfg, uint64_t i, uint64_t t0,
+                         uint32_t n_steps, FISH* fish, real* out_x,
+                         real* out_y, real* out_delta)
+{
+    const real P = (real)cfg->pond_half;
+    const real s = (real)cfg->step;
+    for (uint32_t k = 0; k < n_steps; ++k) {
+        uint32_t r[2];
+        fsbo_swim_words(cfg, i, (uint32_t)(t0 + k + 1), r);
+        real d = swim_one(fish, r[0], r[1], P, s);
+        if (out_x) out_x[k] = fish->x;
+        if (out_y) out_y[k] = fish->y;
+        if (out_delta) out_delta[k] = d;
+    }
+}
+
+real FN(fsbo_eat_fish)(const fsbo_config* cfg, real w, uint32_t n_steps,
+                       const real* delta, const double* max_abs_delta,
+                       real* out_w)
+{
+    const real wmin = (real)cfg->w_min;
+    const real wmax = (real)cfg->w_max;
+    for (uint32_t k = 0; k < n_steps; ++k) {
+        if (max_abs_delta[k] > 0.0)
+            w = eat_one(w, delta[k], (real)max_abs_delta[k], wmin, wmax);
+        if (out_w) out_w[k] = w;
+    }
+    return w;
+}
