@@ -1,0 +1,346 @@
+#!/usr/bin/env python3
+"""Benchmark of the Fish School Behaviour per-step update on GB300.
+
+Default workload: one school of N = 2^28 fish (seed 2), streamed from HBM,
+one bench step = one step of the method over the whole school.  Prints one
+JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload stream|small|resident] [--precision ...]
+
+value      fish-steps/s over all ranks, inputs resident in HBM
+e2e        the same metric through the C ABI with host buffers: host->device
+           copy of the initial state, K steps with per-step statistics read
+           back, device->host copy of the final state
+roofline   the fused per-step pass: algorithmic bytes (32 B per fish-step in
+           binary32, 64 B in binary64 state) / its average launch time, taken
+           with CUDA events on the launching stream during the timed region
+cpu_baseline  the CPU oracle (single thread) on a bounded sample of the
+           same workload
+--impl reference  times the CPU oracle, as it stands, on a bounded sample
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2507_20173_gb300 import workloads  # noqa: E402
+
+METRIC = "fish-steps/sec and % HBM roofline on 1 GB300; batched vs per-school launches"
+UNIT = "fish-steps/s"
+L2_BYTES = 129 * (1 << 20)
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["stream", "small", "resident"], default="stream")
+    ap.add_argument("--precision", choices=["FP32", "FP32_KAHAN", "FP64_ACC", "FP64_STATE"],
+                    default="FP32_KAHAN")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def workload_of(name):
+    return {"stream": workloads.STREAM, "small": workloads.SMALL,
+            "resident": workloads.RESIDENT}[name]
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2507_20173_gb300", "csrc")
+    for name in ("fsb_stream.cu", "fsb_device.cuh"):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(n_fish, precision):
+    """DRAM bytes per fused-pass launch from the committed ncu summary,
+    scaled to this launch's fish count; None if the kernel changed since."""
+    p = os.path.join(ROOT, "profiles", "stream_fused_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("kernel_source_hash") != kernel_source_hash() or d.get("precision") != precision:
+        return None
+    return float(d["dram_bytes_per_fish"]) * n_fish
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
+
+
+def cpu_oracle_rate(n_fish, seed, steps):
+    """Time the CPU oracle (single thread) on n_fish x steps fish-steps."""
+    import oracle
+    cfg = oracle.Config(n_fish=n_fish, seed=seed)
+    school = oracle.init(cfg)
+    t0 = time.perf_counter()
+    oracle.run(cfg, school, 0, steps)
+    dt = time.perf_counter() - t0
+    return n_fish * steps / dt, dt
+
+
+def run_reference(args, world, rank):
+    """The oracle as it stands, each bench step a bounded sample of the
+    workload (2^22 fish of the same school rule, one step)."""
+    wl = workload_of(args.workload)
+    if rank != 0:
+        return
+    import oracle
+    n = min(wl.n_fish, 1 << 22)
+    steps = args.steps if args.steps is not None else wl.steps
+    cfg = oracle.Config(n_fish=n, seed=wl.seed)
+    school = oracle.init(cfg)
+    oracle.run(cfg, school, 0, args.warmup)
+    t0 = time.perf_counter()
+    oracle.run(cfg, school, args.warmup, steps)
+    dt = time.perf_counter() - t0
+    value = n * steps / dt
+    sample = "first %d fish of the %s school (same init rule), %d steps" % (n, wl.name, steps)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl.name, "n_fish_sample": n, "impl_kind": "cpu oracle"},
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local, pg):
+    import torch
+
+    import paper_2507_20173_gb300 as fsb
+    from paper_2507_20173_gb300 import build as fsb_build
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py: no CUDA device")
+    torch.cuda.set_device(local)
+    fsb_build.build()
+    fsb.lib()
+    wl = workload_of(args.workload)
+    steps = args.steps if args.steps is not None else wl.steps
+    warmup = max(3, args.warmup)
+    prec = getattr(fsb, "FSB_" + args.precision)
+    dbl = prec == fsb.FSB_FP64_STATE
+    elem = 8 if dbl else 4
+    n = wl.n_fish
+    cfg = fsb.fsb_config_init(n, wl.seed + rank, precision=prec, school_id=wl.school_id)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident timing
+    school = fsb.School.create(cfg, stream=stream)
+    school.step(warmup)
+    fsb.fsb_set_kernel_timing(school.handle, True)
+    fsb.fsb_kernel_time(school.handle)
+    barrier()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        fsb.fsb_step(school.handle, steps)
+        stop.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = start.elapsed_time(stop)
+    fused_ms, fused_n = fsb.fsb_kernel_time(school.handle)
+    path = fsb.fsb_handle_path(school.handle)
+    school.destroy()
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if pg is not None:
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * n * steps / (ms_max / 1e3)
+
+    # ---- roofline of the fused pass
+    peak, peak_kind = measured_peaks()
+    bytes_per_fish_step = 8 * elem
+    avg_fused_s = (fused_ms / fused_n) / 1e3 if fused_n else None
+    achieved = bytes_per_fish_step * n / avg_fused_s / 1e9 if avg_fused_s else None
+    traffic = ncu_traffic(n, args.precision)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak if achieved else None, "traffic": traffic,
+            "peak_source": peak_kind + " hbm_gbs (STREAM copy)",
+            "kernel": "stream_pass_kernel<fused>", "launches": fused_n,
+            "avg_launch_ms": avg_fused_s * 1e3 if avg_fused_s else None,
+            "algorithmic_bytes_per_launch": bytes_per_fish_step * n}
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        npdt = np.float64 if dbl else np.float32
+        init_school = fsb.School.create(cfg, stream=stream)
+        host0 = init_school.read()
+        init_school.destroy()
+        pin = {k: torch.from_numpy(host0[k]).pin_memory() for k in ("x", "y", "w", "prev")}
+        outs = {k: torch.empty(n, dtype=torch.float64 if dbl else torch.float32).pin_memory()
+                for k in ("x", "y", "w", "prev", "cur")}
+        dev = [torch.empty(n, dtype=torch.float64 if dbl else torch.float32, device="cuda")
+               for _ in range(4)]
+        bufs = fsb.FsbStateDev(*(d.data_ptr() for d in dev))
+        host = fsb.FsbStateHost(*(pin[k].data_ptr() for k in ("x", "y", "w", "prev")))
+        stats = np.zeros(steps, fsb.STATS_DTYPE)
+        barrier()
+        t0 = time.perf_counter()
+        h = fsb.fsb_create(cfg, bufs, host, 0, stream.cuda_stream)
+        fsb.fsb_step(h, steps, stats)
+        fsb.fsb_read_state(h, *(outs[k].numpy() for k in ("x", "y", "w", "prev", "cur")))
+        e2e_s = time.perf_counter() - t0
+        fsb.fsb_destroy(h)
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        if pg is not None:
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_s = float(t.item())
+        e2e = {"value": world * n * steps / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(4 * elem * n / steps),
+               "d2h_bytes_per_step": int((5 * elem * n + 40 * steps) / steps),
+               "what": "fsb_create from pinned host state + fsb_step(K) with host stats + "
+                       "fsb_read_state to pinned host, wall clock"}
+        del pin, outs, dev
+
+    # ---- CPU oracle baseline (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cn, cs = min(n, 1 << 20), 20 if n >= (1 << 20) else wl.steps
+        rate, dt = cpu_oracle_rate(cn, wl.seed, cs)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "%d fish x %d steps of the %s school (same init rule), %.1f s"
+                         % (cn, cs, wl.name, dt)}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": steps, "warmup": warmup, "ms_per_step": ms_max / steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if dbl else "f32", "data": "synthetic",
+                "config": {"workload": wl.name, "n_fish": n, "seed": wl.seed,
+                           "precision": args.precision,
+                           "path": {1: "stream", 2: "resident"}.get(path, str(path)),
+                           "l2": "inputs larger than L2 (%.1f GB state vs 129 MB L2)"
+                                 % (4 * elem * n / 1e9) if 4 * elem * n > L2_BYTES
+                                 else "state fits in L2 (reused across steps)",
+                           "parallelism": "replicas x%d" % world},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": steps + 1, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    world, rank, local, pg = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local, pg)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

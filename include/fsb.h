@@ -1,0 +1,247 @@
+/*
+ * fsb.h -- C ABI of the GB300 Fish School Behaviour library (libfsb.so).
+ *
+ * The library advances fish schools by the per-step update of the Fish School
+ * Behaviour simulation (arxiv 2507.20173): random swim inside the pond
+ * (Sec. 2.1.2), objective = Euclidean distance to the pond centre
+ * (Sec. 2.1.1), delta of the objective, a max reduction over the school
+ * (the eat() reduction of Sec. 2.3.2), feeding normalised by that max and
+ * capped, and the school's barycentre sums.  Where the paper leaves a rule
+ * unwritten, the reading used is stated at the declaration that relies on it.
+ *
+ * Conventions for every entry point:
+ *   - Return value: FSB_OK (0) or a negative fsb_status.  fsb_strerror()
+ *     names a status; fsb_last_error() gives a human-readable detail of the
+ *     last failure on the calling thread.
+ *   - Device pointers are plain CUDA device addresses (e.g. a torch tensor's
+ *     data_ptr()).  Host pointers are plain host addresses; pinned memory is
+ *     faster but not required.
+ *   - Streams are cudaStream_t passed as void*; NULL means the legacy default
+ *     stream.  Calls are asynchronous on the handle's stream unless stated
+ *     otherwise.
+ *   - No entry point may be called while its stream is being captured into a
+ *     CUDA graph by the caller (the library captures its own graphs).
+ *   - One GPU: the device current at fsb_create is the device of the handle.
+ *   - Nothing here falls back to the CPU: without a usable CUDA device every
+ *     call that computes returns FSB_ERR_CUDA.
+ */
+#ifndef FSB_H
+#define FSB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FSB_OK = 0,
+    FSB_ERR_INVALID_ARG = -1,  /* bad pointer, size, enum or config value   */
+    FSB_ERR_CUDA = -2,         /* a CUDA runtime call failed                 */
+    FSB_ERR_OOM = -3,          /* device or pinned allocation failed         */
+    FSB_ERR_UNSUPPORTED = -4,  /* valid request this build cannot serve      */
+    FSB_ERR_TIMEOUT = -5,      /* a bounded device-side wait gave up         */
+    FSB_ERR_STATE = -6         /* device status word latched an error        */
+} fsb_status;
+
+/* Arithmetic of the state and of the barycentre sums.
+ *   FSB_FP32        binary32 state; plain binary32 sums (precision baseline)
+ *   FSB_FP32_KAHAN  binary32 state; compensated binary32 per-thread sums,
+ *                   combined in binary64 (default)
+ *   FSB_FP64_ACC    binary32 state; binary64 sums of exact products
+ *   FSB_FP64_STATE  binary64 state and arithmetic; binary64 sums
+ * In every binary32 mode the per-fish state is bit-identical; only the sums
+ * differ. */
+typedef enum {
+    FSB_FP32 = 0,
+    FSB_FP32_KAHAN = 1,
+    FSB_FP64_ACC = 2,
+    FSB_FP64_STATE = 3
+} fsb_precision;
+
+/* Which kernel family advances a single school.
+ *   FSB_PATH_STREAM    one fused HBM-streaming pass per step
+ *   FSB_PATH_RESIDENT  state held on chip for all steps of a call
+ *   FSB_PATH_AUTO      the library picks (autotune table, else size cutoff) */
+typedef enum {
+    FSB_PATH_AUTO = 0,
+    FSB_PATH_STREAM = 1,
+    FSB_PATH_RESIDENT = 2
+} fsb_path;
+
+/* School configuration: the physics fields of the paper's Config struct
+ * (Sec. 2.1.3: fish population, initial weight, pond dimensions) plus the
+ * generator key and the arithmetic mode.  Use fsb_config_init() for the
+ * defaults below.
+ *   n_fish            >= 1
+ *   seed              Philox4x32-10 key = (seed lo32, seed hi32)
+ *   school_id         XORed into counter word 1 (distinguishes schools)
+ *   init_weight_mode  0: w = w0 (default); 1: w = w0 * (0.5 + u), u uniform
+ *                     in [0,1) from the init draw (the paper says the weight
+ *                     comes from the generator, Sec. 2.1.1, yet Config holds
+ *                     one initial weight, Sec. 2.1.3)
+ *   pond_half         P: the pond is [-P, P]^2 (200x200 -> 100, Sec. 2.1.2)
+ *   step              s: each coordinate moves by (2u - 1) * s per step
+ *                     (default 0.1; the paper gives no step size)
+ *   w0, w_min, w_max  initial weight 1, floor 0, cap 2 (cap = 2 w0)
+ *   precision         fsb_precision
+ *   path              fsb_path (ignored by fsb_run_batch)                  */
+typedef struct {
+    uint64_t n_fish;
+    uint64_t seed;
+    uint32_t school_id;
+    int32_t  init_weight_mode;
+    double   pond_half;
+    double   step;
+    double   w0;
+    double   w_min;
+    double   w_max;
+    int32_t  precision;
+    int32_t  path;
+} fsb_config;
+
+/* Per-fish state arrays on the device, structure of arrays, n_fish elements
+ * each, element type float (binary32 modes) or double (FSB_FP64_STATE):
+ *   x, y            position (Sec. 2.1.1)
+ *   w               weight
+ *   prev_objective  prevObjective of the paper's Fish record: the objective
+ *                   before the latest swim.  currentObjective is not stored:
+ *                   it is sqrt(x*x + y*y) of the stored position, and
+ *                   fsb_read_state recomputes it on the device.
+ * Base addresses must be aligned to the element size; 16-byte alignment
+ * enables the vectorised path. */
+typedef struct {
+    void* x;
+    void* y;
+    void* w;
+    void* prev_objective;
+} fsb_state_dev;
+
+/* The same four arrays in host memory (resume / checkpoint input). */
+typedef struct {
+    const void* x;
+    const void* y;
+    const void* w;
+    const void* prev_objective;
+} fsb_state_host;
+
+/* Statistics of one step t.
+ *   max_abs_delta  M_t = max_i |currentObjective_i - prevObjective_i|, the
+ *                  normaliser of feeding; exact (it is one fish's |delta|)
+ *   eat_max_diff   max_i (prevObjective_i - currentObjective_i): the value
+ *                  the paper's eat() reduces (Sec. 2.3.2); exact
+ *   sum_w, sum_wx, sum_wy
+ *                  barycentre sums over post-swim positions and post-eat
+ *                  weights of step t, accumulated as `precision` says;
+ *                  barycentre = (sum_wx / sum_w, sum_wy / sum_w)            */
+typedef struct {
+    double max_abs_delta;
+    double eat_max_diff;
+    double sum_w;
+    double sum_wx;
+    double sum_wy;
+} fsb_step_stats;
+
+typedef struct fsb_school* fsb_handle;
+
+/* Fill *cfg with the defaults: pond_half 100, step 0.1, w0 1, w_min 0,
+ * w_max 2, init_weight_mode 0, precision FSB_FP32_KAHAN, path FSB_PATH_AUTO,
+ * school_id 0.  Returns FSB_ERR_INVALID_ARG if cfg is NULL. */
+int fsb_config_init(fsb_config* cfg, uint64_t n_fish, uint64_t seed);
+
+/* Create a school on the current device and bind it to `cuda_stream`.
+ *   cfg         validated: n_fish >= 1, P > 0, s >= 0, w_min <= w_max,
+ *               known enums; else FSB_ERR_INVALID_ARG
+ *   buffers     caller-owned device arrays (see fsb_state_dev) that must
+ *               outlive the handle; NULL: the library allocates and owns them
+ *   init        NULL: initialise by the method's own rule (Sec. 2.1.1: Philox
+ *               position uniform over the pond, weight w0, prevObjective =
+ *               currentObjective = distance to the centre).  Otherwise a
+ *               host checkpoint copied to the device (resume)
+ *   start_step  the step counter t of the state (0 for a fresh school; the
+ *               value fsb_read_state reported when resuming)
+ * On success *out holds the handle.  Library scratch (reduction partials,
+ * the per-step statistics ring, the control word) is owned by the handle.
+ * Asynchronous on cuda_stream. */
+int fsb_create(const fsb_config* cfg, const fsb_state_dev* buffers,
+               const fsb_state_host* init, uint64_t start_step,
+               void* cuda_stream, fsb_handle* out);
+
+/* Advance the school by n_steps steps (t -> t + n_steps), each step doing
+ * swim, objective, delta, max, eat and barycentre in that order (Sec. 2.1.2,
+ * Sec. 2.2.1, Sec. 2.3.2).  t + n_steps must stay below 2^32 (the step is a
+ * 32-bit Philox counter word).
+ *   host_stats  NULL, or room for n_steps records; when given the call
+ *               synchronises the stream and fills them in step order
+ * Returns FSB_ERR_INVALID_ARG for n_steps == 0 or counter overflow, and
+ * FSB_ERR_TIMEOUT / FSB_ERR_STATE if a device-side wait gave up or the
+ * device status word is set (checked when the call synchronises).
+ * Asynchronous unless host_stats is given. */
+int fsb_step(fsb_handle h, uint32_t n_steps, fsb_step_stats* host_stats);
+
+/* Copy the school's state to host memory in the paper's field order
+ * (Sec. 2.1.1): x, y, weight, prevObjective, currentObjective, each n_fish
+ * elements of the state type; any pointer may be NULL to skip that field.
+ * currentObjective is recomputed on the device from the stored position.
+ * *step_out (may be NULL) receives the step counter t.  Synchronises the
+ * stream; returns the latched device status, if any. */
+int fsb_read_state(fsb_handle h, void* x, void* y, void* w,
+                   void* prev_objective, void* current_objective,
+                   uint64_t* step_out);
+
+/* Copy the statistics of the last fsb_step call (n_steps records) into
+ * host memory without running anything.  Synchronises the stream. */
+int fsb_last_stats(fsb_handle h, fsb_step_stats* host_stats, uint32_t n_steps);
+
+/* Release the handle and everything it owns (not caller buffers).
+ * Synchronises the stream first.  NULL is accepted. */
+int fsb_destroy(fsb_handle h);
+
+/* Advance many independent schools of uneven size by n_steps, in one
+ * persistent launch over a ragged offset table (the batched form of the same
+ * per-step update; each school is a separate fish school of the paper).
+ *   tmpl        physics fields and precision shared by all schools
+ *               (n_fish, seed, school_id and path are ignored); binary32
+ *               precisions only (FSB_FP64_STATE -> FSB_ERR_UNSUPPORTED)
+ *   n_schools   >= 1
+ *   offsets     host array of n_schools + 1 increasing fish offsets,
+ *               offsets[0] = 0; school k is fish [offsets[k], offsets[k+1])
+ *               and must hold >= 1 fish
+ *   seeds       host array of n_schools keys; school k uses key seeds[k] and
+ *               school id k, so it reproduces a single-school run created
+ *               with that seed and school_id = k
+ *   state       device arrays of offsets[n_schools] fish (binary32), the
+ *               school states at step start_step; advanced in place
+ *   init        nonzero: first initialise every school by the method's rule
+ *               (start_step must then be 0)
+ *   stats       NULL, or host room for n_schools * n_steps records,
+ *               school-major; when given the call synchronises
+ * Asynchronous on cuda_stream unless stats is given. */
+int fsb_run_batch(const fsb_config* tmpl, uint32_t n_schools,
+                  const uint64_t* offsets, const uint64_t* seeds,
+                  const fsb_state_dev* state, int init, uint64_t start_step,
+                  uint32_t n_steps, fsb_step_stats* stats, void* cuda_stream);
+
+/* Kernel timing for one handle, the GPU analogue of the paper's
+ * omp_get_wtime() bracketing of eat() (Sec. 2.3.2).  While enabled, every
+ * launch of the fused per-step pass is bracketed by CUDA events on the
+ * handle's stream; fsb_kernel_time reports the summed device time (ms) and
+ * the launch count since it was enabled, synchronising the stream. */
+int fsb_set_kernel_timing(fsb_handle h, int enable);
+int fsb_kernel_time(fsb_handle h, double* fused_ms, uint64_t* fused_launches);
+
+/* Which single-school path a handle runs (fsb_path value), after AUTO is
+ * resolved. */
+int fsb_handle_path(fsb_handle h, int* path_out);
+
+/* Name of a status code (static string). */
+const char* fsb_strerror(int status);
+
+/* Detail of the last failure on the calling thread (static per thread). */
+const char* fsb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FSB_H */

@@ -1,0 +1,517 @@
+// fsb_api.cpp -- the C ABI of libfsb.so (declared in include/fsb.h).
+//
+// Handle lifecycle, argument validation, path selection, the statistics
+// ring, CUDA-graph capture of the per-call pass sequence, kernel timing and
+// the device status word.  All arithmetic of the method runs in the CUDA
+// kernels (fsb_stream.cu, fsb_resident.cu, fsb_batch.cu); this file only
+// orchestrates.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "fsb_internal.h"
+
+using fsb::BlockPartial;
+using fsb::Ctl;
+using fsb::StreamLaunch;
+
+namespace {
+
+thread_local char g_last_error[512] = "";
+
+int fail(int status, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+  va_end(ap);
+  return status;
+}
+
+#define FSB_CUDA(call)                                                                  \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      return fail(e_ == cudaErrorMemoryAllocation ? FSB_ERR_OOM : FSB_ERR_CUDA,         \
+                  "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                  __LINE__);                                                            \
+    }                                                                                   \
+  } while (0)
+
+constexpr uint32_t kGraphMaxSteps = 2048;  // whole-call graphs up to this size
+constexpr uint32_t kChunk = 512;           // fused passes per chunk graph beyond it
+constexpr int kMaxGraphs = 8;
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+int validate_config(const fsb_config* c) {
+  if (!c) return fail(FSB_ERR_INVALID_ARG, "config is NULL");
+  if (c->n_fish == 0) return fail(FSB_ERR_INVALID_ARG, "n_fish must be >= 1");
+  if (!(c->pond_half > 0.0)) return fail(FSB_ERR_INVALID_ARG, "pond_half must be > 0");
+  if (!(c->step >= 0.0)) return fail(FSB_ERR_INVALID_ARG, "step must be >= 0");
+  if (!(c->w_min <= c->w_max)) return fail(FSB_ERR_INVALID_ARG, "w_min must be <= w_max");
+  if (c->init_weight_mode != 0 && c->init_weight_mode != 1)
+    return fail(FSB_ERR_INVALID_ARG, "init_weight_mode must be 0 or 1");
+  if (c->precision < FSB_FP32 || c->precision > FSB_FP64_STATE)
+    return fail(FSB_ERR_INVALID_ARG, "unknown precision %d", c->precision);
+  if (c->path < FSB_PATH_AUTO || c->path > FSB_PATH_RESIDENT)
+    return fail(FSB_ERR_INVALID_ARG, "unknown path %d", c->path);
+  return FSB_OK;
+}
+
+int acc_mode(int precision) {
+  switch (precision) {
+    case FSB_FP32: return fsb::kAccPlain32;
+    case FSB_FP32_KAHAN: return fsb::kAccKahan32;
+    default: return fsb::kAccF64;
+  }
+}
+
+}  // namespace
+
+struct GraphEntry {
+  uint32_t key;  // n_steps, or (1u << 31) | chunk for a fused-only chunk graph
+  cudaGraphExec_t exec;
+};
+
+struct fsb_school {
+  fsb_config cfg{};
+  int device = 0;
+  cudaStream_t stream = nullptr;       // caller's stream (not owned)
+  cudaStream_t cap_stream = nullptr;   // owned, used only to capture graphs
+  bool owns_state = false;
+  size_t elem = 4;
+  void* x = nullptr;
+  void* y = nullptr;
+  void* w = nullptr;
+  void* pv = nullptr;
+  uint64_t step = 0;
+  uint32_t last_n = 0;
+  int path = FSB_PATH_STREAM;
+  Ctl* ctl = nullptr;
+  BlockPartial* partials = nullptr;
+  fsb_step_stats* ring = nullptr;
+  uint32_t ring_cap = 0;
+  StreamLaunch launch{};
+  std::vector<GraphEntry> graphs;
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_free;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
+  double fused_ms = 0.0;
+  uint64_t fused_launches = 0;
+};
+
+namespace {
+
+int check_status_word(fsb_school* h) {
+  int status = 0;
+  FSB_CUDA(cudaMemcpyAsync(&status, &h->ctl->status, sizeof(int), cudaMemcpyDeviceToHost,
+                           h->stream));
+  FSB_CUDA(cudaStreamSynchronize(h->stream));
+  if (status != 0)
+    return fail(status, "device status word latched %d (%s)", status, fsb_strerror(status));
+  return FSB_OK;
+}
+
+int ensure_ring(fsb_school* h, uint32_t n) {
+  if (h->ring_cap >= n) return FSB_OK;
+  uint32_t cap = h->ring_cap ? h->ring_cap : 1024;
+  while (cap < n) cap = cap > 0x7FFFFFFFu ? n : cap * 2;
+  FSB_CUDA(cudaStreamSynchronize(h->stream));
+  fsb_step_stats* ring = nullptr;
+  FSB_CUDA(cudaMalloc(&ring, sizeof(fsb_step_stats) * cap));
+  FSB_CUDA(cudaMemset(ring, 0, sizeof(fsb_step_stats) * cap));
+  if (h->ring) cudaFree(h->ring);
+  h->ring = ring;
+  h->ring_cap = cap;
+  h->launch.ring = ring;
+  h->launch.ring_cap = cap;
+  // graphs captured the old ring address
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+  h->graphs.clear();
+  return FSB_OK;
+}
+
+int launch_pass(fsb_school* h, int kind, cudaStream_t s) {
+  FSB_CUDA(fsb::launch_stream_pass(h->launch, kind, s));
+  return FSB_OK;
+}
+
+// Enqueue the pass sequence of one call on stream s (capturable).
+int enqueue_call(fsb_school* h, uint32_t n, cudaStream_t s) {
+  int rc = launch_pass(h, fsb::kSwimOnly, s);
+  for (uint32_t k = 1; rc == FSB_OK && k < n; ++k) rc = launch_pass(h, fsb::kFused, s);
+  if (rc == FSB_OK) rc = launch_pass(h, fsb::kSettle, s);
+  return rc;
+}
+
+int get_graph(fsb_school* h, uint32_t key, cudaGraphExec_t* out) {
+  for (auto& g : h->graphs)
+    if (g.key == key) {
+      *out = g.exec;
+      return FSB_OK;
+    }
+  cudaGraph_t graph = nullptr;
+  FSB_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  int rc;
+  if (key & (1u << 31)) {
+    rc = FSB_OK;
+    for (uint32_t k = 0; rc == FSB_OK && k < (key & 0x7FFFFFFFu); ++k)
+      rc = launch_pass(h, fsb::kFused, h->cap_stream);
+  } else {
+    rc = enqueue_call(h, key, h->cap_stream);
+  }
+  cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
+  if (rc != FSB_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  FSB_CUDA(e);
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  FSB_CUDA(e);
+  if (static_cast<int>(h->graphs.size()) >= kMaxGraphs) {
+    cudaGraphExecDestroy(h->graphs.front().exec);
+    h->graphs.erase(h->graphs.begin());
+  }
+  h->graphs.push_back({key, exec});
+  *out = exec;
+  return FSB_OK;
+}
+
+cudaEvent_t take_event(fsb_school* h) {
+  if (!h->ev_free.empty()) {
+    cudaEvent_t e = h->ev_free.back();
+    h->ev_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+int collect_timing(fsb_school* h) {
+  if (h->ev_pending.empty()) return FSB_OK;
+  FSB_CUDA(cudaStreamSynchronize(h->stream));
+  for (auto& pr : h->ev_pending) {
+    float ms = 0.f;
+    FSB_CUDA(cudaEventElapsedTime(&ms, pr.first, pr.second));
+    h->fused_ms += ms;
+    h->fused_launches += 1;
+    h->ev_free.push_back(pr.first);
+    h->ev_free.push_back(pr.second);
+  }
+  h->ev_pending.clear();
+  return FSB_OK;
+}
+
+int run_timed(fsb_school* h, uint32_t n) {
+  int rc = launch_pass(h, fsb::kSwimOnly, h->stream);
+  for (uint32_t k = 1; rc == FSB_OK && k < n; ++k) {
+    cudaEvent_t a = take_event(h), b = take_event(h);
+    if (!a || !b) return fail(FSB_ERR_CUDA, "cudaEventCreate failed");
+    FSB_CUDA(cudaEventRecord(a, h->stream));
+    rc = launch_pass(h, fsb::kFused, h->stream);
+    FSB_CUDA(cudaEventRecord(b, h->stream));
+    h->ev_pending.emplace_back(a, b);
+  }
+  if (rc == FSB_OK) rc = launch_pass(h, fsb::kSettle, h->stream);
+  return rc;
+}
+
+int run_stream(fsb_school* h, uint32_t n) {
+  if (h->timing) return run_timed(h, n);
+  cudaGraphExec_t exec = nullptr;
+  if (n <= kGraphMaxSteps) {
+    int rc = get_graph(h, n, &exec);
+    if (rc != FSB_OK) return rc;
+    FSB_CUDA(cudaGraphLaunch(exec, h->stream));
+    return FSB_OK;
+  }
+  int rc = launch_pass(h, fsb::kSwimOnly, h->stream);
+  uint32_t rem = n - 1;
+  if (rc == FSB_OK && rem >= kChunk) rc = get_graph(h, (1u << 31) | kChunk, &exec);
+  while (rc == FSB_OK && rem >= kChunk) {
+    FSB_CUDA(cudaGraphLaunch(exec, h->stream));
+    rem -= kChunk;
+  }
+  while (rc == FSB_OK && rem > 0) {
+    rc = launch_pass(h, fsb::kFused, h->stream);
+    --rem;
+  }
+  if (rc == FSB_OK) rc = launch_pass(h, fsb::kSettle, h->stream);
+  return rc;
+}
+
+void release(fsb_school* h) {
+  if (!h) return;
+  if (h->stream || h->cap_stream) cudaStreamSynchronize(h->stream);
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+  for (auto& pr : h->ev_pending) {
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
+  for (auto e : h->ev_free) cudaEventDestroy(e);
+  if (h->owns_state) {
+    cudaFree(h->x);
+    cudaFree(h->y);
+    cudaFree(h->w);
+    cudaFree(h->pv);
+  }
+  cudaFree(h->ctl);
+  cudaFree(h->partials);
+  cudaFree(h->ring);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  delete h;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fsb_config_init(fsb_config* cfg, uint64_t n_fish, uint64_t seed) {
+  if (!cfg) return fail(FSB_ERR_INVALID_ARG, "config is NULL");
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->n_fish = n_fish;
+  cfg->seed = seed;
+  cfg->school_id = 0;
+  cfg->init_weight_mode = 0;
+  cfg->pond_half = 100.0;
+  cfg->step = 0.1;
+  cfg->w0 = 1.0;
+  cfg->w_min = 0.0;
+  cfg->w_max = 2.0;
+  cfg->precision = FSB_FP32_KAHAN;
+  cfg->path = FSB_PATH_AUTO;
+  return FSB_OK;
+}
+
+int fsb_create(const fsb_config* cfg, const fsb_state_dev* buffers, const fsb_state_host* init,
+               uint64_t start_step, void* cuda_stream, fsb_handle* out) {
+  if (!out) return fail(FSB_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  int rc = validate_config(cfg);
+  if (rc != FSB_OK) return rc;
+  if (start_step >= 0xFFFFFFFFull)
+    return fail(FSB_ERR_INVALID_ARG, "start_step must be below 2^32 - 1");
+  if (init && (!init->x || !init->y || !init->w || !init->prev_objective))
+    return fail(FSB_ERR_INVALID_ARG, "init has a NULL array");
+  const bool dbl = cfg->precision == FSB_FP64_STATE;
+  const size_t elem = dbl ? 8 : 4;
+  if (buffers) {
+    const void* p[4] = {buffers->x, buffers->y, buffers->w, buffers->prev_objective};
+    for (const void* q : p)
+      if (!q || !aligned(q, elem))
+        return fail(FSB_ERR_INVALID_ARG, "state buffer NULL or not %zu-byte aligned", elem);
+  }
+  if (cfg->path == FSB_PATH_RESIDENT)
+    return fail(FSB_ERR_UNSUPPORTED, "resident path not available in this build");
+
+  fsb_school* h = new (std::nothrow) fsb_school();
+  if (!h) return fail(FSB_ERR_OOM, "host allocation failed");
+  h->cfg = *cfg;
+  h->elem = elem;
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  h->step = start_step;
+  h->path = FSB_PATH_STREAM;
+
+#define FSB_TRY(call)        \
+  do {                       \
+    int r_ = (call);         \
+    if (r_ != FSB_OK) {      \
+      release(h);            \
+      return r_;             \
+    }                        \
+  } while (0)
+
+  FSB_TRY([&]() -> int {
+    FSB_CUDA(cudaGetDevice(&h->device));
+    FSB_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    const size_t bytes = elem * cfg->n_fish;
+    if (buffers) {
+      h->x = buffers->x;
+      h->y = buffers->y;
+      h->w = buffers->w;
+      h->pv = buffers->prev_objective;
+    } else {
+      h->owns_state = true;
+      FSB_CUDA(cudaMalloc(&h->x, bytes));
+      FSB_CUDA(cudaMalloc(&h->y, bytes));
+      FSB_CUDA(cudaMalloc(&h->w, bytes));
+      FSB_CUDA(cudaMalloc(&h->pv, bytes));
+    }
+    FSB_CUDA(cudaMalloc(&h->ctl, sizeof(Ctl)));
+    Ctl c{};
+    c.base_step = start_step;
+    FSB_CUDA(cudaMemcpyAsync(h->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, h->stream));
+
+    StreamLaunch& L = h->launch;
+    L.x = h->x;
+    L.y = h->y;
+    L.w = h->w;
+    L.pv = h->pv;
+    L.n = cfg->n_fish;
+    L.seed = cfg->seed;
+    L.school = cfg->school_id;
+    L.real_is_double = dbl ? 1 : 0;
+    L.acc = acc_mode(cfg->precision);
+    const bool vec_ok = aligned(h->x, 16) && aligned(h->y, 16) && aligned(h->w, 16) &&
+                        aligned(h->pv, 16);
+    L.vec = vec_ok ? (dbl ? 2 : 4) : 1;
+    L.block = 512;
+    L.pond_half = cfg->pond_half;
+    L.step = cfg->step;
+    L.w0 = cfg->w0;
+    L.w_min = cfg->w_min;
+    L.w_max = cfg->w_max;
+    L.ctl = h->ctl;
+    int sms = 0;
+    FSB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    int per_sm = fsb::stream_blocks_per_sm(L);
+    if (per_sm < 1) per_sm = 1;
+    const uint64_t groups = (cfg->n_fish + L.vec - 1) / L.vec;
+    const uint64_t need = (groups + L.block - 1) / L.block;
+    const uint64_t full = static_cast<uint64_t>(sms) * per_sm;
+    L.grid = static_cast<int>(need < full ? need : full);
+    if (L.grid < 1) L.grid = 1;
+    FSB_CUDA(cudaMalloc(&h->partials, sizeof(BlockPartial) * L.grid));
+    L.partials = h->partials;
+    int r = ensure_ring(h, 1024);
+    if (r != FSB_OK) return r;
+
+    if (init) {
+      FSB_CUDA(cudaMemcpyAsync(h->x, init->x, bytes, cudaMemcpyHostToDevice, h->stream));
+      FSB_CUDA(cudaMemcpyAsync(h->y, init->y, bytes, cudaMemcpyHostToDevice, h->stream));
+      FSB_CUDA(cudaMemcpyAsync(h->w, init->w, bytes, cudaMemcpyHostToDevice, h->stream));
+      FSB_CUDA(cudaMemcpyAsync(h->pv, init->prev_objective, bytes, cudaMemcpyHostToDevice,
+                               h->stream));
+    } else {
+      FSB_CUDA(fsb::launch_init(L, cfg->init_weight_mode, h->stream));
+    }
+    return FSB_OK;
+  }());
+#undef FSB_TRY
+  *out = h;
+  return FSB_OK;
+}
+
+int fsb_step(fsb_handle h, uint32_t n_steps, fsb_step_stats* host_stats) {
+  if (!h) return fail(FSB_ERR_INVALID_ARG, "handle is NULL");
+  if (n_steps == 0) return fail(FSB_ERR_INVALID_ARG, "n_steps must be >= 1");
+  if (h->step + n_steps > 0xFFFFFFFFull)
+    return fail(FSB_ERR_INVALID_ARG, "step counter would pass 2^32 - 1");
+  int rc = ensure_ring(h, n_steps);
+  if (rc != FSB_OK) return rc;
+  rc = run_stream(h, n_steps);
+  if (rc != FSB_OK) return rc;
+  h->step += n_steps;
+  h->last_n = n_steps;
+  if (host_stats) {
+    FSB_CUDA(cudaMemcpyAsync(host_stats, h->ring, sizeof(fsb_step_stats) * n_steps,
+                             cudaMemcpyDeviceToHost, h->stream));
+    return check_status_word(h);
+  }
+  return FSB_OK;
+}
+
+int fsb_last_stats(fsb_handle h, fsb_step_stats* host_stats, uint32_t n_steps) {
+  if (!h || !host_stats) return fail(FSB_ERR_INVALID_ARG, "NULL argument");
+  if (n_steps == 0 || n_steps > h->last_n)
+    return fail(FSB_ERR_INVALID_ARG, "n_steps must be in [1, %u]", h->last_n);
+  FSB_CUDA(cudaMemcpyAsync(host_stats, h->ring, sizeof(fsb_step_stats) * n_steps,
+                           cudaMemcpyDeviceToHost, h->stream));
+  return check_status_word(h);
+}
+
+int fsb_read_state(fsb_handle h, void* x, void* y, void* w, void* prev_objective,
+                   void* current_objective, uint64_t* step_out) {
+  if (!h) return fail(FSB_ERR_INVALID_ARG, "handle is NULL");
+  const size_t bytes = h->elem * h->cfg.n_fish;
+  if (x) FSB_CUDA(cudaMemcpyAsync(x, h->x, bytes, cudaMemcpyDeviceToHost, h->stream));
+  if (y) FSB_CUDA(cudaMemcpyAsync(y, h->y, bytes, cudaMemcpyDeviceToHost, h->stream));
+  if (w) FSB_CUDA(cudaMemcpyAsync(w, h->w, bytes, cudaMemcpyDeviceToHost, h->stream));
+  if (prev_objective)
+    FSB_CUDA(cudaMemcpyAsync(prev_objective, h->pv, bytes, cudaMemcpyDeviceToHost, h->stream));
+  if (current_objective) {
+    void* cur = nullptr;
+    FSB_CUDA(cudaMallocAsync(&cur, bytes, h->stream));
+    cudaError_t e = fsb::launch_objective(h->launch, cur, h->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(current_objective, cur, bytes, cudaMemcpyDeviceToHost, h->stream);
+    cudaFreeAsync(cur, h->stream);
+    FSB_CUDA(e);
+  }
+  if (step_out) *step_out = h->step;
+  return check_status_word(h);
+}
+
+int fsb_destroy(fsb_handle h) {
+  if (!h) return FSB_OK;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  release(h);
+  if (e != cudaSuccess) return fail(FSB_ERR_CUDA, "sync at destroy: %s", cudaGetErrorString(e));
+  return FSB_OK;
+}
+
+int fsb_set_kernel_timing(fsb_handle h, int enable) {
+  if (!h) return fail(FSB_ERR_INVALID_ARG, "handle is NULL");
+  int rc = collect_timing(h);
+  if (rc != FSB_OK) return rc;
+  h->timing = enable != 0;
+  h->fused_ms = 0.0;
+  h->fused_launches = 0;
+  return FSB_OK;
+}
+
+int fsb_kernel_time(fsb_handle h, double* fused_ms, uint64_t* fused_launches) {
+  if (!h) return fail(FSB_ERR_INVALID_ARG, "handle is NULL");
+  int rc = collect_timing(h);
+  if (rc != FSB_OK) return rc;
+  if (fused_ms) *fused_ms = h->fused_ms;
+  if (fused_launches) *fused_launches = h->fused_launches;
+  return FSB_OK;
+}
+
+int fsb_handle_path(fsb_handle h, int* path_out) {
+  if (!h || !path_out) return fail(FSB_ERR_INVALID_ARG, "NULL argument");
+  *path_out = h->path;
+  return FSB_OK;
+}
+
+int fsb_run_batch(const fsb_config* tmpl, uint32_t n_schools, const uint64_t* offsets,
+                  const uint64_t* seeds, const fsb_state_dev* state, int init,
+                  uint64_t start_step, uint32_t n_steps, fsb_step_stats* stats,
+                  void* cuda_stream) {
+  (void)tmpl;
+  (void)n_schools;
+  (void)offsets;
+  (void)seeds;
+  (void)state;
+  (void)init;
+  (void)start_step;
+  (void)n_steps;
+  (void)stats;
+  (void)cuda_stream;
+  return fail(FSB_ERR_UNSUPPORTED, "batched launch not available in this build");
+}
+
+const char* fsb_strerror(int status) {
+  switch (status) {
+    case FSB_OK: return "FSB_OK";
+    case FSB_ERR_INVALID_ARG: return "FSB_ERR_INVALID_ARG";
+    case FSB_ERR_CUDA: return "FSB_ERR_CUDA";
+    case FSB_ERR_OOM: return "FSB_ERR_OOM";
+    case FSB_ERR_UNSUPPORTED: return "FSB_ERR_UNSUPPORTED";
+    case FSB_ERR_TIMEOUT: return "FSB_ERR_TIMEOUT";
+    case FSB_ERR_STATE: return "FSB_ERR_STATE";
+    default: return "FSB_ERR_UNKNOWN";
+  }
+}
+
+const char* fsb_last_error(void) { return g_last_error; }
+
+}  // extern "C"

@@ -1,0 +1,251 @@
+"""GPU parity of the streaming path (C ABI) against the CPU oracle.
+
+Per-fish state (x, y, weight, prevObjective, currentObjective) and max|delta|
+must be bit-exact; the paper's eat() statistic max(prev - cur) too; the
+barycentre sums within the tolerance of the arithmetic mode.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2507_20173_gb300 as fsb
+from fsb_testutil import (BARY_TOL, assert_state_equal, assert_stats_match, bary_errors,
+                          oracle_config, oracle_precision)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PRECISIONS = [fsb.FSB_FP32, fsb.FSB_FP32_KAHAN, fsb.FSB_FP64_ACC, fsb.FSB_FP64_STATE]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2507_20173_gb300 import build
+    build.build()
+    fsb.lib()
+
+
+def run_pair(cfg, steps, calls=None):
+    """GPU and oracle side by side; returns (gpu state, gpu stats, oracle
+    school, oracle stats)."""
+    school = fsb.School.create(cfg)
+    calls = calls or [steps]
+    stats = np.concatenate([school.step(n, stats=True) for n in calls])
+    got = school.read()
+    school.destroy()
+    ocfg = oracle_config(cfg)
+    ref = oracle.init(ocfg, oracle_precision(cfg))
+    ref_stats = oracle.run(ocfg, ref, 0, steps)
+    return got, stats, ref, ref_stats
+
+
+@pytest.mark.parametrize("precision", [fsb.FSB_FP32_KAHAN, fsb.FSB_FP64_STATE])
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("n", [1, 2, 3, 31, 32, 33, 4095, 4096, 4097, 10000])
+def test_init_matches_oracle(n, mode, precision):
+    cfg = fsb.fsb_config_init(n, 0xABCDEF0123 + n, init_weight_mode=mode,
+                              precision=precision, school_id=n % 7)
+    school = fsb.School.create(cfg)
+    got = school.read()
+    school.destroy()
+    assert got["step"] == 0
+    ref = oracle.init(oracle_config(cfg), oracle_precision(cfg))
+    assert_state_equal(got, ref, "init N=%d" % n)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_small_school_every_step(precision):
+    """N = 10,000, seed 0, T = 100: stats of every step and the final state."""
+    cfg = fsb.fsb_config_init(10_000, 0, precision=precision)
+    got, stats, ref, ref_stats = run_pair(cfg, 100)
+    assert_state_equal(got, ref, "N=10000 T=100")
+    assert got["step"] == 100
+    assert_stats_match(stats, ref_stats, precision, "N=10000")
+
+
+def test_small_school_state_after_each_step():
+    cfg = fsb.fsb_config_init(10_000, 0)
+    school = fsb.School.create(cfg)
+    ocfg = oracle_config(cfg)
+    ref = oracle.init(ocfg)
+    for t in range(1, 21):
+        school.step(1)
+        ref_stats = oracle.run(ocfg, ref, t - 1, 1)
+        got = school.read()
+        assert_state_equal(got, ref, "step %d" % t)
+        st = np.zeros(1, fsb.STATS_DTYPE)
+        fsb.fsb_last_stats(school.handle, st, 1)
+        assert_stats_match(st, ref_stats, cfg.precision, "step %d" % t)
+    school.destroy()
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 31, 32, 33, 511, 512, 513, 4095, 4096, 4097])
+def test_ragged_sizes(n):
+    cfg = fsb.fsb_config_init(n, 99 + n, school_id=3, step=2.5)
+    got, stats, ref, ref_stats = run_pair(cfg, 9)
+    assert_state_equal(got, ref, "N=%d" % n)
+    assert_stats_match(stats, ref_stats, cfg.precision, "N=%d" % n)
+
+
+@pytest.mark.parametrize("precision", [fsb.FSB_FP32_KAHAN, fsb.FSB_FP64_STATE])
+def test_unaligned_buffers_take_the_scalar_path(precision):
+    """Buffers offset by one element are not 16-byte aligned, so the library
+    runs its scalar kernel; results are the same."""
+    n, steps = 1003, 12
+    cfg = fsb.fsb_config_init(n, 5, precision=precision)
+    dt = torch.float64 if precision == fsb.FSB_FP64_STATE else torch.float32
+    big = [torch.empty(n + 1, dtype=dt, device="cuda") for _ in range(4)]
+    bufs = fsb.FsbStateDev(*(b[1:].data_ptr() for b in big))
+    h = fsb.fsb_create(cfg, bufs, None, 0, torch.cuda.current_stream().cuda_stream)
+    stats = np.zeros(steps, fsb.STATS_DTYPE)
+    fsb.fsb_step(h, steps, stats)
+    npdt = np.float64 if precision == fsb.FSB_FP64_STATE else np.float32
+    got = {k: np.empty(n, npdt) for k in ("x", "y", "w", "prev", "cur")}
+    fsb.fsb_read_state(h, got["x"], got["y"], got["w"], got["prev"], got["cur"])
+    fsb.fsb_destroy(h)
+    ocfg = oracle_config(cfg)
+    ref = oracle.init(ocfg, oracle_precision(cfg))
+    ref_stats = oracle.run(ocfg, ref, 0, steps)
+    assert_state_equal(got, ref, "unaligned")
+    assert_stats_match(stats, ref_stats, precision, "unaligned")
+
+
+def test_split_calls_equal_one_call():
+    cfg = fsb.fsb_config_init(3001, 17)
+    got, stats, ref, ref_stats = run_pair(cfg, 10, calls=[3, 1, 6])
+    assert_state_equal(got, ref, "split")
+    assert_stats_match(stats, ref_stats, cfg.precision, "split")
+
+
+def test_long_call_uses_chunked_graphs():
+    """More steps than one captured graph holds (2048): chunk graphs plus
+    direct launches must give the same trajectory."""
+    cfg = fsb.fsb_config_init(67, 23, step=1.0)
+    got, stats, ref, ref_stats = run_pair(cfg, 2048 + 700)
+    assert_state_equal(got, ref, "long call")
+    assert_stats_match(stats, ref_stats, cfg.precision, "long call")
+
+
+def test_library_owned_buffers_and_side_stream():
+    cfg = fsb.fsb_config_init(2500, 8)
+    s = torch.cuda.Stream()
+    h = fsb.fsb_create(cfg, None, None, 0, s.cuda_stream)
+    stats = np.zeros(15, fsb.STATS_DTYPE)
+    fsb.fsb_step(h, 15, stats)
+    got = {k: np.empty(2500, np.float32) for k in ("x", "y", "w", "prev", "cur")}
+    assert fsb.fsb_read_state(h, got["x"], got["y"], got["w"], got["prev"], got["cur"]) == 15
+    fsb.fsb_destroy(h)
+    ocfg = oracle_config(cfg)
+    ref = oracle.init(ocfg)
+    ref_stats = oracle.run(ocfg, ref, 0, 15)
+    assert_state_equal(got, ref, "library buffers")
+    assert_stats_match(stats, ref_stats, cfg.precision, "library buffers")
+
+
+@pytest.mark.parametrize("precision", [fsb.FSB_FP32_KAHAN, fsb.FSB_FP64_STATE])
+def test_resume_from_host_checkpoint(precision):
+    cfg = fsb.fsb_config_init(4321, 77, precision=precision, init_weight_mode=1)
+    a = fsb.School.create(cfg)
+    a.step(13)
+    mid = a.read()
+    a.step(11)
+    end_a = a.read()
+    a.destroy()
+    b = fsb.School.create(cfg, init={"x": mid["x"], "y": mid["y"], "w": mid["w"],
+                                     "prev_objective": mid["prev"]}, start_step=mid["step"])
+    b.step(11)
+    end_b = b.read()
+    b.destroy()
+    assert end_b["step"] == end_a["step"] == 24
+    for k in ("x", "y", "w", "prev", "cur"):
+        assert np.array_equal(end_a[k], end_b[k]), k
+
+
+def test_runs_are_deterministic():
+    cfg = fsb.fsb_config_init(50_000, 4)
+    outs = []
+    for _ in range(2):
+        s = fsb.School.create(cfg)
+        st = s.step(30, stats=True)
+        outs.append((st, s.read()))
+        s.destroy()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    for k in ("x", "y", "w", "prev"):
+        assert np.array_equal(outs[0][1][k], outs[1][1][k])
+
+
+def test_kernel_timing_counts_fused_launches():
+    cfg = fsb.fsb_config_init(100_000, 1)
+    s = fsb.School.create(cfg)
+    fsb.fsb_set_kernel_timing(s.handle, True)
+    s.step(9)
+    ms, n = fsb.fsb_kernel_time(s.handle)
+    assert n == 8 and ms > 0.0
+    fsb.fsb_set_kernel_timing(s.handle, False)
+    s.destroy()
+
+
+def test_argument_errors():
+    cfg = fsb.fsb_config_init(10, 1)
+    s = fsb.School.create(cfg)
+    with pytest.raises(fsb.FsbError) as e:
+        fsb.fsb_step(s.handle, 0)
+    assert e.value.status == fsb.FSB_ERR_INVALID_ARG
+    s.destroy()
+    with pytest.raises(fsb.FsbError) as e:
+        fsb.fsb_create(fsb.fsb_config_init(10, 1), None, None, 0xFFFFFFFF, None)
+    assert e.value.status == fsb.FSB_ERR_INVALID_ARG
+
+
+def test_still_school_never_eats():
+    cfg = fsb.fsb_config_init(777, 2, step=0.0, init_weight_mode=1)
+    got, stats, ref, ref_stats = run_pair(cfg, 5)
+    assert np.all(stats["max_abs_delta"] == 0.0)
+    assert_state_equal(got, ref, "still")
+
+
+def test_full_size_stream_school_sampled():
+    """N = 2^28, seed 2, T = 100 in the launch configuration the benchmark
+    times.  Sampled fish are followed by the oracle one by one (positions do
+    not depend on weights; weights follow from the GPU's verified maxima);
+    the last step's max|delta|, eat() statistic and barycentre sums are
+    checked against the whole read-back state."""
+    n, steps, seed = 1 << 28, 100, 2
+    free, _ = torch.cuda.mem_get_info()
+    if free < 12 * (1 << 30):
+        pytest.skip("needs ~12 GB of free device memory")
+    cfg = fsb.fsb_config_init(n, seed)
+    s = fsb.School.create(cfg)
+    start = s.read()
+    stats = s.step(steps, stats=True)
+    got = s.read()
+    s.destroy()
+    rng = np.random.default_rng(0)
+    idx = np.unique(np.concatenate([
+        np.arange(0, 4096), np.arange(n - 4096, n),
+        (np.arange(1, 200) * (n // 200)), rng.integers(0, n, 20000)])).astype(np.int64)
+    ocfg = oracle_config(cfg)
+    for i in idx:
+        fish = np.zeros(1, oracle.FISH_F32)
+        fish["x"], fish["y"] = start["x"][i], start["y"][i]
+        fish["weight"] = start["w"][i]
+        fish["prevObjective"] = start["prev"][i]
+        fish["currentObjective"] = start["cur"][i]
+        xs, ys, ds, fish = oracle.track_fish(ocfg, int(i), 0, steps, fish)
+        assert xs[-1] == got["x"][i] and ys[-1] == got["y"][i], i
+        assert fish["prevObjective"][0] == got["prev"][i], i
+        assert fish["currentObjective"][0] == got["cur"][i], i
+        assert np.all(np.abs(ds) <= stats["max_abs_delta"]), i
+        ws = oracle.eat_fish(ocfg, float(start["w"][i]), ds, stats["max_abs_delta"])
+        assert ws[-1] == got["w"][i], i
+    delta = got["cur"] - got["prev"]
+    assert stats["max_abs_delta"][-1] == np.max(np.abs(delta))
+    assert stats["eat_max_diff"][-1] == np.max(got["prev"] - got["cur"])
+    w64 = got["w"].astype(np.float64)
+    ref_w = np.sum(w64)
+    ref_x = np.sum(w64 * got["x"].astype(np.float64))
+    abs_x = np.sum(w64 * np.abs(got["x"].astype(np.float64)))
+    assert abs(stats["sum_w"][-1] - ref_w) / ref_w <= BARY_TOL[cfg.precision]
+    assert abs(stats["sum_wx"][-1] - ref_x) / abs_x <= BARY_TOL[cfg.precision]
