@@ -52,6 +52,8 @@ def parse_args():
     ap.add_argument("--workload", choices=["stream", "small", "resident"], default="stream")
     ap.add_argument("--precision", choices=["FP32", "FP32_KAHAN", "FP64_ACC", "FP64_STATE"],
                     default="FP32_KAHAN")
+    ap.add_argument("--n-fish", type=int, default=None,
+                    help="override the school size (profiling on a smaller case)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -226,7 +228,7 @@ def run_ours(args, world, rank, local, pg):
     prec = getattr(fsb, "FSB_" + args.precision)
     dbl = prec == fsb.FSB_FP64_STATE
     elem = 8 if dbl else 4
-    n = wl.n_fish
+    n = args.n_fish or wl.n_fish
     cfg = fsb.fsb_config_init(n, wl.seed + rank, precision=prec, school_id=wl.school_id)
     stream = torch.cuda.current_stream()
 
@@ -319,7 +321,8 @@ def run_ours(args, world, rank, local, pg):
                 "steps": steps, "warmup": warmup, "ms_per_step": ms_max / steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64" if dbl else "f32", "data": "synthetic",
-                "config": {"workload": wl.name, "n_fish": n, "seed": wl.seed,
+                "config": {"workload": wl.name if n == wl.n_fish else
+                           "%s (resized to N=%d)" % (wl.name, n), "n_fish": n, "seed": wl.seed,
                            "precision": args.precision,
                            "path": {1: "stream", 2: "resident"}.get(path, str(path)),
                            "l2": "inputs larger than L2 (%.1f GB state vs 129 MB L2)"

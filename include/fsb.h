@@ -235,6 +235,35 @@ int fsb_kernel_time(fsb_handle h, double* fused_ms, uint64_t* fused_launches);
  * resolved. */
 int fsb_handle_path(fsb_handle h, int* path_out);
 
+/* Advance a school held in caller-owned device arrays by n_steps steps
+ * WITHOUT ANY DEVICE ALLOCATION.  The paper has no counterpart: this exists
+ * for callers that cannot let a library allocate GPU memory at call time --
+ * hosts that own all device memory through their own arena and forbid later
+ * cudaMalloc, and latency-bound pipelines in which cudaMalloc / cudaFree
+ * (which can synchronise the whole device) would stall their other streams.
+ * It runs the same streaming kernels as fsb_step; their scratch (control
+ * word, per-block reduction partials, per-step statistics ring) lives in one
+ * fixed file-scope __device__ array of about 210 KB that every GPU loading
+ * the library holds until the process exits.
+ *   cfg         as for fsb_create (path is ignored: always streaming)
+ *   state       caller-owned device arrays (fsb_state_dev layout) holding the
+ *               school at step start_step; advanced in place
+ *   start_step  the state's step counter t
+ *   n_steps     1 .. 4096 (the statistics ring's size in the static array);
+ *               larger values return FSB_ERR_INVALID_ARG with that reason in
+ *               fsb_last_error() -- split longer runs into several calls
+ *   stats_out   NULL, or n_steps records in host or device memory, written
+ *               in stream order (synchronise the stream before reading them)
+ * The first call on each device looks up the array's device address (set-up
+ * done once per device, with that device current); make that first call
+ * before any stream capture.  All calls on a device share the one array and
+ * rewrite it: calls whose kernels overlap on the GPU (different streams or
+ * threads) race and corrupt each other's results, so serialise them.
+ * Allocates nothing (no cudaMalloc, cudaFree, graph or event creation).
+ * Asynchronous on cuda_stream. */
+int fsb_step_static(const fsb_config* cfg, const fsb_state_dev* state, uint64_t start_step,
+                    uint32_t n_steps, fsb_step_stats* stats_out, void* cuda_stream);
+
 /* Name of a status code (static string). */
 const char* fsb_strerror(int status);
 

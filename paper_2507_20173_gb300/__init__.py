@@ -40,7 +40,7 @@ FSB_PATH_RESIDENT = 2
 EXPORTED = ("fsb_config_init", "fsb_create", "fsb_step", "fsb_read_state",
             "fsb_last_stats", "fsb_destroy", "fsb_run_batch",
             "fsb_set_kernel_timing", "fsb_kernel_time", "fsb_handle_path",
-            "fsb_strerror", "fsb_last_error")
+            "fsb_strerror", "fsb_last_error", "fsb_step_static")
 
 
 class FsbError(RuntimeError):
@@ -104,6 +104,7 @@ def lib() -> ctypes.CDLL:
         "fsb_kernel_time": [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u64)],
         "fsb_handle_path": [P, ctypes.POINTER(i32)],
         "fsb_strerror": [i32],
+        "fsb_step_static": [cfgp, ctypes.POINTER(FsbStateDev), u64, u32, P, P],
         "fsb_last_error": [],
     }
     for name, args in sigs.items():
@@ -198,6 +199,21 @@ def fsb_run_batch(tmpl: FsbConfig, offsets: np.ndarray, seeds: np.ndarray,
                                seeds.ctypes.data_as(ctypes.c_void_p), ctypes.byref(state),
                                1 if init else 0, start_step, n_steps, sptr,
                                ctypes.c_void_p(stream or 0)), "fsb_run_batch")
+
+
+def fsb_step_static(cfg: FsbConfig, state: FsbStateDev, start_step: int, n_steps: int,
+                    stats_out=None, stream: int | None = None) -> None:
+    """Allocation-free step of caller-owned device arrays (see include/fsb.h).
+    `stats_out`: None, a host numpy array of STATS_DTYPE, or a device address
+    (int) of n_steps records."""
+    ptr = None
+    if isinstance(stats_out, np.ndarray):
+        assert stats_out.dtype == STATS_DTYPE and stats_out.size >= n_steps
+        ptr = stats_out.ctypes.data_as(ctypes.c_void_p)
+    elif stats_out is not None:
+        ptr = ctypes.c_void_p(int(stats_out))
+    _check(lib().fsb_step_static(ctypes.byref(cfg), ctypes.byref(state), start_step, n_steps,
+                                 ptr, ctypes.c_void_p(stream or 0)), "fsb_step_static")
 
 
 def fsb_set_kernel_timing(handle: int, enable: bool) -> None:

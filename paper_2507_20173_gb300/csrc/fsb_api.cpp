@@ -72,6 +72,11 @@ int acc_mode(int precision) {
 
 }  // namespace
 
+namespace fsb {
+// Lets other translation units report through fsb_last_error().
+int record_error(int status, const char* msg) { return fail(status, "%s", msg); }
+}  // namespace fsb
+
 struct GraphEntry {
   uint32_t key;  // n_steps, or (1u << 31) | chunk for a fused-only chunk graph
   cudaGraphExec_t exec;

@@ -53,6 +53,8 @@ struct StreamLaunch {
 cudaError_t launch_stream_pass(const StreamLaunch& L, int pass_kind, cudaStream_t s);
 cudaError_t launch_init(const StreamLaunch& L, int weight_mode, cudaStream_t s);
 cudaError_t launch_objective(const StreamLaunch& L, void* cur, cudaStream_t s);
+// Record `msg` as the calling thread's fsb_last_error() detail; returns status.
+int record_error(int status, const char* msg);
 // Occupancy-derived blocks per SM for the fused pass of this configuration.
 int stream_blocks_per_sm(const StreamLaunch& L);
 
