@@ -49,11 +49,19 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["stream", "small", "resident"], default="stream")
+    ap.add_argument("--workload", choices=["stream", "small", "resident", "batch"],
+                    default="stream")
+    ap.add_argument("--batch-schools", type=int, default=None,
+                    help="use only the first N schools of the batched ensemble")
+    ap.add_argument("--batch-cluster", type=int, default=0)
+    ap.add_argument("--no-per-school", action="store_true")
     ap.add_argument("--precision", choices=["FP32", "FP32_KAHAN", "FP64_ACC", "FP64_STATE"],
                     default="FP32_KAHAN")
     ap.add_argument("--n-fish", type=int, default=None,
                     help="override the school size (profiling on a smaller case)")
+    ap.add_argument("--stream-kernel", type=int, default=0,
+                    help="0 library choice, 1 vector loads, 2 bulk-copy ring")
+    ap.add_argument("--stream-block", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -89,10 +97,33 @@ def measured_peaks():
 def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2507_20173_gb300", "csrc")
-    for name in ("fsb_stream.cu", "fsb_device.cuh"):
+    for name in ("fsb_stream.cu", "fsb_stream_tma.cu", "fsb_stream_common.cuh",
+                 "fsb_device.cuh", "fsb_reduce.cuh"):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
+
+
+def resident_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2507_20173_gb300", "csrc")
+    for name in ("fsb_resident.cu", "fsb_device.cuh", "fsb_reduce.cuh"):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def resident_instr_per_fish_step(precision):
+    """Lane instructions per fish-step of the resident kernel from the
+    committed ncu summary; None if the kernel changed since."""
+    p = os.path.join(ROOT, "profiles", "resident_instr.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("kernel_source_hash") != resident_source_hash() or d.get("precision") != precision:
+        return None
+    return float(d["lane_instr_per_fish_step"])
 
 
 def ncu_traffic(n_fish, precision):
@@ -181,6 +212,112 @@ def cpu_oracle_rate(n_fish, seed, steps):
     return n_fish * steps / dt, dt
 
 
+def run_batch(args, world, rank, local, pg):
+    """The ragged ensemble (4096 schools, log-uniform sizes in [256, 65536],
+    T = 500): one graph-captured persistent launch, against the same schools
+    run one launch per school (the single-school path, serially on one
+    stream)."""
+    import torch
+
+    import paper_2507_20173_gb300 as fsb
+    from paper_2507_20173_gb300 import build as fsb_build
+
+    torch.cuda.set_device(local)
+    fsb_build.build()
+    fsb.lib()
+    wl = workloads.BATCH
+    offsets, seeds = wl.offsets(), wl.seeds()
+    if args.batch_schools:
+        seeds = seeds[:args.batch_schools]
+        offsets = offsets[:args.batch_schools + 1]
+    seeds = seeds + np.uint64(rank * 100000)
+    n_schools = seeds.size
+    total = int(offsets[-1])
+    steps = args.steps if args.steps is not None else wl.steps
+    warmup = max(3, args.warmup)
+    prec = getattr(fsb, "FSB_" + args.precision)
+    tmpl = fsb.fsb_config_init(1, 0, precision=prec)
+    stream = torch.cuda.current_stream()
+    ts = [torch.zeros(total, dtype=torch.float32, device="cuda") for _ in range(4)]
+    state = fsb.FsbStateDev(*(t.data_ptr() for t in ts))
+
+    def barrier():
+        torch.cuda.synchronize()
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    b = fsb.fsb_batch_create(tmpl, offsets, seeds, state, init=True, stream=stream.cuda_stream)
+    if args.batch_cluster:
+        fsb.fsb_batch_set_cluster(b, args.batch_cluster)
+    fsb.fsb_batch_step(b, warmup)
+    fsb.fsb_batch_step(b, steps)          # captures the timed call's graph
+    fsb.fsb_batch_set_timing(b, True)
+    barrier()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        fsb.fsb_batch_step(b, steps)
+        stop.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = start.elapsed_time(stop)
+    kms, kl = fsb.fsb_batch_kernel_time(b)
+    info = fsb.fsb_batch_info(b)
+    fsb.fsb_batch_destroy(b)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if pg is not None:
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * total * steps / (ms_max / 1e3)
+
+    per_school = None
+    if not args.no_per_school:
+        handles = []
+        for k in range(n_schools):
+            lo, hi = int(offsets[k]), int(offsets[k + 1])
+            cfg = fsb.fsb_config_init(hi - lo, int(seeds[k]), school_id=k, precision=prec)
+            bufs = fsb.FsbStateDev(*(t_.data_ptr() + 4 * lo for t_ in ts))
+            handles.append(fsb.fsb_create(cfg, bufs, None, 0, stream.cuda_stream))
+        for h in handles:
+            fsb.fsb_step(h, warmup)
+        barrier()
+        start.record(stream)
+        for h in handles:
+            fsb.fsb_step(h, steps)
+        stop.record(stream)
+        torch.cuda.synchronize()
+        ps_ms = start.elapsed_time(stop)
+        for h in handles:
+            fsb.fsb_destroy(h)
+        per_school = {"value": total * steps / (ps_ms / 1e3), "unit": UNIT,
+                      "ms": ps_ms, "launches": n_schools,
+                      "what": "one fsb_step(T) launch per school on the single-school "
+                              "path (library's choice: resident), serially on one stream"}
+    clocks = clk.summary()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": steps, "warmup": warmup, "ms_per_step": ms_max / steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": wl.name if n_schools == wl.n_schools else
+                           "%s (first %d schools)" % (wl.name, n_schools),
+                           "n_schools": n_schools, "total_fish": total,
+                           "precision": args.precision, "batch": info,
+                           "l2": "state %.2f GB; each school's state stays on chip for the call"
+                                 % (16 * total / 1e9),
+                           "parallelism": "replicas x%d" % world},
+                "roofline": {"bound": "alu", "kernel": "batch_kernel", "launches": kl,
+                             "avg_launch_ms": kms / kl if kl else None, "achieved": None,
+                             "peak": None, "frac": None, "traffic": None,
+                             "unit": "Glane-instr/s"},
+                "per_school": per_school,
+                "batched_over_per_school": (value / world) / per_school["value"]
+                if per_school else None,
+                "cpu_baseline": None, "e2e": None, "gpu_launches": 3, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+
+
 def run_reference(args, world, rank):
     """The oracle as it stands, each bench step a bounded sample of the
     workload (2^22 fish of the same school rule, one step)."""
@@ -238,8 +375,13 @@ def run_ours(args, world, rank, local, pg):
             pg.barrier()
         torch.cuda.synchronize()
 
+    tuning = {"stream_kernel": args.stream_kernel, "stream_block": args.stream_block}
+
     # ---- device-resident timing
     school = fsb.School.create(cfg, stream=stream)
+    if any(tuning.values()):
+        fsb.fsb_set_tuning(school.handle, **tuning)
+    tuning = fsb.fsb_get_tuning(school.handle)
     school.step(warmup)
     fsb.fsb_set_kernel_timing(school.handle, True)
     fsb.fsb_kernel_time(school.handle)
@@ -261,18 +403,34 @@ def run_ours(args, world, rank, local, pg):
     ms_max = float(t.item())
     value = world * n * steps / (ms_max / 1e3)
 
-    # ---- roofline of the fused pass
+    # ---- roofline of the dominant kernel
     peak, peak_kind = measured_peaks()
     bytes_per_fish_step = 8 * elem
     avg_fused_s = (fused_ms / fused_n) / 1e3 if fused_n else None
-    achieved = bytes_per_fish_step * n / avg_fused_s / 1e9 if avg_fused_s else None
-    traffic = ncu_traffic(n, args.precision)
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak if achieved else None, "traffic": traffic,
-            "peak_source": peak_kind + " hbm_gbs (STREAM copy)",
-            "kernel": "stream_pass_kernel<fused>", "launches": fused_n,
-            "avg_launch_ms": avg_fused_s * 1e3 if avg_fused_s else None,
-            "algorithmic_bytes_per_launch": bytes_per_fish_step * n}
+    if path == fsb.FSB_PATH_RESIDENT:
+        # one launch advances all `steps` steps with the state on chip: bound
+        # by instruction issue, 152 SMs x 4 schedulers x 32 lanes per clock
+        ipfs = resident_instr_per_fish_step(args.precision)
+        fish_steps_per_launch = n * steps
+        rate = fish_steps_per_launch / avg_fused_s if avg_fused_s else None
+        roof = {"bound": "alu", "unit": "Glane-instr/s", "kernel": "resident_kernel",
+                "launches": fused_n, "avg_launch_ms": avg_fused_s * 1e3 if avg_fused_s else None,
+                "fish_steps_per_launch": fish_steps_per_launch,
+                "lane_instr_per_fish_step": ipfs, "traffic": None}
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        roof["peak_source"] = "issue peak %d SMs x 128 lanes x measured median SM clock" % sms
+        roof["_sms"] = sms
+        roof["achieved"] = rate * ipfs / 1e9 if (rate and ipfs) else None
+    else:
+        achieved = bytes_per_fish_step * n / avg_fused_s / 1e9 if avg_fused_s else None
+        traffic = ncu_traffic(n, args.precision)
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None, "traffic": traffic,
+                "peak_source": peak_kind + " hbm_gbs (STREAM copy)",
+                "kernel": ("stream_pass_tma_kernel<fused>" if tuning["stream_kernel"] == 2
+                           else "stream_pass_kernel<fused>"), "launches": fused_n,
+                "avg_launch_ms": avg_fused_s * 1e3 if avg_fused_s else None,
+                "algorithmic_bytes_per_launch": bytes_per_fish_step * n}
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
@@ -292,6 +450,8 @@ def run_ours(args, world, rank, local, pg):
         barrier()
         t0 = time.perf_counter()
         h = fsb.fsb_create(cfg, bufs, host, 0, stream.cuda_stream)
+        if args.stream_kernel or args.stream_block:
+            fsb.fsb_set_tuning(h, stream_kernel=args.stream_kernel, stream_block=args.stream_block)
         fsb.fsb_step(h, steps, stats)
         fsb.fsb_read_state(h, *(outs[k].numpy() for k in ("x", "y", "w", "prev", "cur")))
         e2e_s = time.perf_counter() - t0
@@ -316,6 +476,12 @@ def run_ours(args, world, rank, local, pg):
                "sample": "%d fish x %d steps of the %s school (same init rule), %.1f s"
                          % (cn, cs, wl.name, dt)}
 
+    clocks = clk.summary()
+    if roof.get("bound") == "alu":
+        sms = roof.pop("_sms")
+        mhz = clocks.get("sm_mhz") or 2070.0
+        roof["peak"] = sms * 4 * 32 * mhz * 1e6 / 1e9
+        roof["frac"] = roof["achieved"] / roof["peak"] if roof.get("achieved") else None
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": steps, "warmup": warmup, "ms_per_step": ms_max / steps,
@@ -328,9 +494,10 @@ def run_ours(args, world, rank, local, pg):
                            "l2": "inputs larger than L2 (%.1f GB state vs 129 MB L2)"
                                  % (4 * elem * n / 1e9) if 4 * elem * n > L2_BYTES
                                  else "state fits in L2 (reused across steps)",
-                           "parallelism": "replicas x%d" % world},
+                           "parallelism": "replicas x%d" % world, "tuning": tuning},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": steps + 1, "clocks": clk.summary()}
+                "gpu_launches": steps + 1 if path != fsb.FSB_PATH_RESIDENT else 1,
+                "clocks": clocks}
         print(json.dumps(line), flush=True)
 
 
@@ -339,6 +506,8 @@ def main():
     world, rank, local, pg = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload == "batch":
+        run_batch(args, world, rank, local, pg)
     else:
         run_ours(args, world, rank, local, pg)
     if pg is not None:

@@ -198,30 +198,67 @@ int fsb_last_stats(fsb_handle h, fsb_step_stats* host_stats, uint32_t n_steps);
  * Synchronises the stream first.  NULL is accepted. */
 int fsb_destroy(fsb_handle h);
 
-/* Advance many independent schools of uneven size by n_steps, in one
- * persistent launch over a ragged offset table (the batched form of the same
- * per-step update; each school is a separate fish school of the paper).
+/* ---- Batched schools (many independent fish schools in one launch) ----
+ *
+ * Each school is a separate fish school of the paper, advanced by the same
+ * per-step update (Sec. 2.1.2 swim, Sec. 2.1.1 objective, delta, the
+ * Sec. 2.3.2 max reduction, feeding, barycentre); a batch runs all of them
+ * in one persistent launch of thread-block clusters that pop schools from a
+ * largest-first work list over a ragged offset table and keep each school's
+ * state on chip for all steps of a call.  The launch is captured in a CUDA
+ * graph per call length and replayed.
+ *
  *   tmpl        physics fields and precision shared by all schools
  *               (n_fish, seed, school_id and path are ignored); binary32
  *               precisions only (FSB_FP64_STATE -> FSB_ERR_UNSUPPORTED)
  *   n_schools   >= 1
  *   offsets     host array of n_schools + 1 increasing fish offsets,
  *               offsets[0] = 0; school k is fish [offsets[k], offsets[k+1])
- *               and must hold >= 1 fish
+ *               and holds >= 1 fish and at most 65536 (a cluster of eight
+ *               blocks; larger schools -> FSB_ERR_UNSUPPORTED, use fsb_create)
  *   seeds       host array of n_schools keys; school k uses key seeds[k] and
  *               school id k, so it reproduces a single-school run created
  *               with that seed and school_id = k
- *   state       device arrays of offsets[n_schools] fish (binary32), the
- *               school states at step start_step; advanced in place
- *   init        nonzero: first initialise every school by the method's rule
- *               (start_step must then be 0)
+ *   state       device arrays (fsb_state_dev layout, binary32, 4-byte
+ *               aligned) of offsets[n_schools] fish: the school states at
+ *               step start_step; advanced in place; caller-owned
+ *   init        nonzero: initialise every school by the method's rule
+ *               (Sec. 2.1.1) at the start of the first fsb_batch_step,
+ *               which may then have n_steps = 0; start_step must be 0
  *   stats       NULL, or host room for n_schools * n_steps records,
- *               school-major; when given the call synchronises
- * Asynchronous on cuda_stream unless stats is given. */
-int fsb_run_batch(const fsb_config* tmpl, uint32_t n_schools,
-                  const uint64_t* offsets, const uint64_t* seeds,
-                  const fsb_state_dev* state, int init, uint64_t start_step,
-                  uint32_t n_steps, fsb_step_stats* stats, void* cuda_stream);
+ *               school-major (record k * n_steps + s is school k, step s)
+ * The offset table and keys are copied at creation. */
+typedef struct fsb_batch* fsb_batch_handle;
+
+int fsb_batch_create(const fsb_config* tmpl, uint32_t n_schools, const uint64_t* offsets,
+                     const uint64_t* seeds, const fsb_state_dev* state, int init,
+                     uint64_t start_step, void* cuda_stream, fsb_batch_handle* out);
+
+/* Advance every school of the batch by n_steps.  Asynchronous on the
+ * batch's stream unless stats is given (then synchronises and fills it). */
+int fsb_batch_step(fsb_batch_handle b, uint32_t n_steps, fsb_step_stats* stats);
+
+/* Blocks per cluster of the batch launch: 0 (the library's choice: the
+ * smallest of 1, 2, 4, 8 that holds the largest school), 1, 2, 4 or 8.
+ * Too small for the largest school -> FSB_ERR_UNSUPPORTED.  Synchronises. */
+int fsb_batch_set_cluster(fsb_batch_handle b, int cluster);
+
+/* Launch shape and step counter of a batch (any pointer may be NULL). */
+int fsb_batch_info(fsb_batch_handle b, int* cluster, int* n_clusters, uint32_t* n_big,
+                   uint64_t* step);
+
+/* Device time of the batch launches since timing was enabled (CUDA events
+ * on the batch's stream around each launch). */
+int fsb_batch_set_timing(fsb_batch_handle b, int enable);
+int fsb_batch_kernel_time(fsb_batch_handle b, double* ms, uint64_t* launches);
+
+int fsb_batch_destroy(fsb_batch_handle b);
+
+/* One-shot form: create, one fsb_batch_step of n_steps, destroy. */
+int fsb_run_batch(const fsb_config* tmpl, uint32_t n_schools, const uint64_t* offsets,
+                  const uint64_t* seeds, const fsb_state_dev* state, int init,
+                  uint64_t start_step, uint32_t n_steps, fsb_step_stats* stats,
+                  void* cuda_stream);
 
 /* Kernel timing for one handle, the GPU analogue of the paper's
  * omp_get_wtime() bracketing of eat() (Sec. 2.3.2).  While enabled, every
@@ -230,6 +267,42 @@ int fsb_run_batch(const fsb_config* tmpl, uint32_t n_schools,
  * the launch count since it was enabled, synchronising the stream. */
 int fsb_set_kernel_timing(fsb_handle h, int enable);
 int fsb_kernel_time(fsb_handle h, double* fused_ms, uint64_t* fused_launches);
+
+/* Test hook for failure detection, resident path only (no counterpart in
+ * the paper).  On the next fsb_step call, block `block` (>= 0; -1 clears)
+ * skips its arrival at the grid barrier of step index `step` of that call,
+ * so every block's bounded wait runs out; the call then reports
+ * FSB_ERR_TIMEOUT at its next synchronising point, no block hangs, and the
+ * school's state is left as it was before the call.  `timeout_ns` (0 keeps
+ * the current value, default 1 s) bounds every device-side wait of the
+ * handle from then on.  Nothing faults on the GPU: the failure is made on the
+ * host side by withholding one arrival. */
+int fsb_set_fault_injection(fsb_handle h, int block, uint32_t step, uint64_t timeout_ns);
+
+/* Launch shape of a handle's kernels (0 in a field = the library's choice).
+ * Set by the autotuner (paper_2507_20173_gb300.autotune) or by hand; the
+ * results do not depend on it except for the rounding of the barycentre
+ * sums, whose reduction tree follows the grid.
+ *   stream_kernel        1: vector loads; 2: bulk asynchronous copies into a
+ *                        shared-memory ring (binary32, 16-byte aligned state)
+ *   stream_block         threads per block of the streaming pass: 256 or 512
+ *   stream_blocks_per_sm blocks per SM of the streaming grid (capped by
+ *                        occupancy)
+ *   resident_fpt         fish per thread of the resident kernel: 4, 8, 12, 16
+ *   resident_block       threads per block of the resident kernel (multiple
+ *                        of 32, at most the variant's compiled maximum)
+ * A combination that cannot run returns FSB_ERR_INVALID_ARG and leaves the
+ * handle unchanged.  Synchronises the handle's stream. */
+typedef struct {
+    int32_t stream_kernel;
+    int32_t stream_block;
+    int32_t stream_blocks_per_sm;
+    int32_t resident_fpt;
+    int32_t resident_block;
+} fsb_tuning;
+
+int fsb_set_tuning(fsb_handle h, const fsb_tuning* t);
+int fsb_get_tuning(fsb_handle h, fsb_tuning* t);
 
 /* Which single-school path a handle runs (fsb_path value), after AUTO is
  * resolved. */

@@ -40,7 +40,10 @@ FSB_PATH_RESIDENT = 2
 EXPORTED = ("fsb_config_init", "fsb_create", "fsb_step", "fsb_read_state",
             "fsb_last_stats", "fsb_destroy", "fsb_run_batch",
             "fsb_set_kernel_timing", "fsb_kernel_time", "fsb_handle_path",
-            "fsb_strerror", "fsb_last_error", "fsb_step_static")
+            "fsb_strerror", "fsb_last_error", "fsb_step_static", "fsb_set_fault_injection",
+            "fsb_set_tuning", "fsb_get_tuning", "fsb_batch_create", "fsb_batch_step",
+            "fsb_batch_set_cluster", "fsb_batch_info", "fsb_batch_set_timing",
+            "fsb_batch_kernel_time", "fsb_batch_destroy")
 
 
 class FsbError(RuntimeError):
@@ -74,6 +77,15 @@ class FsbStepStats(ctypes.Structure):
                 ("sum_wy", ctypes.c_double)]
 
 
+class FsbTuning(ctypes.Structure):
+    _fields_ = [("stream_kernel", ctypes.c_int32), ("stream_block", ctypes.c_int32),
+                ("stream_blocks_per_sm", ctypes.c_int32), ("resident_fpt", ctypes.c_int32),
+                ("resident_block", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 STATS_DTYPE = np.dtype([("max_abs_delta", "<f8"), ("eat_max_diff", "<f8"),
                         ("sum_w", "<f8"), ("sum_wx", "<f8"), ("sum_wy", "<f8")])
 
@@ -103,6 +115,18 @@ def lib() -> ctypes.CDLL:
         "fsb_set_kernel_timing": [P, i32],
         "fsb_kernel_time": [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u64)],
         "fsb_handle_path": [P, ctypes.POINTER(i32)],
+        "fsb_set_fault_injection": [P, i32, u32, u64],
+        "fsb_set_tuning": [P, ctypes.POINTER(FsbTuning)],
+        "fsb_batch_create": [cfgp, u32, P, P, ctypes.POINTER(FsbStateDev), i32, u64, P,
+                             ctypes.POINTER(P)],
+        "fsb_batch_step": [P, u32, P],
+        "fsb_batch_set_cluster": [P, i32],
+        "fsb_batch_info": [P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(u32),
+                           ctypes.POINTER(u64)],
+        "fsb_batch_set_timing": [P, i32],
+        "fsb_batch_kernel_time": [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u64)],
+        "fsb_batch_destroy": [P],
+        "fsb_get_tuning": [P, ctypes.POINTER(FsbTuning)],
         "fsb_strerror": [i32],
         "fsb_step_static": [cfgp, ctypes.POINTER(FsbStateDev), u64, u32, P, P],
         "fsb_last_error": [],
@@ -216,6 +240,56 @@ def fsb_step_static(cfg: FsbConfig, state: FsbStateDev, start_step: int, n_steps
                                  ptr, ctypes.c_void_p(stream or 0)), "fsb_step_static")
 
 
+def fsb_batch_create(tmpl: FsbConfig, offsets: np.ndarray, seeds: np.ndarray,
+                     state: FsbStateDev, init: bool = False, start_step: int = 0,
+                     stream: int | None = None) -> int:
+    offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+    seeds = np.ascontiguousarray(seeds, dtype=np.uint64)
+    assert offsets.size == seeds.size + 1
+    h = ctypes.c_void_p()
+    _check(lib().fsb_batch_create(ctypes.byref(tmpl), seeds.size,
+                                  offsets.ctypes.data_as(ctypes.c_void_p),
+                                  seeds.ctypes.data_as(ctypes.c_void_p), ctypes.byref(state),
+                                  1 if init else 0, start_step, ctypes.c_void_p(stream or 0),
+                                  ctypes.byref(h)), "fsb_batch_create")
+    return h.value
+
+
+def fsb_batch_step(handle: int, n_steps: int, stats: np.ndarray | None = None) -> None:
+    ptr = None
+    if stats is not None:
+        assert stats.dtype == STATS_DTYPE and stats.flags["C_CONTIGUOUS"]
+        ptr = stats.ctypes.data_as(ctypes.c_void_p)
+    _check(lib().fsb_batch_step(ctypes.c_void_p(handle), n_steps, ptr), "fsb_batch_step")
+
+
+def fsb_batch_set_cluster(handle: int, cluster: int) -> None:
+    _check(lib().fsb_batch_set_cluster(ctypes.c_void_p(handle), cluster), "fsb_batch_set_cluster")
+
+
+def fsb_batch_info(handle: int) -> dict:
+    c, nc, nb, st = ctypes.c_int(), ctypes.c_int(), ctypes.c_uint32(), ctypes.c_uint64()
+    _check(lib().fsb_batch_info(ctypes.c_void_p(handle), ctypes.byref(c), ctypes.byref(nc),
+                                ctypes.byref(nb), ctypes.byref(st)), "fsb_batch_info")
+    return {"cluster": c.value, "n_clusters": nc.value, "n_big": nb.value, "step": st.value}
+
+
+def fsb_batch_set_timing(handle: int, enable: bool) -> None:
+    _check(lib().fsb_batch_set_timing(ctypes.c_void_p(handle), 1 if enable else 0),
+           "fsb_batch_set_timing")
+
+
+def fsb_batch_kernel_time(handle: int) -> tuple[float, int]:
+    ms, n = ctypes.c_double(), ctypes.c_uint64()
+    _check(lib().fsb_batch_kernel_time(ctypes.c_void_p(handle), ctypes.byref(ms),
+                                       ctypes.byref(n)), "fsb_batch_kernel_time")
+    return ms.value, n.value
+
+
+def fsb_batch_destroy(handle: int) -> None:
+    _check(lib().fsb_batch_destroy(ctypes.c_void_p(handle)), "fsb_batch_destroy")
+
+
 def fsb_set_kernel_timing(handle: int, enable: bool) -> None:
     _check(lib().fsb_set_kernel_timing(ctypes.c_void_p(handle), 1 if enable else 0),
            "fsb_set_kernel_timing")
@@ -227,6 +301,22 @@ def fsb_kernel_time(handle: int) -> tuple[float, int]:
     _check(lib().fsb_kernel_time(ctypes.c_void_p(handle), ctypes.byref(ms), ctypes.byref(n)),
            "fsb_kernel_time")
     return ms.value, n.value
+
+
+def fsb_set_fault_injection(handle: int, block: int, step: int, timeout_ns: int = 0) -> None:
+    _check(lib().fsb_set_fault_injection(ctypes.c_void_p(handle), block, step, timeout_ns),
+           "fsb_set_fault_injection")
+
+
+def fsb_set_tuning(handle: int, **fields) -> None:
+    t = FsbTuning(**fields)
+    _check(lib().fsb_set_tuning(ctypes.c_void_p(handle), ctypes.byref(t)), "fsb_set_tuning")
+
+
+def fsb_get_tuning(handle: int) -> dict:
+    t = FsbTuning()
+    _check(lib().fsb_get_tuning(ctypes.c_void_p(handle), ctypes.byref(t)), "fsb_get_tuning")
+    return t.as_dict()
 
 
 def fsb_handle_path(handle: int) -> int:

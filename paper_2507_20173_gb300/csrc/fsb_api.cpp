@@ -100,7 +100,13 @@ struct fsb_school {
   BlockPartial* partials = nullptr;
   fsb_step_stats* ring = nullptr;
   uint32_t ring_cap = 0;
+  int sms = 0;
+  fsb_tuning tuning{};
   StreamLaunch launch{};
+  fsb::ResidentLaunch res{};
+  fsb::ResCtl* rctl = nullptr;
+  double* sums = nullptr;
+  size_t sums_cap = 0;             // doubles
   std::vector<GraphEntry> graphs;
   bool timing = false;
   std::vector<cudaEvent_t> ev_free;
@@ -141,7 +147,10 @@ int ensure_ring(fsb_school* h, uint32_t n) {
 }
 
 int launch_pass(fsb_school* h, int kind, cudaStream_t s) {
-  FSB_CUDA(fsb::launch_stream_pass(h->launch, kind, s));
+  if (h->launch.tma)
+    FSB_CUDA(fsb::launch_stream_pass_tma(h->launch, kind, s));
+  else
+    FSB_CUDA(fsb::launch_stream_pass(h->launch, kind, s));
   return FSB_OK;
 }
 
@@ -252,6 +261,117 @@ int run_stream(fsb_school* h, uint32_t n) {
   return rc;
 }
 
+// Pick (fish per thread, block, grid) so a school of n fish sits in
+// registers across at most one block per SM.  Returns false if it does not
+// fit on chip.
+bool resident_config(int sms, int acc, uint64_t n, fsb::ResidentLaunch* R, int want_fpt = 0,
+                     int want_block = 0) {
+  const int fpts[] = {4, 8, 12, 16};
+  for (int fpt : fpts) {
+    if (want_fpt && fpt != want_fpt) continue;
+    int maxb = fsb::resident_max_block(fpt);
+    if (want_block) {
+      if (want_block % 32 || want_block > maxb) return false;
+      maxb = want_block;
+    }
+    const uint64_t per_block = static_cast<uint64_t>(maxb) * fpt;
+    uint64_t grid = (n + per_block - 1) / per_block;
+    if (grid > static_cast<uint64_t>(sms)) continue;
+    if (grid < 1) grid = 1;
+    const uint64_t slice = (n + grid - 1) / grid;
+    const uint64_t threads = (slice + fpt - 1) / fpt;
+    const int block = static_cast<int>(((threads + 31) / 32) * 32);
+    if (block > maxb) continue;
+    if (fsb::resident_blocks_per_sm(fpt, acc, block) < 1) continue;
+    R->fpt = fpt;
+    R->block = block;
+    R->grid = static_cast<int>((n + slice - 1) / slice);
+    R->slice = slice;
+    return true;
+  }
+  return false;
+}
+
+constexpr int kMaxPartialsPerSm = 8;
+
+// Streaming launch shape: kernel variant, block, grid.  Invalidates graphs.
+int configure_stream(fsb_school* h, int kernel, int block, int blocks_per_sm) {
+  StreamLaunch L = h->launch;
+  const bool tma_ok = !L.real_is_double && L.vec == 4;
+  if (kernel == 0) kernel = 1;
+  if (kernel == 2 && !tma_ok)
+    return fail(FSB_ERR_INVALID_ARG, "bulk-copy kernel needs binary32, 16-byte aligned state");
+  if (kernel != 1 && kernel != 2) return fail(FSB_ERR_INVALID_ARG, "unknown stream kernel");
+  if (block == 0) block = 256;
+  if (block != 256 && block != 512) return fail(FSB_ERR_INVALID_ARG, "stream block must be 256/512");
+  L.tma = kernel == 2 ? 1 : 0;
+  L.block = block;
+  // the vector kernel is compiled for 1, 3 or 4 guaranteed blocks per SM
+  // (register budgets of 255, 80 and 64 per thread at 256 threads)
+  L.min_blocks = 1;
+  if (!L.tma && block == 256 && !L.real_is_double && L.vec == 4 &&
+      (blocks_per_sm == 3 || blocks_per_sm == 4))
+    L.min_blocks = blocks_per_sm;
+  int per_sm = 0;
+  if (L.tma) {
+    FSB_CUDA(fsb::stream_tma_prepare(L));
+    per_sm = fsb::stream_tma_blocks_per_sm(L);
+  } else {
+    per_sm = fsb::stream_blocks_per_sm(L);
+  }
+  if (per_sm < 1) return fail(FSB_ERR_INVALID_ARG, "stream kernel cannot be resident");
+  if (blocks_per_sm > 0 && blocks_per_sm < per_sm) per_sm = blocks_per_sm;
+  if (per_sm > kMaxPartialsPerSm) per_sm = kMaxPartialsPerSm;
+  const uint64_t unit = L.tma ? static_cast<uint64_t>(block) * 4 : static_cast<uint64_t>(block) * L.vec;
+  const uint64_t need = (h->cfg.n_fish + unit - 1) / unit;
+  const uint64_t full = static_cast<uint64_t>(h->sms) * per_sm;
+  L.grid = static_cast<int>(need < full ? need : full);
+  if (L.grid < 1) L.grid = 1;
+  h->launch = L;
+  h->tuning.stream_kernel = kernel;
+  h->tuning.stream_block = block;
+  h->tuning.stream_blocks_per_sm = per_sm;
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+  h->graphs.clear();
+  return FSB_OK;
+}
+
+int ensure_sums(fsb_school* h, uint32_t n) {
+  const size_t need = static_cast<size_t>(n) * h->res.grid * 3;
+  if (h->sums_cap >= need) return FSB_OK;
+  FSB_CUDA(cudaStreamSynchronize(h->stream));
+  double* p = nullptr;
+  FSB_CUDA(cudaMalloc(&p, need * sizeof(double)));
+  if (h->sums) cudaFree(h->sums);
+  h->sums = p;
+  h->sums_cap = need;
+  return FSB_OK;
+}
+
+int run_resident(fsb_school* h, uint32_t n) {
+  int rc = ensure_sums(h, n);
+  if (rc != FSB_OK) return rc;
+  fsb::ResidentLaunch& R = h->res;
+  R.base_step = h->step;
+  R.n_steps = n;
+  R.sums = h->sums;
+  R.ring = h->ring;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (h->timing) {
+    a = take_event(h);
+    b = take_event(h);
+    if (!a || !b) return fail(FSB_ERR_CUDA, "cudaEventCreate failed");
+    FSB_CUDA(cudaEventRecord(a, h->stream));
+  }
+  FSB_CUDA(fsb::launch_resident(R, h->stream));
+  if (h->timing) {
+    FSB_CUDA(cudaEventRecord(b, h->stream));
+    h->ev_pending.emplace_back(a, b);
+  }
+  R.inject_cta = -1;  // a fault injection applies to one call only
+  return FSB_OK;
+}
+
 void release(fsb_school* h) {
   if (!h) return;
   if (h->stream || h->cap_stream) cudaStreamSynchronize(h->stream);
@@ -268,6 +388,8 @@ void release(fsb_school* h) {
     cudaFree(h->pv);
   }
   cudaFree(h->ctl);
+  cudaFree(h->rctl);
+  cudaFree(h->sums);
   cudaFree(h->partials);
   cudaFree(h->ring);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -313,8 +435,6 @@ int fsb_create(const fsb_config* cfg, const fsb_state_dev* buffers, const fsb_st
       if (!q || !aligned(q, elem))
         return fail(FSB_ERR_INVALID_ARG, "state buffer NULL or not %zu-byte aligned", elem);
   }
-  if (cfg->path == FSB_PATH_RESIDENT)
-    return fail(FSB_ERR_UNSUPPORTED, "resident path not available in this build");
 
   fsb_school* h = new (std::nothrow) fsb_school();
   if (!h) return fail(FSB_ERR_OOM, "host allocation failed");
@@ -367,7 +487,6 @@ int fsb_create(const fsb_config* cfg, const fsb_state_dev* buffers, const fsb_st
     const bool vec_ok = aligned(h->x, 16) && aligned(h->y, 16) && aligned(h->w, 16) &&
                         aligned(h->pv, 16);
     L.vec = vec_ok ? (dbl ? 2 : 4) : 1;
-    L.block = 512;
     L.pond_half = cfg->pond_half;
     L.step = cfg->step;
     L.w0 = cfg->w0;
@@ -376,17 +495,46 @@ int fsb_create(const fsb_config* cfg, const fsb_state_dev* buffers, const fsb_st
     L.ctl = h->ctl;
     int sms = 0;
     FSB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
-    int per_sm = fsb::stream_blocks_per_sm(L);
-    if (per_sm < 1) per_sm = 1;
-    const uint64_t groups = (cfg->n_fish + L.vec - 1) / L.vec;
-    const uint64_t need = (groups + L.block - 1) / L.block;
-    const uint64_t full = static_cast<uint64_t>(sms) * per_sm;
-    L.grid = static_cast<int>(need < full ? need : full);
-    if (L.grid < 1) L.grid = 1;
-    FSB_CUDA(cudaMalloc(&h->partials, sizeof(BlockPartial) * L.grid));
+    h->sms = sms;
+    FSB_CUDA(cudaMalloc(&h->partials, sizeof(BlockPartial) * sms * kMaxPartialsPerSm));
     L.partials = h->partials;
+    int r0 = configure_stream(h, 0, 0, 0);
+    if (r0 != FSB_OK) return r0;
+
+    // resident path: binary32 state that fits in registers across the SMs
+    fsb::ResidentLaunch& R = h->res;
+    const bool fits = !dbl && resident_config(sms, h->launch.acc, cfg->n_fish, &R);
+    if (cfg->path == FSB_PATH_RESIDENT && !fits)
+      return fail(FSB_ERR_UNSUPPORTED,
+                  "resident path: school of %llu fish does not fit on chip (binary32 only)",
+                  static_cast<unsigned long long>(cfg->n_fish));
+    h->path = (cfg->path == FSB_PATH_STREAM || !fits) ? FSB_PATH_STREAM : FSB_PATH_RESIDENT;
+    if (h->path == FSB_PATH_RESIDENT) {
+      R.x = h->x;
+      R.y = h->y;
+      R.w = h->w;
+      R.pv = h->pv;
+      R.n = cfg->n_fish;
+      R.seed = cfg->seed;
+      R.school = cfg->school_id;
+      R.pond_half = cfg->pond_half;
+      R.step = cfg->step;
+      R.w0 = cfg->w0;
+      R.w_min = cfg->w_min;
+      R.w_max = cfg->w_max;
+      R.acc = h->launch.acc;
+      h->tuning.resident_fpt = R.fpt;
+      h->tuning.resident_block = R.block;
+      R.ctl = h->ctl;
+      R.timeout_ns = 1000000000ull;
+      R.inject_cta = -1;
+      R.inject_step = 0;
+      FSB_CUDA(cudaMalloc(&h->rctl, sizeof(fsb::ResCtl)));
+      R.rctl = h->rctl;
+    }
     int r = ensure_ring(h, 1024);
     if (r != FSB_OK) return r;
+    StreamLaunch& L2 = h->launch;
 
     if (init) {
       FSB_CUDA(cudaMemcpyAsync(h->x, init->x, bytes, cudaMemcpyHostToDevice, h->stream));
@@ -395,7 +543,7 @@ int fsb_create(const fsb_config* cfg, const fsb_state_dev* buffers, const fsb_st
       FSB_CUDA(cudaMemcpyAsync(h->pv, init->prev_objective, bytes, cudaMemcpyHostToDevice,
                                h->stream));
     } else {
-      FSB_CUDA(fsb::launch_init(L, cfg->init_weight_mode, h->stream));
+      FSB_CUDA(fsb::launch_init(L2, cfg->init_weight_mode, h->stream));
     }
     return FSB_OK;
   }());
@@ -411,7 +559,7 @@ int fsb_step(fsb_handle h, uint32_t n_steps, fsb_step_stats* host_stats) {
     return fail(FSB_ERR_INVALID_ARG, "step counter would pass 2^32 - 1");
   int rc = ensure_ring(h, n_steps);
   if (rc != FSB_OK) return rc;
-  rc = run_stream(h, n_steps);
+  rc = h->path == FSB_PATH_RESIDENT ? run_resident(h, n_steps) : run_stream(h, n_steps);
   if (rc != FSB_OK) return rc;
   h->step += n_steps;
   h->last_n = n_steps;
@@ -481,27 +629,52 @@ int fsb_kernel_time(fsb_handle h, double* fused_ms, uint64_t* fused_launches) {
   return FSB_OK;
 }
 
+int fsb_set_tuning(fsb_handle h, const fsb_tuning* t) {
+  if (!h || !t) return fail(FSB_ERR_INVALID_ARG, "NULL argument");
+  FSB_CUDA(cudaStreamSynchronize(h->stream));
+  const StreamLaunch saved = h->launch;
+  const fsb_tuning saved_t = h->tuning;
+  int rc = configure_stream(h, t->stream_kernel, t->stream_block, t->stream_blocks_per_sm);
+  if (rc != FSB_OK) {
+    h->launch = saved;
+    h->tuning = saved_t;
+    return rc;
+  }
+  if (h->path == FSB_PATH_RESIDENT && (t->resident_fpt || t->resident_block)) {
+    fsb::ResidentLaunch R = h->res;
+    if (!resident_config(h->sms, R.acc, h->cfg.n_fish, &R, t->resident_fpt, t->resident_block)) {
+      h->launch = saved;
+      h->tuning = saved_t;
+      return fail(FSB_ERR_INVALID_ARG, "resident tuning does not fit this school");
+    }
+    h->res = R;
+    h->tuning.resident_fpt = R.fpt;
+    h->tuning.resident_block = R.block;
+  }
+  return FSB_OK;
+}
+
+int fsb_get_tuning(fsb_handle h, fsb_tuning* t) {
+  if (!h || !t) return fail(FSB_ERR_INVALID_ARG, "NULL argument");
+  *t = h->tuning;
+  return FSB_OK;
+}
+
+int fsb_set_fault_injection(fsb_handle h, int block, uint32_t step, uint64_t timeout_ns) {
+  if (!h) return fail(FSB_ERR_INVALID_ARG, "handle is NULL");
+  if (h->path != FSB_PATH_RESIDENT)
+    return fail(FSB_ERR_UNSUPPORTED, "fault injection applies to the resident path only");
+  if (block >= h->res.grid) return fail(FSB_ERR_INVALID_ARG, "block out of range");
+  h->res.inject_cta = block < 0 ? -1 : block;
+  h->res.inject_step = step;
+  if (timeout_ns) h->res.timeout_ns = timeout_ns;
+  return FSB_OK;
+}
+
 int fsb_handle_path(fsb_handle h, int* path_out) {
   if (!h || !path_out) return fail(FSB_ERR_INVALID_ARG, "NULL argument");
   *path_out = h->path;
   return FSB_OK;
-}
-
-int fsb_run_batch(const fsb_config* tmpl, uint32_t n_schools, const uint64_t* offsets,
-                  const uint64_t* seeds, const fsb_state_dev* state, int init,
-                  uint64_t start_step, uint32_t n_steps, fsb_step_stats* stats,
-                  void* cuda_stream) {
-  (void)tmpl;
-  (void)n_schools;
-  (void)offsets;
-  (void)seeds;
-  (void)state;
-  (void)init;
-  (void)start_step;
-  (void)n_steps;
-  (void)stats;
-  (void)cuda_stream;
-  return fail(FSB_ERR_UNSUPPORTED, "batched launch not available in this build");
 }
 
 const char* fsb_strerror(int status) {

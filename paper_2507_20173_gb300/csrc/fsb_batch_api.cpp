@@ -1,0 +1,386 @@
+// fsb_batch_api.cpp -- C ABI of the batched (many schools) path: the batch
+// handle (work list, device copies of the offset table and keys, statistics
+// buffer, cached CUDA graph per call length) and the one-shot fsb_run_batch.
+// All arithmetic runs in fsb_batch.cu.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "fsb_internal.h"
+
+namespace {
+
+int bfail(int status, const char* fmt, ...) {
+  char buf[400];
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  return fsb::record_error(status, buf);
+}
+
+#define BCUDA(call)                                                                        \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return bfail(e_ == cudaErrorMemoryAllocation ? FSB_ERR_OOM : FSB_ERR_CUDA,           \
+                   "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,      \
+                   __LINE__);                                                              \
+  } while (0)
+
+struct BatchGraph {
+  uint32_t n_steps;
+  int init;
+  cudaGraphExec_t exec;
+};
+
+}  // namespace
+
+struct fsb_batch {
+  fsb_config tmpl{};
+  uint32_t n_schools = 0;
+  uint64_t max_school = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  unsigned long long* d_offsets = nullptr;
+  unsigned long long* d_seeds = nullptr;
+  uint32_t* d_order = nullptr;
+  unsigned long long* d_base = nullptr;
+  fsb::BatchCtl* d_bctl = nullptr;
+  fsb_step_stats* d_stats = nullptr;
+  size_t stats_cap = 0;
+  std::vector<uint32_t> sizes_sorted;  // school index by size, largest first
+  std::vector<uint64_t> offsets;       // host copy of the offset table
+  int pending_init = 0;
+  uint64_t step = 0;
+  uint32_t last_n = 0;
+  fsb::BatchLaunch L{};
+  std::vector<BatchGraph> graphs;
+  bool timing = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+  double kernel_ms = 0.0;
+  uint64_t launches = 0;
+};
+
+namespace {
+
+// Whole-cluster queue: schools larger than one block holds (when the
+// cluster has more than one block), then every other school; each queue
+// largest first (longest-processing-time order).
+int build_order(fsb_batch* b, int cluster) {
+  const uint64_t cap = fsb::batch_block_capacity();
+  std::vector<uint32_t> order;
+  order.reserve(b->n_schools);
+  std::vector<uint32_t> big, small;
+  for (uint32_t k : b->sizes_sorted) {
+    const uint64_t n = b->offsets[k + 1] - b->offsets[k];
+    if (cluster > 1 && n > cap)
+      big.push_back(k);
+    else
+      small.push_back(k);
+  }
+  const uint32_t n_big = static_cast<uint32_t>(big.size());
+  order.insert(order.end(), big.begin(), big.end());
+  order.insert(order.end(), small.begin(), small.end());
+  BCUDA(cudaMemcpy(b->d_order, order.data(), sizeof(uint32_t) * order.size(),
+                   cudaMemcpyHostToDevice));
+  b->L.n_big = n_big;
+  return FSB_OK;
+}
+
+int configure_cluster(fsb_batch* b, int cluster) {
+  const uint64_t cap = fsb::batch_block_capacity();
+  if (cluster == 0) {
+    cluster = 1;
+    while (static_cast<uint64_t>(cluster) * cap < b->max_school && cluster < 8) cluster *= 2;
+  }
+  if (cluster != 1 && cluster != 2 && cluster != 4 && cluster != 8)
+    return bfail(FSB_ERR_INVALID_ARG, "batch cluster size must be 1, 2, 4 or 8");
+  if (static_cast<uint64_t>(cluster) * cap < b->max_school)
+    return bfail(FSB_ERR_UNSUPPORTED,
+                 "largest school (%llu fish) exceeds a cluster of %d blocks (%llu fish)",
+                 static_cast<unsigned long long>(b->max_school), cluster,
+                 static_cast<unsigned long long>(cluster * cap));
+  const int n_clusters = fsb::batch_max_clusters(cluster, b->L.acc);
+  if (n_clusters < 1)
+    return bfail(FSB_ERR_UNSUPPORTED, "clusters of %d blocks cannot be resident", cluster);
+  b->L.cluster = cluster;
+  b->L.n_clusters = n_clusters;
+  int rc = build_order(b, cluster);
+  if (rc != FSB_OK) return rc;
+  for (auto& g : b->graphs) cudaGraphExecDestroy(g.exec);
+  b->graphs.clear();
+  return FSB_OK;
+}
+
+int ensure_stats(fsb_batch* b, uint32_t n_steps) {
+  const size_t need = static_cast<size_t>(b->n_schools) * (n_steps ? n_steps : 1);
+  if (b->stats_cap >= need) return FSB_OK;
+  BCUDA(cudaStreamSynchronize(b->stream));
+  fsb_step_stats* p = nullptr;
+  BCUDA(cudaMalloc(&p, sizeof(fsb_step_stats) * need));
+  if (b->d_stats) cudaFree(b->d_stats);
+  b->d_stats = p;
+  b->stats_cap = need;
+  for (auto& g : b->graphs) cudaGraphExecDestroy(g.exec);
+  b->graphs.clear();
+  return FSB_OK;
+}
+
+int enqueue(fsb_batch* b, uint32_t n_steps, int init, cudaStream_t s) {
+  fsb::BatchLaunch L = b->L;
+  L.n_steps = n_steps;
+  L.init = init;
+  L.stats = b->d_stats;
+  BCUDA(fsb::launch_batch(L, s));
+  if (n_steps) BCUDA(fsb::launch_bump_step(b->d_base, n_steps, s));
+  return FSB_OK;
+}
+
+int get_graph(fsb_batch* b, uint32_t n_steps, int init, cudaGraphExec_t* out) {
+  for (auto& g : b->graphs)
+    if (g.n_steps == n_steps && g.init == init) {
+      *out = g.exec;
+      return FSB_OK;
+    }
+  BCUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+  const int rc = enqueue(b, n_steps, init, b->cap_stream);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(b->cap_stream, &graph);
+  if (rc != FSB_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  BCUDA(e);
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  BCUDA(e);
+  if (b->graphs.size() >= 8) {
+    cudaGraphExecDestroy(b->graphs.front().exec);
+    b->graphs.erase(b->graphs.begin());
+  }
+  b->graphs.push_back({n_steps, init, exec});
+  *out = exec;
+  return FSB_OK;
+}
+
+void release(fsb_batch* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  for (auto& g : b->graphs) cudaGraphExecDestroy(g.exec);
+  for (auto& p : b->ev) {
+    cudaEventDestroy(p.first);
+    cudaEventDestroy(p.second);
+  }
+  cudaFree(b->d_offsets);
+  cudaFree(b->d_seeds);
+  cudaFree(b->d_order);
+  cudaFree(b->d_base);
+  cudaFree(b->d_bctl);
+  cudaFree(b->d_stats);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fsb_batch_create(const fsb_config* tmpl, uint32_t n_schools, const uint64_t* offsets,
+                     const uint64_t* seeds, const fsb_state_dev* state, int init,
+                     uint64_t start_step, void* cuda_stream, fsb_batch_handle* out) {
+  if (!out) return bfail(FSB_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!tmpl || !offsets || !seeds || !state)
+    return bfail(FSB_ERR_INVALID_ARG, "NULL argument");
+  if (n_schools == 0) return bfail(FSB_ERR_INVALID_ARG, "n_schools must be >= 1");
+  if (tmpl->precision == FSB_FP64_STATE)
+    return bfail(FSB_ERR_UNSUPPORTED, "the batched path holds binary32 state only");
+  if (tmpl->precision < FSB_FP32 || tmpl->precision > FSB_FP64_STATE)
+    return bfail(FSB_ERR_INVALID_ARG, "unknown precision");
+  if (!(tmpl->pond_half > 0.0) || !(tmpl->step >= 0.0) || !(tmpl->w_min <= tmpl->w_max) ||
+      (tmpl->init_weight_mode != 0 && tmpl->init_weight_mode != 1))
+    return bfail(FSB_ERR_INVALID_ARG, "invalid physics in the template configuration");
+  if (offsets[0] != 0) return bfail(FSB_ERR_INVALID_ARG, "offsets[0] must be 0");
+  uint64_t max_school = 0;
+  for (uint32_t k = 0; k < n_schools; ++k) {
+    if (offsets[k + 1] <= offsets[k])
+      return bfail(FSB_ERR_INVALID_ARG, "school %u is empty or offsets decrease", k);
+    max_school = std::max<uint64_t>(max_school, offsets[k + 1] - offsets[k]);
+  }
+  if (init && start_step != 0)
+    return bfail(FSB_ERR_INVALID_ARG, "initialising schools requires start_step 0");
+  if (start_step >= 0xFFFFFFFFull) return bfail(FSB_ERR_INVALID_ARG, "start_step too large");
+  const void* p[4] = {state->x, state->y, state->w, state->prev_objective};
+  for (const void* q : p)
+    if (!q || (reinterpret_cast<uintptr_t>(q) % 4) != 0)
+      return bfail(FSB_ERR_INVALID_ARG, "state array NULL or not 4-byte aligned");
+
+  fsb_batch* b = new (std::nothrow) fsb_batch();
+  if (!b) return bfail(FSB_ERR_OOM, "host allocation failed");
+  b->tmpl = *tmpl;
+  b->n_schools = n_schools;
+  b->max_school = max_school;
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+  b->pending_init = init ? 1 : 0;
+  b->step = start_step;
+  b->offsets.assign(offsets, offsets + n_schools + 1);
+  b->sizes_sorted.resize(n_schools);
+  std::iota(b->sizes_sorted.begin(), b->sizes_sorted.end(), 0u);
+  std::stable_sort(b->sizes_sorted.begin(), b->sizes_sorted.end(), [&](uint32_t a, uint32_t c) {
+    return offsets[a + 1] - offsets[a] > offsets[c + 1] - offsets[c];
+  });
+  auto body = [&]() -> int {
+    BCUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+    BCUDA(cudaMalloc(&b->d_offsets, sizeof(unsigned long long) * (n_schools + 1)));
+    BCUDA(cudaMalloc(&b->d_seeds, sizeof(unsigned long long) * n_schools));
+    BCUDA(cudaMalloc(&b->d_order, sizeof(uint32_t) * n_schools));
+    BCUDA(cudaMalloc(&b->d_base, sizeof(unsigned long long)));
+    BCUDA(cudaMalloc(&b->d_bctl, sizeof(fsb::BatchCtl)));
+    BCUDA(cudaMemcpy(b->d_offsets, offsets, sizeof(unsigned long long) * (n_schools + 1),
+                     cudaMemcpyHostToDevice));
+    BCUDA(cudaMemcpy(b->d_seeds, seeds, sizeof(unsigned long long) * n_schools,
+                     cudaMemcpyHostToDevice));
+    const unsigned long long base = start_step;
+    BCUDA(cudaMemcpy(b->d_base, &base, sizeof(base), cudaMemcpyHostToDevice));
+    fsb::BatchLaunch& L = b->L;
+    L.x = state->x;
+    L.y = state->y;
+    L.w = state->w;
+    L.pv = state->prev_objective;
+    L.offsets = b->d_offsets;
+    L.seeds = b->d_seeds;
+    L.order = b->d_order;
+    L.n_schools = n_schools;
+    L.pond_half = tmpl->pond_half;
+    L.step = tmpl->step;
+    L.w0 = tmpl->w0;
+    L.w_min = tmpl->w_min;
+    L.w_max = tmpl->w_max;
+    L.acc = tmpl->precision == FSB_FP32 ? fsb::kAccPlain32
+            : tmpl->precision == FSB_FP32_KAHAN ? fsb::kAccKahan32 : fsb::kAccF64;
+    L.weight_mode = tmpl->init_weight_mode;
+    L.base_step = b->d_base;
+    L.bctl = b->d_bctl;
+    int rc = configure_cluster(b, 0);
+    if (rc != FSB_OK) return rc;
+    return ensure_stats(b, 1);
+  };
+  const int rc = body();
+  if (rc != FSB_OK) {
+    release(b);
+    return rc;
+  }
+  *out = b;
+  return FSB_OK;
+}
+
+int fsb_batch_step(fsb_batch_handle b, uint32_t n_steps, fsb_step_stats* host_stats) {
+  if (!b) return bfail(FSB_ERR_INVALID_ARG, "batch handle is NULL");
+  if (n_steps == 0 && !b->pending_init)
+    return bfail(FSB_ERR_INVALID_ARG, "n_steps must be >= 1 (0 only to initialise)");
+  if (b->step + n_steps > 0xFFFFFFFFull)
+    return bfail(FSB_ERR_INVALID_ARG, "step counter would pass 2^32 - 1");
+  int rc = ensure_stats(b, n_steps);
+  if (rc != FSB_OK) return rc;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (b->timing) {
+    BCUDA(cudaEventCreate(&e0));
+    BCUDA(cudaEventCreate(&e1));
+    BCUDA(cudaEventRecord(e0, b->stream));
+  }
+  cudaGraphExec_t exec = nullptr;
+  rc = get_graph(b, n_steps, b->pending_init, &exec);
+  if (rc != FSB_OK) return rc;
+  BCUDA(cudaGraphLaunch(exec, b->stream));
+  if (b->timing) {
+    BCUDA(cudaEventRecord(e1, b->stream));
+    b->ev.emplace_back(e0, e1);
+  }
+  b->pending_init = 0;
+  b->step += n_steps;
+  b->last_n = n_steps;
+  if (host_stats && n_steps) {
+    BCUDA(cudaMemcpyAsync(host_stats, b->d_stats,
+                          sizeof(fsb_step_stats) * static_cast<size_t>(b->n_schools) * n_steps,
+                          cudaMemcpyDeviceToHost, b->stream));
+    BCUDA(cudaStreamSynchronize(b->stream));
+  }
+  return FSB_OK;
+}
+
+int fsb_batch_set_cluster(fsb_batch_handle b, int cluster) {
+  if (!b) return bfail(FSB_ERR_INVALID_ARG, "batch handle is NULL");
+  BCUDA(cudaStreamSynchronize(b->stream));
+  const fsb::BatchLaunch saved = b->L;
+  const int rc = configure_cluster(b, cluster);
+  if (rc != FSB_OK) {
+    b->L = saved;
+    build_order(b, saved.cluster);
+  }
+  return rc;
+}
+
+int fsb_batch_info(fsb_batch_handle b, int* cluster, int* n_clusters, uint32_t* n_big,
+                   uint64_t* step) {
+  if (!b) return bfail(FSB_ERR_INVALID_ARG, "batch handle is NULL");
+  if (cluster) *cluster = b->L.cluster;
+  if (n_clusters) *n_clusters = b->L.n_clusters;
+  if (n_big) *n_big = b->L.n_big;
+  if (step) *step = b->step;
+  return FSB_OK;
+}
+
+int fsb_batch_set_timing(fsb_batch_handle b, int enable) {
+  if (!b) return bfail(FSB_ERR_INVALID_ARG, "batch handle is NULL");
+  b->timing = enable != 0;
+  return FSB_OK;
+}
+
+int fsb_batch_kernel_time(fsb_batch_handle b, double* ms, uint64_t* launches) {
+  if (!b) return bfail(FSB_ERR_INVALID_ARG, "batch handle is NULL");
+  BCUDA(cudaStreamSynchronize(b->stream));
+  for (auto& p : b->ev) {
+    float t = 0.f;
+    BCUDA(cudaEventElapsedTime(&t, p.first, p.second));
+    b->kernel_ms += t;
+    b->launches += 1;
+    cudaEventDestroy(p.first);
+    cudaEventDestroy(p.second);
+  }
+  b->ev.clear();
+  if (ms) *ms = b->kernel_ms;
+  if (launches) *launches = b->launches;
+  return FSB_OK;
+}
+
+int fsb_batch_destroy(fsb_batch_handle b) {
+  if (!b) return FSB_OK;
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  release(b);
+  if (e != cudaSuccess)
+    return bfail(FSB_ERR_CUDA, "sync at batch destroy: %s", cudaGetErrorString(e));
+  return FSB_OK;
+}
+
+int fsb_run_batch(const fsb_config* tmpl, uint32_t n_schools, const uint64_t* offsets,
+                  const uint64_t* seeds, const fsb_state_dev* state, int init,
+                  uint64_t start_step, uint32_t n_steps, fsb_step_stats* stats,
+                  void* cuda_stream) {
+  fsb_batch_handle b = nullptr;
+  int rc = fsb_batch_create(tmpl, n_schools, offsets, seeds, state, init, start_step,
+                            cuda_stream, &b);
+  if (rc != FSB_OK) return rc;
+  rc = fsb_batch_step(b, n_steps, stats);
+  const int rc2 = fsb_batch_destroy(b);
+  return rc != FSB_OK ? rc : rc2;
+}
+
+}  // extern "C"

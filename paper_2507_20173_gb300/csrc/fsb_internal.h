@@ -26,6 +26,14 @@ struct alignas(16) BlockPartial {
   double spare;
 };
 
+// Control block of one resident launch; zeroed before every launch.
+struct alignas(16) ResCtl {
+  unsigned bar_count;     // grid-barrier arrivals (monotonic within a launch)
+  unsigned max_slot[3];   // rotating per-step slots: bits of max |delta|
+  unsigned ekey_slot[3];  // rotating per-step slots: order key of max(prev-cur)
+  unsigned spare;
+};
+
 enum PassKind : int { kSwimOnly = 0, kFused = 1, kSettle = 2 };
 enum AccMode : int { kAccPlain32 = 0, kAccKahan32 = 1, kAccF64 = 2 };
 
@@ -43,6 +51,8 @@ struct StreamLaunch {
   int vec;          // 1 or vector width
   int block;        // threads per block
   int grid;         // blocks
+  int tma;          // 1: bulk-copy ring kernel (fsb_stream_tma.cu)
+  int min_blocks;   // vector kernel: blocks per SM its register budget guarantees
   double pond_half, step, w0, w_min, w_max;
   Ctl* ctl;
   BlockPartial* partials;
@@ -51,8 +61,80 @@ struct StreamLaunch {
 };
 
 cudaError_t launch_stream_pass(const StreamLaunch& L, int pass_kind, cudaStream_t s);
+// Bulk-copy-fed variant (binary32, 16-byte aligned state, block 256 or 512).
+bool stream_tma_supported(const StreamLaunch& L);
+cudaError_t stream_tma_prepare(const StreamLaunch& L);
+int stream_tma_blocks_per_sm(const StreamLaunch& L);
+cudaError_t launch_stream_pass_tma(const StreamLaunch& L, int pass_kind, cudaStream_t s);
 cudaError_t launch_init(const StreamLaunch& L, int weight_mode, cudaStream_t s);
 cudaError_t launch_objective(const StreamLaunch& L, void* cur, cudaStream_t s);
+// Launch description of the resident single-school kernel (binary32 state).
+struct ResidentLaunch {
+  void* x;
+  void* y;
+  void* w;
+  void* pv;
+  uint64_t n;
+  uint64_t slice;   // fish per block
+  uint64_t seed;
+  uint32_t school;
+  double pond_half, step, w0, w_min, w_max;
+  int acc;          // AccMode
+  int fpt;          // fish per thread: 4, 8, 12 or 16
+  int block;        // threads per block (<= resident_max_block(fpt))
+  int grid;         // blocks, all co-resident (cooperative launch)
+  uint64_t base_step;
+  uint32_t n_steps;
+  Ctl* ctl;
+  ResCtl* rctl;
+  double* sums;     // n_steps * grid * 3 barycentre partials
+  fsb_step_stats* ring;
+  unsigned long long timeout_ns;
+  int inject_cta;   // test hook: this block skips one barrier arrival (-1 none)
+  uint32_t inject_step;
+};
+
+cudaError_t launch_resident(const ResidentLaunch& L, cudaStream_t s);
+int resident_max_block(int fpt);
+int resident_blocks_per_sm(int fpt, int acc, int block);
+size_t resident_smem_bytes(int fpt, int block);
+
+// Work-list counters of one batch launch; zeroed before every launch.
+struct alignas(16) BatchCtl {
+  unsigned next_big;    // next index into the whole-cluster queue
+  unsigned next_small;  // next index into the per-block queue
+  unsigned spare[2];
+};
+
+// Launch description of the batched (many schools) kernel, binary32 state.
+struct BatchLaunch {
+  void* x;
+  void* y;
+  void* w;
+  void* pv;
+  const unsigned long long* offsets;  // device, n_schools + 1
+  const unsigned long long* seeds;    // device, n_schools
+  const uint32_t* order;              // device, whole-cluster queue then per-block queue
+  uint32_t n_big;
+  uint32_t n_schools;
+  double pond_half, step, w0, w_min, w_max;
+  int acc;
+  int init;
+  int weight_mode;
+  const unsigned long long* base_step;  // device: step counter at the start of the launch
+  uint32_t n_steps;
+  BatchCtl* bctl;
+  fsb_step_stats* stats;              // device, n_schools * n_steps
+  int cluster;                        // blocks per cluster: 1, 2, 4, 8
+  int n_clusters;                     // resident clusters (persistent grid)
+};
+
+cudaError_t launch_batch(const BatchLaunch& L, cudaStream_t s);
+int batch_max_clusters(int cluster, int acc);
+uint64_t batch_block_capacity();
+int batch_threads();
+cudaError_t launch_bump_step(unsigned long long* base_step, uint32_t n, cudaStream_t s);
+
 // Record `msg` as the calling thread's fsb_last_error() detail; returns status.
 int record_error(int status, const char* msg);
 // Occupancy-derived blocks per SM for the fused pass of this configuration.

@@ -1,0 +1,291 @@
+// fsb_stream_tma.cu -- the streaming pass fed by bulk asynchronous copies.
+//
+// Same pass semantics as fsb_stream.cu (binary32 state, vectorised), but the
+// loads are decoupled from the per-fish arithmetic: each block owns a ring of
+// STAGES shared-memory tiles, and one elected thread keeps STAGES tiles of
+// (x, y, w, prevObjective) in flight with cp.async.bulk copies that complete
+// on an mbarrier per stage.  The block's threads wait on the stage's mbarrier,
+// take their four fish of each array out of shared memory (one 16-byte load
+// per array), release the stage (the elected thread immediately refills it
+// with the tile STAGES ahead), run the per-fish step and store the results
+// straight to HBM with 16-byte stores.  With 96-192 KB of copies in flight per
+// SM the HBM latency is covered without needing many resident warps, which
+// the register-heavy per-fish body (Philox, two square roots, a division)
+// does not allow.
+//
+// Every wait on an mbarrier is bounded by a %globaltimer deadline; a block
+// that gives up latches FSB_ERR_TIMEOUT, waits (bounded) for the copies it
+// still has in flight so none lands in freed shared memory, and leaves.
+// Whole tiles go through the copy ring; the last n % TILE fish are handled
+// with plain loads by one block.
+#include <cstdint>
+
+#include "fsb_stream_common.cuh"
+
+namespace fsb {
+namespace {
+
+constexpr unsigned long long kTmaWaitNs = 1000000000ull;  // 1 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
+                                         unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n"
+      " .reg .pred p;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for phase `parity` of *bar.  Returns false (status latched)
+// when the deadline passes or another block has already failed.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity,
+                                                  Ctl* ctl) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (unsigned spins = 0;; ++spins) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((spins & 63u) == 63u) {
+      if (ld_relaxed_gpu(&ctl->status) != 0) return false;
+      if (global_ns() - t0 > kTmaWaitNs) {
+        if (atomicCAS(&ctl->status, 0, static_cast<int>(FSB_ERR_TIMEOUT)) == 0)
+          atomicExch(&ctl->timeout_site, 0x7A000000u | blockIdx.x);
+        return false;
+      }
+    }
+  }
+}
+
+template <int THREADS, int STAGES>
+struct TmaRing {
+  float4 buf[STAGES][4][THREADS];   // per stage: x, y, w, prevObjective tiles
+  unsigned long long full[STAGES];  // one mbarrier per stage
+};
+
+template <int THREADS, int STAGES, int PASS, int ACC>
+__global__ void __launch_bounds__(THREADS) stream_pass_tma_kernel(StreamArgs<float> a) {
+  using B = uint32_t;
+  using Acc = SumAcc<ACC>;
+  using Ring = TmaRing<THREADS, STAGES>;
+  constexpr int kTile = THREADS * 4;
+  constexpr unsigned kTileBytes = kTile * sizeof(float);
+  constexpr int kArrays = PASS == kSwimOnly ? 2 : 4;
+
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  Ring& R = *reinterpret_cast<Ring*>(smem_raw);
+
+  uint32_t j;
+  uint64_t base;
+  if (!pass_prologue<PASS>(a.ctl, a.ctl, a.ring_cap, j, base)) return;
+  float M = 0.f;
+  if (PASS != kSwimOnly) M = static_cast<float>(a.ring[j - 1].max_abs_delta);
+  const uint32_t t = static_cast<uint32_t>(base + j + 1);
+
+  const uint64_t n_tiles = a.n / kTile;
+  const uint64_t my_tiles =
+      n_tiles > blockIdx.x ? (n_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int s = 0; s < STAGES; ++s) mbar_init(&R.full[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  float* const src[4] = {a.x, a.y, a.w, a.pv};
+  auto issue = [&](uint64_t k) {  // elected thread only
+    const int s = static_cast<int>(k % STAGES);
+    const uint64_t off = (blockIdx.x + k * gridDim.x) * static_cast<uint64_t>(kTile);
+    mbar_expect_tx(&R.full[s], kArrays * kTileBytes);
+#pragma unroll
+    for (int q = 0; q < kArrays; ++q) bulk_g2s(R.buf[s][q], src[q] + off, kTileBytes, &R.full[s]);
+  };
+  if (threadIdx.x == 0)
+    for (uint64_t k = 0; k < my_tiles && k < static_cast<uint64_t>(STAGES); ++k) issue(k);
+
+  Acc acc;
+  B maxb = 0, ekey = 0;
+  uint64_t k = 0;
+  bool ok = true;
+  for (; k < my_tiles; ++k) {
+    const int s = static_cast<int>(k % STAGES);
+    const unsigned parity = static_cast<unsigned>((k / STAGES) & 1);
+    bool mine = mbar_wait_bounded(&R.full[s], parity, a.ctl);
+    float4 v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (q < kArrays) v[q] = R.buf[s][q][threadIdx.x];
+    // every thread has its data (or the block gives up together): release
+    // the stage and refill it with the tile STAGES ahead
+    ok = __syncthreads_and(mine) != 0;
+    if (!ok) break;
+    if (threadIdx.x == 0 && k + STAGES < my_tiles) issue(k + STAGES);
+
+    const uint64_t tile = blockIdx.x + k * gridDim.x;
+    const uint64_t g = tile * THREADS + threadIdx.x;  // float4 index
+    float x[4] = {v[0].x, v[0].y, v[0].z, v[0].w};
+    float y[4] = {v[1].x, v[1].y, v[1].z, v[1].w};
+    float w[4], pv[4];
+    if (PASS != kSwimOnly) {
+      w[0] = v[2].x; w[1] = v[2].y; w[2] = v[2].z; w[3] = v[2].w;
+      pv[0] = v[3].x; pv[1] = v[3].y; pv[2] = v[3].z; pv[3] = v[3].w;
+    }
+    fish_pass4<float, PASS>(x, y, w, pv, g * 4, M, t, a.key, a.school, a.ph, acc, maxb, ekey);
+    if (PASS != kSettle) {
+      reinterpret_cast<float4*>(a.x)[g] = make_float4(x[0], x[1], x[2], x[3]);
+      reinterpret_cast<float4*>(a.y)[g] = make_float4(y[0], y[1], y[2], y[3]);
+      reinterpret_cast<float4*>(a.pv)[g] = make_float4(pv[0], pv[1], pv[2], pv[3]);
+    }
+    if (PASS != kSwimOnly)
+      reinterpret_cast<float4*>(a.w)[g] = make_float4(w[0], w[1], w[2], w[3]);
+  }
+  if (!ok) {
+    // leave only after the copies still in flight have landed (bounded)
+    if (threadIdx.x == 0) {
+      for (uint64_t q = k; q < my_tiles && q < k + STAGES; ++q) {
+        const int s = static_cast<int>(q % STAGES);
+        const unsigned long long t0 = global_ns();
+        while (!mbar_try_wait(&R.full[s], static_cast<unsigned>((q / STAGES) & 1)) &&
+               global_ns() - t0 < kTmaWaitNs) {
+        }
+      }
+    }
+    __syncthreads();
+    return;
+  }
+
+  // ragged tail: the last n % TILE fish, plain loads, one block
+  if (blockIdx.x == n_tiles % gridDim.x) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint64_t i = n_tiles * kTile + threadIdx.x + static_cast<uint64_t>(q) * THREADS;
+      if (i < a.n) {
+        float x = a.x[i], y = a.y[i], w = 0.f, pv = 0.f;
+        if (PASS != kSwimOnly) {
+          w = a.w[i];
+          pv = a.pv[i];
+        }
+        fish_pass<float, PASS>(x, y, w, pv, i, M, t, a.key, a.school, a.ph, acc, maxb, ekey);
+        if (PASS != kSettle) {
+          a.x[i] = x;
+          a.y[i] = y;
+          a.pv[i] = pv;
+        }
+        if (PASS != kSwimOnly) a.w[i] = w;
+      }
+    }
+  }
+
+  pass_epilogue<float, PASS, ACC, THREADS>(a, acc, maxb, ekey, j, base);
+}
+
+template <int THREADS, int STAGES, int PASS>
+const void* pick_acc(int acc) {
+  switch (acc) {
+    case kAccPlain32:
+      return reinterpret_cast<const void*>(&stream_pass_tma_kernel<THREADS, STAGES, PASS, kAccPlain32>);
+    case kAccKahan32:
+      return reinterpret_cast<const void*>(&stream_pass_tma_kernel<THREADS, STAGES, PASS, kAccKahan32>);
+    case kAccF64:
+      return reinterpret_cast<const void*>(&stream_pass_tma_kernel<THREADS, STAGES, PASS, kAccF64>);
+    default:
+      return nullptr;
+  }
+}
+
+template <int THREADS, int STAGES>
+const void* pick_pass(int pass, int acc) {
+  switch (pass) {
+    case kSwimOnly: return pick_acc<THREADS, STAGES, kSwimOnly>(acc);
+    case kFused: return pick_acc<THREADS, STAGES, kFused>(acc);
+    case kSettle: return pick_acc<THREADS, STAGES, kSettle>(acc);
+    default: return nullptr;
+  }
+}
+
+constexpr int kStages = 4;
+
+const void* pick(const StreamLaunch& L, int pass, size_t* smem) {
+  if (L.real_is_double || L.vec != 4) return nullptr;
+  switch (L.block) {
+    case 256:
+      *smem = sizeof(TmaRing<256, kStages>);
+      return pick_pass<256, kStages>(pass, L.acc);
+    case 512:
+      *smem = sizeof(TmaRing<512, kStages>);
+      return pick_pass<512, kStages>(pass, L.acc);
+    default:
+      return nullptr;
+  }
+}
+
+}  // namespace
+
+bool stream_tma_supported(const StreamLaunch& L) {
+  size_t smem = 0;
+  return pick(L, kFused, &smem) != nullptr;
+}
+
+cudaError_t stream_tma_prepare(const StreamLaunch& L) {
+  for (int pass = kSwimOnly; pass <= kSettle; ++pass) {
+    size_t smem = 0;
+    const void* fn = pick(L, pass, &smem);
+    if (!fn) return cudaErrorInvalidValue;
+    cudaError_t e =
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+int stream_tma_blocks_per_sm(const StreamLaunch& L) {
+  size_t smem = 0;
+  const void* fn = pick(L, kFused, &smem);
+  if (!fn) return 0;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, L.block, smem) != cudaSuccess) return 0;
+  return nb;
+}
+
+cudaError_t launch_stream_pass_tma(const StreamLaunch& L, int pass_kind, cudaStream_t s) {
+  size_t smem = 0;
+  const void* fn = pick(L, pass_kind, &smem);
+  if (!fn || L.grid <= 0) return cudaErrorInvalidValue;
+  StreamArgs<float> a = make_stream_args<float>(L);
+  void* args[] = {&a};
+  return cudaLaunchKernel(fn, dim3(L.grid), dim3(L.block), args, smem, s);
+}
+
+}  // namespace fsb

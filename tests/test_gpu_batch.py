@@ -1,0 +1,175 @@
+"""GPU parity of the batched path (many schools of uneven size in one
+persistent launch) against the CPU oracle, school by school."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2507_20173_gb300 as fsb
+from fsb_testutil import assert_state_equal, assert_stats_match
+from paper_2507_20173_gb300 import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+EDGE_SIZES = [1, 2, 31, 257, 512, 4097, 8191, 8192, 8193, 12000, 20000, 40000, 65536, 3, 700]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2507_20173_gb300 import build
+    build.build()
+    fsb.lib()
+
+
+def make_state(total):
+    ts = [torch.zeros(int(total), dtype=torch.float32, device="cuda") for _ in range(4)]
+    return ts, fsb.FsbStateDev(*(t.data_ptr() for t in ts))
+
+
+def read_state(ts):
+    x, y, w, pv = (t.cpu().numpy() for t in ts)
+    cur = None
+    return {"x": x, "y": y, "w": w, "prev": pv}
+
+
+def oracle_school(tmpl, n, seed, school_id, steps, **kw):
+    cfg = oracle.Config(n_fish=int(n), seed=int(seed), school_id=int(school_id),
+                        init_weight_mode=tmpl.init_weight_mode, pond_half=tmpl.pond_half,
+                        step=tmpl.step, w0=tmpl.w0, w_min=tmpl.w_min, w_max=tmpl.w_max)
+    school = oracle.init(cfg)
+    stats = oracle.run(cfg, school, 0, steps) if steps else None
+    return school, stats
+
+
+def check_batch(tmpl, offsets, seeds, got, stats, steps, precision):
+    for k in range(seeds.size):
+        lo, hi = int(offsets[k]), int(offsets[k + 1])
+        ref, ref_stats = oracle_school(tmpl, hi - lo, seeds[k], k, steps)
+        sub = {"x": got["x"][lo:hi], "y": got["y"][lo:hi], "w": got["w"][lo:hi],
+               "prev": got["prev"][lo:hi],
+               "cur": np.sqrt(got["x"][lo:hi] * got["x"][lo:hi] +
+                              got["y"][lo:hi] * got["y"][lo:hi])}
+        ref_cmp = ref.copy()
+        # currentObjective is derived on the device by fsb_read_state for a
+        # single school; here it is recomputed in binary32 by numpy (each
+        # operation correctly rounded), matching the stored positions
+        assert_state_equal(sub, ref_cmp, "school %d (N=%d)" % (k, hi - lo))
+        if steps:
+            assert_stats_match(stats[k * steps:(k + 1) * steps], ref_stats, precision,
+                               "school %d" % k)
+
+
+@pytest.mark.parametrize("cluster", [2, 4, 8])
+def test_edge_size_batch_every_cluster_size(cluster):
+    sizes = np.array(EDGE_SIZES, dtype=np.uint64)
+    if cluster * 8192 < sizes.max():
+        sizes = np.minimum(sizes, cluster * 8192)
+    offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    seeds = (1000 + np.arange(sizes.size)).astype(np.uint64)
+    tmpl = fsb.fsb_config_init(1, 0, step=2.0, init_weight_mode=1)
+    ts, state = make_state(offsets[-1])
+    b = fsb.fsb_batch_create(tmpl, offsets, seeds, state, init=True)
+    fsb.fsb_batch_set_cluster(b, cluster)
+    info = fsb.fsb_batch_info(b)
+    assert info["cluster"] == cluster and info["n_clusters"] >= 1
+    steps = 6
+    stats = np.zeros(sizes.size * steps, fsb.STATS_DTYPE)
+    fsb.fsb_batch_step(b, steps, stats)
+    fsb.fsb_batch_destroy(b)
+    check_batch(tmpl, offsets, seeds, read_state(ts), stats, steps, tmpl.precision)
+
+
+def test_single_block_clusters_for_small_schools():
+    sizes = np.array([1, 5, 100, 8192, 4000, 333], dtype=np.uint64)
+    offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    seeds = (7 + np.arange(sizes.size)).astype(np.uint64)
+    tmpl = fsb.fsb_config_init(1, 0)
+    ts, state = make_state(offsets[-1])
+    b = fsb.fsb_batch_create(tmpl, offsets, seeds, state, init=True)
+    assert fsb.fsb_batch_info(b)["cluster"] == 1
+    stats = np.zeros(sizes.size * 9, fsb.STATS_DTYPE)
+    fsb.fsb_batch_step(b, 9, stats)
+    fsb.fsb_batch_destroy(b)
+    check_batch(tmpl, offsets, seeds, read_state(ts), stats, 9, tmpl.precision)
+
+
+def test_init_only_and_split_calls():
+    sizes = np.array([300, 9000, 17], dtype=np.uint64)
+    offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    seeds = np.array([5, 6, 2 ** 40 + 3], dtype=np.uint64)
+    tmpl = fsb.fsb_config_init(1, 0)
+    ts, state = make_state(offsets[-1])
+    b = fsb.fsb_batch_create(tmpl, offsets, seeds, state, init=True)
+    fsb.fsb_batch_step(b, 0)
+    torch.cuda.synchronize()
+    check_batch(tmpl, offsets, seeds, read_state(ts), None, 0, tmpl.precision)
+    s1 = np.zeros(sizes.size * 3, fsb.STATS_DTYPE)
+    s2 = np.zeros(sizes.size * 4, fsb.STATS_DTYPE)
+    fsb.fsb_batch_step(b, 3, s1)
+    fsb.fsb_batch_step(b, 4, s2)
+    assert fsb.fsb_batch_info(b)["step"] == 7
+    fsb.fsb_batch_destroy(b)
+    got = read_state(ts)
+    stats = np.concatenate([np.concatenate([s1[k * 3:(k + 1) * 3], s2[k * 4:(k + 1) * 4]])
+                            for k in range(sizes.size)])
+    check_batch(tmpl, offsets, seeds, got, stats, 7, tmpl.precision)
+
+
+def test_batch_school_equals_single_school_run():
+    sizes = np.array([1000, 20000, 4096], dtype=np.uint64)
+    offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    seeds = np.array([11, 12, 13], dtype=np.uint64)
+    tmpl = fsb.fsb_config_init(1, 0)
+    ts, state = make_state(offsets[-1])
+    fsb.fsb_run_batch(tmpl, offsets, seeds, state, 10, init=True)
+    torch.cuda.synchronize()
+    got = read_state(ts)
+    for k in range(3):
+        cfg = fsb.fsb_config_init(int(sizes[k]), int(seeds[k]), school_id=k)
+        s = fsb.School.create(cfg)
+        s.step(10)
+        one = s.read()
+        s.destroy()
+        lo, hi = int(offsets[k]), int(offsets[k + 1])
+        for f in ("x", "y", "w", "prev"):
+            assert np.array_equal(one[f], got[f][lo:hi]), (k, f)
+
+
+@pytest.mark.parametrize("precision", [fsb.FSB_FP32, fsb.FSB_FP64_ACC])
+def test_ragged_ensemble_sample(precision):
+    """A 64-school sample of the log-uniform [256, 65536] ensemble."""
+    wl = workloads.ragged_batch(64, 256, 65536, seed=3)
+    offsets, seeds = wl.offsets(), wl.seeds()
+    tmpl = fsb.fsb_config_init(1, 0, precision=precision)
+    ts, state = make_state(offsets[-1])
+    steps = 8
+    stats = np.zeros(seeds.size * steps, fsb.STATS_DTYPE)
+    fsb.fsb_run_batch(tmpl, offsets, seeds, state, steps, init=True, stats=stats)
+    check_batch(tmpl, offsets, seeds, read_state(ts), stats, steps, precision)
+
+
+def test_batch_argument_errors():
+    tmpl = fsb.fsb_config_init(1, 0)
+    ts, state = make_state(70000)
+    with pytest.raises(fsb.FsbError) as e:
+        fsb.fsb_batch_create(tmpl, np.array([0, 70000], np.uint64), np.array([1], np.uint64),
+                             state, init=True)
+    assert e.value.status == fsb.FSB_ERR_UNSUPPORTED
+    with pytest.raises(fsb.FsbError) as e:
+        fsb.fsb_batch_create(tmpl, np.array([0, 10, 10], np.uint64), np.array([1, 2], np.uint64),
+                             state, init=True)
+    assert e.value.status == fsb.FSB_ERR_INVALID_ARG
+    t64 = fsb.fsb_config_init(1, 0, precision=fsb.FSB_FP64_STATE)
+    with pytest.raises(fsb.FsbError) as e:
+        fsb.fsb_batch_create(t64, np.array([0, 10], np.uint64), np.array([1], np.uint64),
+                             state, init=True)
+    assert e.value.status == fsb.FSB_ERR_UNSUPPORTED
+    b = fsb.fsb_batch_create(tmpl, np.array([0, 10000], np.uint64), np.array([1], np.uint64),
+                             state, init=True)
+    with pytest.raises(fsb.FsbError) as e:
+        fsb.fsb_batch_set_cluster(b, 1)          # 10000 fish do not fit one block
+    assert e.value.status == fsb.FSB_ERR_UNSUPPORTED
+    fsb.fsb_batch_step(b, 2)
+    fsb.fsb_batch_destroy(b)

@@ -15,6 +15,11 @@ from fsb_testutil import (BARY_TOL, assert_state_equal, assert_stats_match, bary
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+def stream_cfg(n, seed, **kw):
+    """Configuration pinned to the streaming path."""
+    return fsb.fsb_config_init(n, seed, path=fsb.FSB_PATH_STREAM, **kw)
+
+
 PRECISIONS = [fsb.FSB_FP32, fsb.FSB_FP32_KAHAN, fsb.FSB_FP64_ACC, fsb.FSB_FP64_STATE]
 
 
@@ -45,7 +50,7 @@ def run_pair(cfg, steps, calls=None):
 @pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("n", [1, 2, 3, 31, 32, 33, 4095, 4096, 4097, 10000])
 def test_init_matches_oracle(n, mode, precision):
-    cfg = fsb.fsb_config_init(n, 0xABCDEF0123 + n, init_weight_mode=mode,
+    cfg = stream_cfg(n, 0xABCDEF0123 + n, init_weight_mode=mode,
                               precision=precision, school_id=n % 7)
     school = fsb.School.create(cfg)
     got = school.read()
@@ -58,7 +63,7 @@ def test_init_matches_oracle(n, mode, precision):
 @pytest.mark.parametrize("precision", PRECISIONS)
 def test_small_school_every_step(precision):
     """N = 10,000, seed 0, T = 100: stats of every step and the final state."""
-    cfg = fsb.fsb_config_init(10_000, 0, precision=precision)
+    cfg = stream_cfg(10_000, 0, precision=precision)
     got, stats, ref, ref_stats = run_pair(cfg, 100)
     assert_state_equal(got, ref, "N=10000 T=100")
     assert got["step"] == 100
@@ -66,7 +71,7 @@ def test_small_school_every_step(precision):
 
 
 def test_small_school_state_after_each_step():
-    cfg = fsb.fsb_config_init(10_000, 0)
+    cfg = stream_cfg(10_000, 0)
     school = fsb.School.create(cfg)
     ocfg = oracle_config(cfg)
     ref = oracle.init(ocfg)
@@ -83,7 +88,7 @@ def test_small_school_state_after_each_step():
 
 @pytest.mark.parametrize("n", [1, 2, 3, 5, 31, 32, 33, 511, 512, 513, 4095, 4096, 4097])
 def test_ragged_sizes(n):
-    cfg = fsb.fsb_config_init(n, 99 + n, school_id=3, step=2.5)
+    cfg = stream_cfg(n, 99 + n, school_id=3, step=2.5)
     got, stats, ref, ref_stats = run_pair(cfg, 9)
     assert_state_equal(got, ref, "N=%d" % n)
     assert_stats_match(stats, ref_stats, cfg.precision, "N=%d" % n)
@@ -94,7 +99,7 @@ def test_unaligned_buffers_take_the_scalar_path(precision):
     """Buffers offset by one element are not 16-byte aligned, so the library
     runs its scalar kernel; results are the same."""
     n, steps = 1003, 12
-    cfg = fsb.fsb_config_init(n, 5, precision=precision)
+    cfg = stream_cfg(n, 5, precision=precision)
     dt = torch.float64 if precision == fsb.FSB_FP64_STATE else torch.float32
     big = [torch.empty(n + 1, dtype=dt, device="cuda") for _ in range(4)]
     bufs = fsb.FsbStateDev(*(b[1:].data_ptr() for b in big))
@@ -112,8 +117,41 @@ def test_unaligned_buffers_take_the_scalar_path(precision):
     assert_stats_match(stats, ref_stats, precision, "unaligned")
 
 
+VARIANTS = [(1, 256), (1, 512), (2, 256), (2, 512)]
+
+
+@pytest.mark.parametrize("kernel,block", VARIANTS)
+@pytest.mark.parametrize("n", [1, 33, 2047, 2048, 2049, 4096 * 3 + 5, 1_000_003])
+def test_stream_kernel_variants(kernel, block, n):
+    """Every launch shape of the streaming pass (vector loads or bulk-copy
+    ring, 256 or 512 threads): whole tiles, a ragged tail, fewer tiles than
+    blocks."""
+    cfg = stream_cfg(n, 1234 + n, step=1.5, init_weight_mode=1)
+    school = fsb.School.create(cfg)
+    fsb.fsb_set_tuning(school.handle, stream_kernel=kernel, stream_block=block)
+    t = fsb.fsb_get_tuning(school.handle)
+    assert (t["stream_kernel"], t["stream_block"]) == (kernel, block)
+    stats = school.step(7, stats=True)
+    got = school.read()
+    school.destroy()
+    ocfg = oracle_config(cfg)
+    ref = oracle.init(ocfg)
+    ref_stats = oracle.run(ocfg, ref, 0, 7)
+    assert_state_equal(got, ref, "variant %d/%d N=%d" % (kernel, block, n))
+    assert_stats_match(stats, ref_stats, cfg.precision, "variant %d/%d N=%d" % (kernel, block, n))
+
+
+def test_bulk_copy_kernel_needs_binary32_aligned_state():
+    s = fsb.School.create(stream_cfg(1000, 1, precision=fsb.FSB_FP64_STATE))
+    with pytest.raises(fsb.FsbError) as e:
+        fsb.fsb_set_tuning(s.handle, stream_kernel=2)
+    assert e.value.status == fsb.FSB_ERR_INVALID_ARG
+    assert fsb.fsb_get_tuning(s.handle)["stream_kernel"] == 1
+    s.destroy()
+
+
 def test_split_calls_equal_one_call():
-    cfg = fsb.fsb_config_init(3001, 17)
+    cfg = stream_cfg(3001, 17)
     got, stats, ref, ref_stats = run_pair(cfg, 10, calls=[3, 1, 6])
     assert_state_equal(got, ref, "split")
     assert_stats_match(stats, ref_stats, cfg.precision, "split")
@@ -122,14 +160,14 @@ def test_split_calls_equal_one_call():
 def test_long_call_uses_chunked_graphs():
     """More steps than one captured graph holds (2048): chunk graphs plus
     direct launches must give the same trajectory."""
-    cfg = fsb.fsb_config_init(67, 23, step=1.0)
+    cfg = stream_cfg(67, 23, step=1.0)
     got, stats, ref, ref_stats = run_pair(cfg, 2048 + 700)
     assert_state_equal(got, ref, "long call")
     assert_stats_match(stats, ref_stats, cfg.precision, "long call")
 
 
 def test_library_owned_buffers_and_side_stream():
-    cfg = fsb.fsb_config_init(2500, 8)
+    cfg = stream_cfg(2500, 8)
     s = torch.cuda.Stream()
     h = fsb.fsb_create(cfg, None, None, 0, s.cuda_stream)
     stats = np.zeros(15, fsb.STATS_DTYPE)
@@ -146,7 +184,7 @@ def test_library_owned_buffers_and_side_stream():
 
 @pytest.mark.parametrize("precision", [fsb.FSB_FP32_KAHAN, fsb.FSB_FP64_STATE])
 def test_resume_from_host_checkpoint(precision):
-    cfg = fsb.fsb_config_init(4321, 77, precision=precision, init_weight_mode=1)
+    cfg = stream_cfg(4321, 77, precision=precision, init_weight_mode=1)
     a = fsb.School.create(cfg)
     a.step(13)
     mid = a.read()
@@ -164,7 +202,7 @@ def test_resume_from_host_checkpoint(precision):
 
 
 def test_runs_are_deterministic():
-    cfg = fsb.fsb_config_init(50_000, 4)
+    cfg = stream_cfg(50_000, 4)
     outs = []
     for _ in range(2):
         s = fsb.School.create(cfg)
@@ -177,7 +215,7 @@ def test_runs_are_deterministic():
 
 
 def test_kernel_timing_counts_fused_launches():
-    cfg = fsb.fsb_config_init(100_000, 1)
+    cfg = stream_cfg(100_000, 1)
     s = fsb.School.create(cfg)
     fsb.fsb_set_kernel_timing(s.handle, True)
     s.step(9)
@@ -188,19 +226,19 @@ def test_kernel_timing_counts_fused_launches():
 
 
 def test_argument_errors():
-    cfg = fsb.fsb_config_init(10, 1)
+    cfg = stream_cfg(10, 1)
     s = fsb.School.create(cfg)
     with pytest.raises(fsb.FsbError) as e:
         fsb.fsb_step(s.handle, 0)
     assert e.value.status == fsb.FSB_ERR_INVALID_ARG
     s.destroy()
     with pytest.raises(fsb.FsbError) as e:
-        fsb.fsb_create(fsb.fsb_config_init(10, 1), None, None, 0xFFFFFFFF, None)
+        fsb.fsb_create(stream_cfg(10, 1), None, None, 0xFFFFFFFF, None)
     assert e.value.status == fsb.FSB_ERR_INVALID_ARG
 
 
 def test_still_school_never_eats():
-    cfg = fsb.fsb_config_init(777, 2, step=0.0, init_weight_mode=1)
+    cfg = stream_cfg(777, 2, step=0.0, init_weight_mode=1)
     got, stats, ref, ref_stats = run_pair(cfg, 5)
     assert np.all(stats["max_abs_delta"] == 0.0)
     assert_state_equal(got, ref, "still")
@@ -216,7 +254,7 @@ def test_full_size_stream_school_sampled():
     free, _ = torch.cuda.mem_get_info()
     if free < 12 * (1 << 30):
         pytest.skip("needs ~12 GB of free device memory")
-    cfg = fsb.fsb_config_init(n, seed)
+    cfg = stream_cfg(n, seed)
     s = fsb.School.create(cfg)
     start = s.read()
     stats = s.step(steps, stats=True)
