@@ -243,9 +243,12 @@ int fsb_batch_step(fsb_batch_handle b, uint32_t n_steps, fsb_step_stats* stats);
  * Too small for the largest school -> FSB_ERR_UNSUPPORTED.  Synchronises. */
 int fsb_batch_set_cluster(fsb_batch_handle b, int cluster);
 
-/* Launch shape and step counter of a batch (any pointer may be NULL). */
-int fsb_batch_info(fsb_batch_handle b, int* cluster, int* n_clusters, uint32_t* n_big,
-                   uint64_t* step);
+/* Launch shape and step counter of a batch (any pointer may be NULL):
+ * blocks per cluster, resident clusters, single-block filler blocks that run
+ * beside the clusters on the SMs they leave idle, schools in the
+ * whole-cluster queue, step counter. */
+int fsb_batch_info(fsb_batch_handle b, int* cluster, int* n_clusters, int* filler_blocks,
+                   uint32_t* n_big, uint64_t* step);
 
 /* Device time of the batch launches since timing was enabled (CUDA events
  * on the batch's stream around each launch). */
@@ -303,6 +306,27 @@ typedef struct {
 
 int fsb_set_tuning(fsb_handle h, const fsb_tuning* t);
 int fsb_get_tuning(fsb_handle h, fsb_tuning* t);
+
+/* Autotuner (no counterpart in the paper's method; the GPU analogue of its
+ * thread-count / schedule / chunk study, Sec. 2.2.2).  Measures every launch
+ * shape of both single-school paths for a school of cfg->n_fish fish in
+ * cfg->precision, on a scratch school (library-owned state, freed before
+ * return), n_steps timed steps each, and reports the fastest: *best_path
+ * (FSB_PATH_STREAM or FSB_PATH_RESIDENT -- this fixes the cutoff between
+ * the two kernels for that size), *best_tuning (apply with fsb_set_tuning
+ * to a handle created with that path), its throughput and how many shapes
+ * ran.  Synchronous; needs room for one more school of that size. */
+int fsb_autotune(const fsb_config* cfg, uint32_t n_steps, int* best_path,
+                 fsb_tuning* best_tuning, double* best_fish_steps_per_s,
+                 uint32_t* candidates_tried);
+
+/* Batch autotuner: times the batch of fsb_batch_create's arguments with
+ * clusters of 1, 2, 4 and 8 blocks (those that hold the largest school) and
+ * reports the fastest.  OVERWRITES `state` (every school is initialised and
+ * stepped).  Synchronous. */
+int fsb_autotune_batch(const fsb_config* tmpl, uint32_t n_schools, const uint64_t* offsets,
+                       const uint64_t* seeds, const fsb_state_dev* state, uint32_t n_steps,
+                       int* best_cluster, double* best_fish_steps_per_s);
 
 /* Which single-school path a handle runs (fsb_path value), after AUTO is
  * resolved. */

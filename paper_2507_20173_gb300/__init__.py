@@ -43,7 +43,8 @@ EXPORTED = ("fsb_config_init", "fsb_create", "fsb_step", "fsb_read_state",
             "fsb_strerror", "fsb_last_error", "fsb_step_static", "fsb_set_fault_injection",
             "fsb_set_tuning", "fsb_get_tuning", "fsb_batch_create", "fsb_batch_step",
             "fsb_batch_set_cluster", "fsb_batch_info", "fsb_batch_set_timing",
-            "fsb_batch_kernel_time", "fsb_batch_destroy")
+            "fsb_batch_kernel_time", "fsb_batch_destroy", "fsb_autotune",
+            "fsb_autotune_batch")
 
 
 class FsbError(RuntimeError):
@@ -121,11 +122,15 @@ def lib() -> ctypes.CDLL:
                              ctypes.POINTER(P)],
         "fsb_batch_step": [P, u32, P],
         "fsb_batch_set_cluster": [P, i32],
-        "fsb_batch_info": [P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(u32),
-                           ctypes.POINTER(u64)],
+        "fsb_batch_info": [P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                           ctypes.POINTER(u32), ctypes.POINTER(u64)],
         "fsb_batch_set_timing": [P, i32],
         "fsb_batch_kernel_time": [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u64)],
         "fsb_batch_destroy": [P],
+        "fsb_autotune": [cfgp, u32, ctypes.POINTER(i32), ctypes.POINTER(FsbTuning),
+                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u32)],
+        "fsb_autotune_batch": [cfgp, u32, P, P, ctypes.POINTER(FsbStateDev), u32,
+                               ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double)],
         "fsb_get_tuning": [P, ctypes.POINTER(FsbTuning)],
         "fsb_strerror": [i32],
         "fsb_step_static": [cfgp, ctypes.POINTER(FsbStateDev), u64, u32, P, P],
@@ -268,10 +273,13 @@ def fsb_batch_set_cluster(handle: int, cluster: int) -> None:
 
 
 def fsb_batch_info(handle: int) -> dict:
-    c, nc, nb, st = ctypes.c_int(), ctypes.c_int(), ctypes.c_uint32(), ctypes.c_uint64()
+    c, nc, fb = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    nb, st = ctypes.c_uint32(), ctypes.c_uint64()
     _check(lib().fsb_batch_info(ctypes.c_void_p(handle), ctypes.byref(c), ctypes.byref(nc),
-                                ctypes.byref(nb), ctypes.byref(st)), "fsb_batch_info")
-    return {"cluster": c.value, "n_clusters": nc.value, "n_big": nb.value, "step": st.value}
+                                ctypes.byref(fb), ctypes.byref(nb), ctypes.byref(st)),
+           "fsb_batch_info")
+    return {"cluster": c.value, "n_clusters": nc.value, "filler_blocks": fb.value,
+            "n_big": nb.value, "step": st.value}
 
 
 def fsb_batch_set_timing(handle: int, enable: bool) -> None:
@@ -288,6 +296,28 @@ def fsb_batch_kernel_time(handle: int) -> tuple[float, int]:
 
 def fsb_batch_destroy(handle: int) -> None:
     _check(lib().fsb_batch_destroy(ctypes.c_void_p(handle)), "fsb_batch_destroy")
+
+
+def fsb_autotune(cfg: FsbConfig, n_steps: int) -> dict:
+    path, t = ctypes.c_int(), FsbTuning()
+    rate, tried = ctypes.c_double(), ctypes.c_uint32()
+    _check(lib().fsb_autotune(ctypes.byref(cfg), n_steps, ctypes.byref(path), ctypes.byref(t),
+                              ctypes.byref(rate), ctypes.byref(tried)), "fsb_autotune")
+    return {"path": path.value, "tuning": t.as_dict(), "fish_steps_per_s": rate.value,
+            "candidates": tried.value}
+
+
+def fsb_autotune_batch(tmpl: FsbConfig, offsets: np.ndarray, seeds: np.ndarray,
+                       state: FsbStateDev, n_steps: int) -> dict:
+    offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+    seeds = np.ascontiguousarray(seeds, dtype=np.uint64)
+    c, rate = ctypes.c_int(), ctypes.c_double()
+    _check(lib().fsb_autotune_batch(ctypes.byref(tmpl), seeds.size,
+                                    offsets.ctypes.data_as(ctypes.c_void_p),
+                                    seeds.ctypes.data_as(ctypes.c_void_p), ctypes.byref(state),
+                                    n_steps, ctypes.byref(c), ctypes.byref(rate)),
+           "fsb_autotune_batch")
+    return {"cluster": c.value, "fish_steps_per_s": rate.value}
 
 
 def fsb_set_kernel_timing(handle: int, enable: bool) -> None:

@@ -18,6 +18,11 @@
 // single-school path bit for bit.  Waits are hardware barriers on uniform
 // control flow (every decision a cluster takes is broadcast from rank 0),
 // so no block can be left waiting for another.
+//
+// Clusters of eight blocks cannot tile every SM (they must sit inside one
+// GPC), so a second, single-block launch of the same kernel runs beside the
+// cluster launch on the SMs left over; it only pops from the per-block
+// queue, which both launches share.
 #include <cstdint>
 
 #include <cooperative_groups.h>
@@ -50,10 +55,13 @@ struct BatchArgs {
   fsb_step_stats* stats;                           // n_schools * n_steps, school-major
 };
 
-// Per-block partial of one step exchanged across the cluster.
+// Per-block partial of one step exchanged across the cluster (the sums in
+// the accumulation mode's partial type, so the exchange stays in binary32
+// in the binary32 modes).
+template <typename Part>
 struct ClusterPartial {
   uint32_t max_bits, e_key;
-  double sum_w, sum_wx, sum_wy;
+  Part sum_w, sum_wx, sum_wy;
 };
 
 constexpr int kBatchThreads = 512;
@@ -62,25 +70,25 @@ constexpr int kMaxCluster = 8;
 
 template <int ACC>
 struct BlockReduce {
-  using Sum = typename SumAcc<ACC>::Sum;
+  using Part = typename SumAcc<ACC>::Part;
   uint32_t s_max[32], s_ekey[32];
-  Sum s_w[32], s_x[32], s_y[32];
+  Part s_w[32], s_x[32], s_y[32];
 };
 
 // Block reduction of (max, key, three sums); the result is valid in thread 0.
 template <int ACC>
 __device__ __forceinline__ void block_reduce(BlockReduce<ACC>& R, uint32_t& m, uint32_t& e,
-                                             typename SumAcc<ACC>::Sum& sw,
-                                             typename SumAcc<ACC>::Sum& sx,
-                                             typename SumAcc<ACC>::Sum& sy) {
-  using Sum = typename SumAcc<ACC>::Sum;
+                                             typename SumAcc<ACC>::Part& sw,
+                                             typename SumAcc<ACC>::Part& sx,
+                                             typename SumAcc<ACC>::Part& sy) {
+  using Part = typename SumAcc<ACC>::Part;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int nw = kBatchThreads / 32;
   m = warp_max(m);
   e = warp_max(e);
-  sw = warp_sum(sw);
-  sx = warp_sum(sx);
-  sy = warp_sum(sy);
+  sw = warp_merge(sw);
+  sx = warp_merge(sx);
+  sy = warp_merge(sy);
   __syncthreads();  // previous use of R is finished
   if (lane == 0) {
     R.s_max[warp] = m;
@@ -93,14 +101,14 @@ __device__ __forceinline__ void block_reduce(BlockReduce<ACC>& R, uint32_t& m, u
   if (warp == 0) {
     m = lane < nw ? R.s_max[lane] : 0u;
     e = lane < nw ? R.s_ekey[lane] : 0u;
-    sw = lane < nw ? R.s_w[lane] : Sum(0);
-    sx = lane < nw ? R.s_x[lane] : Sum(0);
-    sy = lane < nw ? R.s_y[lane] : Sum(0);
+    sw = lane < nw ? R.s_w[lane] : part_zero<Part>();
+    sx = lane < nw ? R.s_x[lane] : part_zero<Part>();
+    sy = lane < nw ? R.s_y[lane] : part_zero<Part>();
     m = warp_max(m);
     e = warp_max(e);
-    sw = warp_sum(sw);
-    sx = warp_sum(sx);
-    sy = warp_sum(sy);
+    sw = warp_merge(sw);
+    sx = warp_merge(sx);
+    sy = warp_merge(sy);
   }
 }
 
@@ -110,10 +118,11 @@ __device__ __forceinline__ void block_reduce(BlockReduce<ACC>& R, uint32_t& m, u
 template <int ACC>
 __device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int rank, int nb,
                                            BlockReduce<ACC>& R,
-                                           ClusterPartial (*xchg)[kMaxCluster], uint32_t* s_M,
+                                           ClusterPartial<typename SumAcc<ACC>::Part> (*xchg)[kMaxCluster],
+                                           uint32_t* s_M,
                                            uint32_t* s_E, float (*spv)[kBatchThreads]) {
   using Acc = SumAcc<ACC>;
-  using Sum = typename Acc::Sum;
+  using Part = typename Acc::Part;
   const int tid = threadIdx.x;
   const uint64_t s_lo = a.offsets[k];
   // in-school fish indices fit 32 bits (schools hold at most C * 8192 fish)
@@ -151,7 +160,7 @@ __device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int r
   // Each step: swim -> local maxima (+ the previous step's sums) -> one
   // exchange -> eat.  The exchange of step u carries the sums of step u - 1;
   // one extra exchange after the last step carries the last sums.
-  Sum sw = Sum(0), sx = Sum(0), sy = Sum(0);
+  Part sw = part_zero<Part>(), sx = part_zero<Part>(), sy = part_zero<Part>();
   for (uint32_t u = 1; u <= a.n_steps + 1; ++u) {
     const bool swim_step = u <= a.n_steps;
     uint32_t mb = 0, ek = 0;
@@ -180,45 +189,45 @@ __device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int r
         *s_E = ek;
         if (u > 1) {
           fsb_step_stats* st = a.stats + static_cast<uint64_t>(k) * a.n_steps + (u - 2);
-          st->sum_w = static_cast<double>(sw);
-          st->sum_wx = static_cast<double>(sx);
-          st->sum_wy = static_cast<double>(sy);
+          st->sum_w = to_double(sw);
+          st->sum_wx = to_double(sx);
+          st->sum_wy = to_double(sy);
         }
       }
       __syncthreads();
     } else {
       // every block writes its partial into rank 0's slot for this parity
       if (tid == 0) {
-        ClusterPartial* dst = cluster.map_shared_rank(&xchg[u & 1][rank], 0);
-        ClusterPartial p;
+        ClusterPartial<Part>* dst = cluster.map_shared_rank(&xchg[u & 1][rank], 0);
+        ClusterPartial<Part> p;
         p.max_bits = mb;
         p.e_key = ek;
-        p.sum_w = static_cast<double>(sw);
-        p.sum_wx = static_cast<double>(sx);
-        p.sum_wy = static_cast<double>(sy);
+        p.sum_w = sw;
+        p.sum_wx = sx;
+        p.sum_wy = sy;
         *dst = p;
       }
       cluster.sync();
       // fold the nb partials in rank order (identical in every block)
       if (tid == 0) {
-        const ClusterPartial* src = cluster.map_shared_rank(&xchg[u & 1][0], 0);
+        const ClusterPartial<Part>* src = cluster.map_shared_rank(&xchg[u & 1][0], 0);
         uint32_t m = 0, e = 0;
-        Sum fw = Sum(0), fx = Sum(0), fy = Sum(0);
+        Part fw = part_zero<Part>(), fx = part_zero<Part>(), fy = part_zero<Part>();
         for (int r = 0; r < nb; ++r) {
-          const ClusterPartial p = src[r];
+          const ClusterPartial<Part> p = src[r];
           m = p.max_bits > m ? p.max_bits : m;
           e = p.e_key > e ? p.e_key : e;
-          fw = sum2(fw, Sum(p.sum_w));
-          fx = sum2(fx, Sum(p.sum_wx));
-          fy = sum2(fy, Sum(p.sum_wy));
+          fw = merge(fw, p.sum_w);
+          fx = merge(fx, p.sum_wx);
+          fy = merge(fy, p.sum_wy);
         }
         *s_M = m;
         *s_E = e;
         if (rank == 0 && u > 1) {
           fsb_step_stats* st = a.stats + static_cast<uint64_t>(k) * a.n_steps + (u - 2);
-          st->sum_w = static_cast<double>(fw);
-          st->sum_wx = static_cast<double>(fx);
-          st->sum_wy = static_cast<double>(fy);
+          st->sum_w = to_double(fw);
+          st->sum_wx = to_double(fx);
+          st->sum_wy = to_double(fy);
         }
       }
       __syncthreads();
@@ -239,9 +248,9 @@ __device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int r
         acc.add(w[q], x[q], y[q]);
       }
     }
-    sw = Sum(acc.rw());
-    sx = Sum(acc.rx());
-    sy = Sum(acc.ry());
+    sw = acc.pw();
+    sx = acc.px();
+    sy = acc.py();
   }
   if (nb > 1) cluster.sync();  // rank 0's slots are free again for the next school
 
@@ -260,7 +269,7 @@ __device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int r
 template <int CLUSTER, int ACC>
 __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs a) {
   __shared__ BlockReduce<ACC> R;
-  __shared__ ClusterPartial xchg[2][kMaxCluster];
+  __shared__ ClusterPartial<typename SumAcc<ACC>::Part> xchg[2][kMaxCluster];
   __shared__ float spv[kBatchFpt][kBatchThreads];
   __shared__ uint32_t s_M, s_E, s_pick;
   cg::cluster_group cluster = cg::this_cluster();
@@ -354,9 +363,11 @@ int batch_max_clusters(int cluster, int acc) {
   return n;
 }
 
-cudaError_t launch_batch(const BatchLaunch& L, cudaStream_t s) {
+cudaError_t launch_batch(const BatchLaunch& L, cudaStream_t s, cudaStream_t side,
+                         cudaEvent_t fork, cudaEvent_t join) {
   const void* fn = pick(L.cluster, L.acc);
-  if (!fn || L.n_clusters < 1) return cudaErrorInvalidValue;
+  const void* fill = pick(1, L.acc);
+  if (!fn || !fill || L.n_clusters < 1) return cudaErrorInvalidValue;
   BatchArgs a;
   a.x = static_cast<float*>(L.x);
   a.y = static_cast<float*>(L.y);
@@ -381,9 +392,22 @@ cudaError_t launch_batch(const BatchLaunch& L, cudaStream_t s) {
   void* args[] = {&a};
   cudaError_t e = cudaMemsetAsync(L.bctl, 0, sizeof(BatchCtl), s);
   if (e != cudaSuccess) return e;
+  const bool filler = L.filler_blocks > 0 && L.cluster > 1 && side && fork && join;
+  if (filler) {
+    if ((e = cudaEventRecord(fork, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(side, fork, 0)) != cudaSuccess) return e;
+  }
   cudaLaunchAttribute attr[1];
   cudaLaunchConfig_t cfg = make_config(L.cluster, L.n_clusters * L.cluster, s, attr);
-  return cudaLaunchKernelExC(&cfg, fn, args);
+  if ((e = cudaLaunchKernelExC(&cfg, fn, args)) != cudaSuccess) return e;
+  if (filler) {
+    cudaLaunchAttribute attr2[1];
+    cudaLaunchConfig_t cfg2 = make_config(1, L.filler_blocks, side, attr2);
+    if ((e = cudaLaunchKernelExC(&cfg2, fill, args)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(join, side)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(s, join, 0)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace fsb

@@ -48,6 +48,9 @@ struct fsb_batch {
   uint64_t max_school = 0;
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  int sms = 0;
   unsigned long long* d_offsets = nullptr;
   unsigned long long* d_seeds = nullptr;
   uint32_t* d_order = nullptr;
@@ -112,6 +115,12 @@ int configure_cluster(fsb_batch* b, int cluster) {
     return bfail(FSB_ERR_UNSUPPORTED, "clusters of %d blocks cannot be resident", cluster);
   b->L.cluster = cluster;
   b->L.n_clusters = n_clusters;
+  b->L.filler_blocks = 0;
+  if (cluster > 1) {
+    const int left = b->sms - n_clusters * cluster;
+    const int per_sm = fsb::batch_max_clusters(1, b->L.acc) / (b->sms > 0 ? b->sms : 1);
+    b->L.filler_blocks = left > 0 ? left * (per_sm > 0 ? per_sm : 1) : 0;
+  }
   int rc = build_order(b, cluster);
   if (rc != FSB_OK) return rc;
   for (auto& g : b->graphs) cudaGraphExecDestroy(g.exec);
@@ -138,7 +147,7 @@ int enqueue(fsb_batch* b, uint32_t n_steps, int init, cudaStream_t s) {
   L.n_steps = n_steps;
   L.init = init;
   L.stats = b->d_stats;
-  BCUDA(fsb::launch_batch(L, s));
+  BCUDA(fsb::launch_batch(L, s, b->side_stream, b->ev_fork, b->ev_join));
   if (n_steps) BCUDA(fsb::launch_bump_step(b->d_base, n_steps, s));
   return FSB_OK;
 }
@@ -186,6 +195,9 @@ void release(fsb_batch* b) {
   cudaFree(b->d_bctl);
   cudaFree(b->d_stats);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  if (b->side_stream) cudaStreamDestroy(b->side_stream);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->ev_join) cudaEventDestroy(b->ev_join);
   delete b;
 }
 
@@ -239,6 +251,12 @@ int fsb_batch_create(const fsb_config* tmpl, uint32_t n_schools, const uint64_t*
   });
   auto body = [&]() -> int {
     BCUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+    BCUDA(cudaStreamCreateWithFlags(&b->side_stream, cudaStreamNonBlocking));
+    BCUDA(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
+    BCUDA(cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming));
+    int dev = 0;
+    BCUDA(cudaGetDevice(&dev));
+    BCUDA(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev));
     BCUDA(cudaMalloc(&b->d_offsets, sizeof(unsigned long long) * (n_schools + 1)));
     BCUDA(cudaMalloc(&b->d_seeds, sizeof(unsigned long long) * n_schools));
     BCUDA(cudaMalloc(&b->d_order, sizeof(uint32_t) * n_schools));
@@ -328,10 +346,11 @@ int fsb_batch_set_cluster(fsb_batch_handle b, int cluster) {
   return rc;
 }
 
-int fsb_batch_info(fsb_batch_handle b, int* cluster, int* n_clusters, uint32_t* n_big,
-                   uint64_t* step) {
+int fsb_batch_info(fsb_batch_handle b, int* cluster, int* n_clusters, int* filler_blocks,
+                   uint32_t* n_big, uint64_t* step) {
   if (!b) return bfail(FSB_ERR_INVALID_ARG, "batch handle is NULL");
   if (cluster) *cluster = b->L.cluster;
+  if (filler_blocks) *filler_blocks = b->L.filler_blocks;
   if (n_clusters) *n_clusters = b->L.n_clusters;
   if (n_big) *n_big = b->L.n_big;
   if (step) *step = b->step;

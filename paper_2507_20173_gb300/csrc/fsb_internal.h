@@ -127,9 +127,15 @@ struct BatchLaunch {
   fsb_step_stats* stats;              // device, n_schools * n_steps
   int cluster;                        // blocks per cluster: 1, 2, 4, 8
   int n_clusters;                     // resident clusters (persistent grid)
+  int filler_blocks;                  // single-block launch beside it on the SMs the
+                                      // clusters leave idle (per-block queue only)
 };
 
-cudaError_t launch_batch(const BatchLaunch& L, cudaStream_t s);
+// Zeroes the work-list counters, then launches the cluster kernel on `s` and,
+// if L.filler_blocks > 0, the single-block filler on `side` (forked from and
+// joined back into `s` through the two events).
+cudaError_t launch_batch(const BatchLaunch& L, cudaStream_t s, cudaStream_t side,
+                         cudaEvent_t fork, cudaEvent_t join);
 int batch_max_clusters(int cluster, int acc);
 uint64_t batch_block_capacity();
 int batch_threads();

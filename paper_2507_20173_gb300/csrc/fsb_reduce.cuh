@@ -12,6 +12,59 @@ namespace fsb {
 
 constexpr unsigned kFullMask = 0xFFFFFFFFu;
 
+// A binary32 value with its rounding error carried alongside (hi + lo).
+struct F2 {
+  float hi, lo;
+};
+
+// Knuth's TwoSum: s = fl(a + b) and the exact error e, a + b = s + e.
+__device__ __forceinline__ F2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+
+// Merge operators of the three per-step partial types: binary32 (plain
+// sums), compensated binary32 pairs, binary64.  Reductions run on these so
+// the per-step path of the on-chip kernels issues no binary64 arithmetic in
+// the binary32 modes (binary64 runs at a small fraction of the binary32
+// rate on this GPU).
+__device__ __forceinline__ float merge(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double merge(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ F2 merge(F2 a, F2 b) {
+  const F2 t = two_sum(a.hi, b.hi);
+  return {t.hi, __fadd_rn(__fadd_rn(a.lo, b.lo), t.lo)};
+}
+__device__ __forceinline__ float shfl_xor(float v, int off) {
+  return __shfl_xor_sync(0xFFFFFFFFu, v, off);
+}
+__device__ __forceinline__ double shfl_xor(double v, int off) {
+  return __shfl_xor_sync(0xFFFFFFFFu, v, off);
+}
+__device__ __forceinline__ F2 shfl_xor(F2 v, int off) {
+  return {__shfl_xor_sync(0xFFFFFFFFu, v.hi, off), __shfl_xor_sync(0xFFFFFFFFu, v.lo, off)};
+}
+template <typename T>
+__device__ __forceinline__ T warp_merge(T v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v = merge(v, shfl_xor(v, off));
+  return v;
+}
+__device__ __forceinline__ double to_double(float v) { return static_cast<double>(v); }
+__device__ __forceinline__ double to_double(double v) { return v; }
+__device__ __forceinline__ double to_double(F2 v) {
+  return static_cast<double>(v.hi) + static_cast<double>(v.lo);
+}
+template <typename T>
+__device__ __forceinline__ T part_zero();
+template <>
+__device__ __forceinline__ float part_zero<float>() { return 0.f; }
+template <>
+__device__ __forceinline__ double part_zero<double>() { return 0.0; }
+template <>
+__device__ __forceinline__ F2 part_zero<F2>() { return {0.f, 0.f}; }
+
 template <int ACC>
 struct SumAcc;
 
@@ -19,6 +72,7 @@ struct SumAcc;
 template <>
 struct SumAcc<kAccPlain32> {
   using Sum = float;
+  using Part = float;
   float w = 0.f, x = 0.f, y = 0.f;
   __device__ __forceinline__ void add(float wi, float xi, float yi) {
     w = __fadd_rn(w, wi);
@@ -33,12 +87,16 @@ struct SumAcc<kAccPlain32> {
   __device__ __forceinline__ float rw() const { return w; }
   __device__ __forceinline__ float rx() const { return x; }
   __device__ __forceinline__ float ry() const { return y; }
+  __device__ __forceinline__ Part pw() const { return w; }
+  __device__ __forceinline__ Part px() const { return x; }
+  __device__ __forceinline__ Part py() const { return y; }
 };
 
 // Kahan-compensated binary32 per thread; combined in binary64 above.
 template <>
 struct SumAcc<kAccKahan32> {
   using Sum = double;
+  using Part = F2;
   float sw = 0.f, cw = 0.f, sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
   __device__ __forceinline__ static void kadd(float& s, float& c, float v) {
     const float yv = __fsub_rn(v, c);
@@ -67,12 +125,17 @@ struct SumAcc<kAccKahan32> {
   __device__ __forceinline__ double rw() const { return double(sw) - double(cw); }
   __device__ __forceinline__ double rx() const { return double(sx) - double(cx); }
   __device__ __forceinline__ double ry() const { return double(sy) - double(cy); }
+  // Kahan keeps the negated error in c: the value is s - c
+  __device__ __forceinline__ Part pw() const { return {sw, -cw}; }
+  __device__ __forceinline__ Part px() const { return {sx, -cx}; }
+  __device__ __forceinline__ Part py() const { return {sy, -cy}; }
 };
 
 // Binary64 accumulation (products of binary32 operands are exact).
 template <>
 struct SumAcc<kAccF64> {
   using Sum = double;
+  using Part = double;
   double w = 0.0, x = 0.0, y = 0.0;
   template <typename Real>
   __device__ __forceinline__ void add(Real wi, Real xi, Real yi) {
@@ -90,6 +153,9 @@ struct SumAcc<kAccF64> {
   __device__ __forceinline__ double rw() const { return w; }
   __device__ __forceinline__ double rx() const { return x; }
   __device__ __forceinline__ double ry() const { return y; }
+  __device__ __forceinline__ Part pw() const { return w; }
+  __device__ __forceinline__ Part px() const { return x; }
+  __device__ __forceinline__ Part py() const { return y; }
 };
 
 __device__ __forceinline__ float sum2(float a, float b) { return __fadd_rn(a, b); }

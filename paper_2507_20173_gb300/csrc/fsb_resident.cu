@@ -75,9 +75,10 @@ template <int FPT, int MAXB, int ACC>
 __global__ void __launch_bounds__(MAXB, 1) resident_kernel(ResidentArgs a) {
   using Acc = SumAcc<ACC>;
   using Sum = typename Acc::Sum;
+  using Part = typename Acc::Part;
   extern __shared__ float pend[];
   __shared__ uint32_t s_max[32], s_ekey[32];
-  __shared__ Sum s_w[32], s_x[32], s_y[32];
+  __shared__ Part s_w[32], s_x[32], s_y[32];
   __shared__ uint32_t s_M, s_E;
   __shared__ int s_abort;
 
@@ -213,7 +214,7 @@ __global__ void __launch_bounds__(MAXB, 1) resident_kernel(ResidentArgs a) {
     // ---- D: one block reduction for M_{u+1}, E_{u+1} and the sums of u
     mb = warp_max(mb);
     ek = warp_max(ek);
-    Sum sw = warp_sum(Sum(acc.rw())), sx = warp_sum(Sum(acc.rx())), sy = warp_sum(Sum(acc.ry()));
+    Part sw = warp_merge(acc.pw()), sx = warp_merge(acc.px()), sy = warp_merge(acc.py());
     if (lane == 0) {
       s_max[warp] = mb;
       s_ekey[warp] = ek;
@@ -225,19 +226,19 @@ __global__ void __launch_bounds__(MAXB, 1) resident_kernel(ResidentArgs a) {
     if (warp == 0) {
       uint32_t m = lane < nw ? s_max[lane] : 0u;
       uint32_t e = lane < nw ? s_ekey[lane] : 0u;
-      sw = lane < nw ? s_w[lane] : Sum(0);
-      sx = lane < nw ? s_x[lane] : Sum(0);
-      sy = lane < nw ? s_y[lane] : Sum(0);
+      sw = lane < nw ? s_w[lane] : part_zero<Part>();
+      sx = lane < nw ? s_x[lane] : part_zero<Part>();
+      sy = lane < nw ? s_y[lane] : part_zero<Part>();
       m = warp_max(m);
       e = warp_max(e);
-      sw = warp_sum(sw);
-      sx = warp_sum(sx);
-      sy = warp_sum(sy);
+      sw = warp_merge(sw);
+      sx = warp_merge(sx);
+      sy = warp_merge(sy);
       if (lane == 0) {
         double* p = a.sums + (static_cast<uint64_t>(u - 1) * gridDim.x + blockIdx.x) * 3;
-        p[0] = static_cast<double>(sw);
-        p[1] = static_cast<double>(sx);
-        p[2] = static_cast<double>(sy);
+        p[0] = to_double(sw);
+        p[1] = to_double(sx);
+        p[2] = to_double(sy);
         if (has_next)
           publish(u + 1, m, e);
         else if (multi)
@@ -264,6 +265,7 @@ __global__ void __launch_bounds__(MAXB, 1) resident_kernel(ResidentArgs a) {
   if (tid == 0 && multi && !grid_wait(a, a.n_steps + 1)) s_abort = 1;
   __syncthreads();
   if (s_abort) return;
+  __shared__ Sum f_w[32], f_x[32], f_y[32];
   for (uint32_t s = blockIdx.x; s < a.n_steps; s += gridDim.x) {
     Sum fw = Sum(0), fx = Sum(0), fy = Sum(0);
     for (uint32_t b = tid; b < gridDim.x; b += B) {
@@ -277,15 +279,15 @@ __global__ void __launch_bounds__(MAXB, 1) resident_kernel(ResidentArgs a) {
     fy = warp_sum(fy);
     __syncthreads();
     if (lane == 0) {
-      s_w[warp] = fw;
-      s_x[warp] = fx;
-      s_y[warp] = fy;
+      f_w[warp] = fw;
+      f_x[warp] = fx;
+      f_y[warp] = fy;
     }
     __syncthreads();
     if (warp == 0) {
-      fw = lane < nw ? s_w[lane] : Sum(0);
-      fx = lane < nw ? s_x[lane] : Sum(0);
-      fy = lane < nw ? s_y[lane] : Sum(0);
+      fw = lane < nw ? f_w[lane] : Sum(0);
+      fx = lane < nw ? f_x[lane] : Sum(0);
+      fy = lane < nw ? f_y[lane] : Sum(0);
       fw = warp_sum(fw);
       fx = warp_sum(fx);
       fy = warp_sum(fy);
