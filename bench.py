@@ -49,7 +49,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["stream", "small", "resident", "batch"],
+    ap.add_argument("--workload", choices=["stream", "small", "resident", "batch", "precision"],
                     default="stream")
     ap.add_argument("--batch-schools", type=int, default=None,
                     help="use only the first N schools of the batched ensemble")
@@ -62,6 +62,8 @@ def parse_args():
     ap.add_argument("--stream-kernel", type=int, default=0,
                     help="0 library choice, 1 vector loads, 2 bulk-copy ring")
     ap.add_argument("--stream-block", type=int, default=0)
+    ap.add_argument("--reference-fish", type=int, default=1 << 22,
+                    help="fish per bench step of the CPU reference arm")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -83,6 +85,18 @@ def dist_setup(args):
         dist.init_process_group(backend=backend)
         pg = dist
     return world, rank, local, pg
+
+
+def reduce_max(value, pg):
+    """Max of a float over all ranks (identity on one rank).  NCCL reduces a
+    CUDA tensor, gloo a CPU one."""
+    if pg is None:
+        return float(value)
+    import torch
+    dev = "cuda" if pg.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
 
 
 def measured_peaks():
@@ -265,10 +279,7 @@ def run_batch(args, world, rank, local, pg):
     kms, kl = fsb.fsb_batch_kernel_time(b)
     info = fsb.fsb_batch_info(b)
     fsb.fsb_batch_destroy(b)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if pg is not None:
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = reduce_max(ms, pg)
     value = world * total * steps / (ms_max / 1e3)
 
     per_school = None
@@ -318,6 +329,88 @@ def run_batch(args, world, rank, local, pg):
         print(json.dumps(line), flush=True)
 
 
+def exact_sums(w, x, y):
+    """Reference sums of the read-back state: binary64 products (exact for
+    binary32 inputs), summed pairwise in binary64 in 4096 chunks whose sums
+    are added exactly by math.fsum; relative error about 1e-15 of sum |w x|,
+    far below the 1e-12 the binary64 modes are held to."""
+    import math
+    w64, x64, y64 = (np.asarray(a, dtype=np.float64) for a in (w, x, y))
+    wx, wy = w64 * x64, w64 * y64
+
+    def fsum_chunked(v):
+        return math.fsum(np.sum(c) for c in np.array_split(v, 4096))
+    return {"sum_w": fsum_chunked(w64), "sum_wx": fsum_chunked(wx), "sum_wy": fsum_chunked(wy),
+            "abs_wx": float(np.sum(np.abs(wx))), "abs_wy": float(np.sum(np.abs(wy)))}
+
+
+def run_precision(args, world, rank, local):
+    """Precision study: one school of N = 2^24 fish (seed 100, a member of
+    the 64-school study ensemble), T = 1000 steps, in each arithmetic mode.
+    Reports each mode's throughput, the error of its barycentre sums at
+    steps 1, 10, 100 and 1000 against the exact sums of the read-back state
+    (normalised by sum |w x|), and the drift between the binary32 and the
+    binary64 trajectories (the same draws, different rounding)."""
+    import torch
+
+    import paper_2507_20173_gb300 as fsb
+    from paper_2507_20173_gb300 import build as fsb_build
+
+    torch.cuda.set_device(local)
+    fsb_build.build()
+    fsb.lib()
+    n = args.n_fish or (1 << 24)
+    total = args.steps if args.steps is not None else 1000
+    marks = [m for m in (1, 10, 100, 1000) if m <= total]
+    stream = torch.cuda.current_stream()
+    modes = {}
+    finals = {}
+    for name in ("FP32", "FP32_KAHAN", "FP64_ACC", "FP64_STATE"):
+        cfg = fsb.fsb_config_init(n, 100, precision=getattr(fsb, "FSB_" + name),
+                                  path=fsb.FSB_PATH_STREAM)
+        s = fsb.School.create(cfg, stream=stream)
+        errs = {}
+        done = 0
+        elapsed = 0.0
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for m in marks:
+            k = m - done
+            torch.cuda.synchronize()
+            start.record(stream)
+            st = s.step(k, stats=True)
+            stop.record(stream)
+            torch.cuda.synchronize()
+            elapsed += start.elapsed_time(stop) / 1e3
+            done = m
+            got = s.read()
+            ex = exact_sums(got["w"], got["x"], got["y"])
+            last = st[-1]
+            errs[str(m)] = {
+                "sum_w": abs(last["sum_w"] - ex["sum_w"]) / abs(ex["sum_w"]),
+                "sum_wx": abs(last["sum_wx"] - ex["sum_wx"]) / ex["abs_wx"],
+                "sum_wy": abs(last["sum_wy"] - ex["sum_wy"]) / ex["abs_wy"],
+                "bary_x_abs_err": abs(last["sum_wx"] / last["sum_w"] - ex["sum_wx"] / ex["sum_w"])}
+        finals[name] = got
+        s.destroy()
+        modes[name] = {"fish_steps_per_s": n * total / elapsed, "errors": errs}
+    drift = {f: float(np.max(np.abs(finals["FP32_KAHAN"][f].astype(np.float64) -
+                                    finals["FP64_STATE"][f])))
+             for f in ("x", "y", "w")}
+    drift["mean_abs_x"] = float(np.mean(np.abs(finals["FP32_KAHAN"]["x"].astype(np.float64) -
+                                               finals["FP64_STATE"]["x"])))
+    if rank == 0:
+        line = {"metric": "precision study: barycentre error and throughput per arithmetic mode",
+                "value": modes["FP32_KAHAN"]["fish_steps_per_s"], "unit": UNIT, "n_gpus": 1,
+                "steps": total, "warmup": 0, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
+                "config": {"workload": "precision N=2^%d T=%d seed 100" % (n.bit_length() - 1,
+                                                                          total),
+                           "note": "one school of the 64-school ensemble; errors against exact "
+                                   "host sums of the read-back state"},
+                "modes": modes, "trajectory_drift_fp32_vs_fp64_state": drift}
+        print(json.dumps(line), flush=True)
+
+
 def run_reference(args, world, rank):
     """The oracle as it stands, each bench step a bounded sample of the
     workload (2^22 fish of the same school rule, one step)."""
@@ -325,7 +418,7 @@ def run_reference(args, world, rank):
     if rank != 0:
         return
     import oracle
-    n = min(wl.n_fish, 1 << 22)
+    n = min(wl.n_fish, args.reference_fish)
     steps = args.steps if args.steps is not None else wl.steps
     cfg = oracle.Config(n_fish=n, seed=wl.seed)
     school = oracle.init(cfg)
@@ -397,10 +490,7 @@ def run_ours(args, world, rank, local, pg):
     fused_ms, fused_n = fsb.fsb_kernel_time(school.handle)
     path = fsb.fsb_handle_path(school.handle)
     school.destroy()
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if pg is not None:
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = reduce_max(ms, pg)
     value = world * n * steps / (ms_max / 1e3)
 
     # ---- roofline of the dominant kernel
@@ -456,10 +546,7 @@ def run_ours(args, world, rank, local, pg):
         fsb.fsb_read_state(h, *(outs[k].numpy() for k in ("x", "y", "w", "prev", "cur")))
         e2e_s = time.perf_counter() - t0
         fsb.fsb_destroy(h)
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        if pg is not None:
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_s = float(t.item())
+        e2e_s = reduce_max(e2e_s, pg)
         e2e = {"value": world * n * steps / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": int(4 * elem * n / steps),
                "d2h_bytes_per_step": int((5 * elem * n + 40 * steps) / steps),
@@ -508,6 +595,8 @@ def main():
         run_reference(args, world, rank)
     elif args.workload == "batch":
         run_batch(args, world, rank, local, pg)
+    elif args.workload == "precision":
+        run_precision(args, world, rank, local)
     else:
         run_ours(args, world, rank, local, pg)
     if pg is not None:

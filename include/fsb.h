@@ -294,6 +294,8 @@ int fsb_set_fault_injection(fsb_handle h, int block, uint32_t step, uint64_t tim
  *   resident_fpt         fish per thread of the resident kernel: 4, 8, 12, 16
  *   resident_block       threads per block of the resident kernel (multiple
  *                        of 32, at most the variant's compiled maximum)
+ *   stream_stages        bulk-copy kernel: shared-memory tiles in flight per
+ *                        block, 2, 3 or 4
  * A combination that cannot run returns FSB_ERR_INVALID_ARG and leaves the
  * handle unchanged.  Synchronises the handle's stream. */
 typedef struct {
@@ -302,6 +304,7 @@ typedef struct {
     int32_t stream_blocks_per_sm;
     int32_t resident_fpt;
     int32_t resident_block;
+    int32_t stream_stages;
 } fsb_tuning;
 
 int fsb_set_tuning(fsb_handle h, const fsb_tuning* t);

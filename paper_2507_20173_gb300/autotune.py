@@ -17,7 +17,7 @@ import sys
 import paper_2507_20173_gb300 as fsb
 
 TABLE_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_table.json")
-DEFAULT_SIZES = [1 << k for k in range(10, 29, 2)] + [10_000, 1 << 20, 1 << 21, 1 << 23]
+DEFAULT_SIZES = sorted(set([1 << k for k in range(10, 29, 2)] + [10_000, 1 << 21, 1 << 23]))
 PRECISIONS = {"FP32": fsb.FSB_FP32, "FP32_KAHAN": fsb.FSB_FP32_KAHAN,
               "FP64_ACC": fsb.FSB_FP64_ACC, "FP64_STATE": fsb.FSB_FP64_STATE}
 

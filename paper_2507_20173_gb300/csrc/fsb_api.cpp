@@ -295,17 +295,23 @@ bool resident_config(int sms, int acc, uint64_t n, fsb::ResidentLaunch* R, int w
 constexpr int kMaxPartialsPerSm = 8;
 
 // Streaming launch shape: kernel variant, block, grid.  Invalidates graphs.
-int configure_stream(fsb_school* h, int kernel, int block, int blocks_per_sm) {
+int configure_stream(fsb_school* h, int kernel, int block, int blocks_per_sm, int stages) {
   StreamLaunch L = h->launch;
   const bool tma_ok = !L.real_is_double && L.vec == 4;
-  if (kernel == 0) kernel = 1;
+  // defaults measured on GB300 at N = 2^28: bulk-copy ring, 512 threads, 2
+  // stages (0.92 of the copy peak); vector loads, 256 threads, 4 blocks/SM
+  if (kernel == 0) kernel = tma_ok ? 2 : 1;
+  if (stages == 0) stages = 2;
+  if (stages < 2 || stages > 4) return fail(FSB_ERR_INVALID_ARG, "stream stages must be 2..4");
   if (kernel == 2 && !tma_ok)
     return fail(FSB_ERR_INVALID_ARG, "bulk-copy kernel needs binary32, 16-byte aligned state");
   if (kernel != 1 && kernel != 2) return fail(FSB_ERR_INVALID_ARG, "unknown stream kernel");
-  if (block == 0) block = 256;
+  if (block == 0) block = kernel == 2 ? 512 : 256;
+  if (blocks_per_sm == 0 && kernel == 1 && block == 256) blocks_per_sm = 4;
   if (block != 256 && block != 512) return fail(FSB_ERR_INVALID_ARG, "stream block must be 256/512");
   L.tma = kernel == 2 ? 1 : 0;
   L.block = block;
+  L.stages = stages;
   // the vector kernel is compiled for 1, 3 or 4 guaranteed blocks per SM
   // (register budgets of 255, 80 and 64 per thread at 256 threads)
   L.min_blocks = 1;
@@ -331,6 +337,7 @@ int configure_stream(fsb_school* h, int kernel, int block, int blocks_per_sm) {
   h->tuning.stream_kernel = kernel;
   h->tuning.stream_block = block;
   h->tuning.stream_blocks_per_sm = per_sm;
+  h->tuning.stream_stages = L.tma ? stages : 0;
   for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
   h->graphs.clear();
   return FSB_OK;
@@ -498,7 +505,7 @@ int fsb_create(const fsb_config* cfg, const fsb_state_dev* buffers, const fsb_st
     h->sms = sms;
     FSB_CUDA(cudaMalloc(&h->partials, sizeof(BlockPartial) * sms * kMaxPartialsPerSm));
     L.partials = h->partials;
-    int r0 = configure_stream(h, 0, 0, 0);
+    int r0 = configure_stream(h, 0, 0, 0, 0);
     if (r0 != FSB_OK) return r0;
 
     // resident path: binary32 state that fits in registers across the SMs
@@ -634,7 +641,8 @@ int fsb_set_tuning(fsb_handle h, const fsb_tuning* t) {
   FSB_CUDA(cudaStreamSynchronize(h->stream));
   const StreamLaunch saved = h->launch;
   const fsb_tuning saved_t = h->tuning;
-  int rc = configure_stream(h, t->stream_kernel, t->stream_block, t->stream_blocks_per_sm);
+  int rc = configure_stream(h, t->stream_kernel, t->stream_block, t->stream_blocks_per_sm,
+                            t->stream_stages);
   if (rc != FSB_OK) {
     h->launch = saved;
     h->tuning = saved_t;

@@ -3,8 +3,9 @@
 // reports the fastest.
 //
 // Candidates:
-//   streaming path: {vector loads, bulk-copy ring} x {256, 512} threads x
-//                   {occupancy, 3, 4} guaranteed blocks per SM
+//   streaming path: vector loads x {256, 512} threads x {occupancy, 3, 4}
+//                   guaranteed blocks per SM; bulk-copy ring x {256, 512}
+//                   threads x {2, 3, 4} stages
 //   resident path:  fish per thread {4, 8, 12, 16} x the block sizes that
 //                   keep the school in registers across at most one block
 //                   per SM
@@ -67,19 +68,26 @@ extern "C" int fsb_autotune(const fsb_config* cfg, uint32_t n_steps, int* best_p
   if (n_steps == 0) return fsb::record_error(FSB_ERR_INVALID_ARG, "n_steps must be >= 1");
   const bool dbl = cfg->precision == FSB_FP64_STATE;
   std::vector<Candidate> cands;
-  const int kernels[] = {1, 2};
   const int blocks[] = {256, 512};
   const int minbs[] = {0, 3, 4};
-  for (int k : kernels)
+  for (int b : blocks)
+    for (int m : minbs) {  // vector-load kernel
+      if (m && (b != 256 || dbl)) continue;
+      Candidate c{};
+      c.path = FSB_PATH_STREAM;
+      c.t.stream_kernel = 1;
+      c.t.stream_block = b;
+      c.t.stream_blocks_per_sm = m;
+      cands.push_back(c);
+    }
+  if (!dbl)
     for (int b : blocks)
-      for (int m : minbs) {
-        if (k == 2 && (dbl || m)) continue;
-        if (m && (b != 256 || dbl)) continue;
+      for (int st = 2; st <= 4; ++st) {  // bulk-copy ring
         Candidate c{};
         c.path = FSB_PATH_STREAM;
-        c.t.stream_kernel = k;
+        c.t.stream_kernel = 2;
         c.t.stream_block = b;
-        c.t.stream_blocks_per_sm = m;
+        c.t.stream_stages = st;
         cands.push_back(c);
       }
   if (!dbl) {

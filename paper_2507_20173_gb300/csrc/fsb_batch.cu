@@ -86,9 +86,9 @@ __device__ __forceinline__ void block_reduce(BlockReduce<ACC>& R, uint32_t& m, u
   constexpr int nw = kBatchThreads / 32;
   m = warp_max(m);
   e = warp_max(e);
-  sw = warp_merge(sw);
-  sx = warp_merge(sx);
-  sy = warp_merge(sy);
+  sw = warp_tree(sw);
+  sx = warp_tree(sx);
+  sy = warp_tree(sy);
   __syncthreads();  // previous use of R is finished
   if (lane == 0) {
     R.s_max[warp] = m;

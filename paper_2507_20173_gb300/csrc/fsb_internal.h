@@ -53,6 +53,7 @@ struct StreamLaunch {
   int grid;         // blocks
   int tma;          // 1: bulk-copy ring kernel (fsb_stream_tma.cu)
   int min_blocks;   // vector kernel: blocks per SM its register budget guarantees
+  int stages;       // bulk-copy kernel: tiles in flight per block (2, 3, 4; 0 = 2)
   double pond_half, step, w0, w_min, w_max;
   Ctl* ctl;
   BlockPartial* partials;

@@ -51,6 +51,21 @@ __device__ __forceinline__ T warp_merge(T v) {
   for (int off = 16; off > 0; off >>= 1) v = merge(v, shfl_xor(v, off));
   return v;
 }
+// Intra-warp reduction of per-thread partials: compensated pairs are summed
+// as two independent binary32 trees (hi and lo; five roundings each, so the
+// error stays near 5 ulps of the warp's magnitudes), the exact TwoSum merge
+// being kept for the cross-warp level (warp_merge).
+__device__ __forceinline__ float warp_tree(float v) { return warp_merge(v); }
+__device__ __forceinline__ double warp_tree(double v) { return warp_merge(v); }
+__device__ __forceinline__ F2 warp_tree(F2 v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    v.hi = __fadd_rn(v.hi, __shfl_xor_sync(0xFFFFFFFFu, v.hi, off));
+    v.lo = __fadd_rn(v.lo, __shfl_xor_sync(0xFFFFFFFFu, v.lo, off));
+  }
+  return v;
+}
+
 __device__ __forceinline__ double to_double(float v) { return static_cast<double>(v); }
 __device__ __forceinline__ double to_double(double v) { return v; }
 __device__ __forceinline__ double to_double(F2 v) {

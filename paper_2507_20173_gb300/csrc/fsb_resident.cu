@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(MAXB, 1) resident_kernel(ResidentArgs a) {
     // ---- D: one block reduction for M_{u+1}, E_{u+1} and the sums of u
     mb = warp_max(mb);
     ek = warp_max(ek);
-    Part sw = warp_merge(acc.pw()), sx = warp_merge(acc.px()), sy = warp_merge(acc.py());
+    Part sw = warp_tree(acc.pw()), sx = warp_tree(acc.px()), sy = warp_tree(acc.py());
     if (lane == 0) {
       s_max[warp] = mb;
       s_ekey[warp] = ek;

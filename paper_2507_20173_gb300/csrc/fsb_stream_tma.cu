@@ -235,19 +235,30 @@ const void* pick_pass(int pass, int acc) {
   }
 }
 
-constexpr int kStages = 4;
+template <int THREADS>
+const void* pick_stages(int stages, int pass, int acc, size_t* smem) {
+  switch (stages) {
+    case 2:
+      *smem = sizeof(TmaRing<THREADS, 2>);
+      return pick_pass<THREADS, 2>(pass, acc);
+    case 3:
+      *smem = sizeof(TmaRing<THREADS, 3>);
+      return pick_pass<THREADS, 3>(pass, acc);
+    case 4:
+      *smem = sizeof(TmaRing<THREADS, 4>);
+      return pick_pass<THREADS, 4>(pass, acc);
+    default:
+      return nullptr;
+  }
+}
 
 const void* pick(const StreamLaunch& L, int pass, size_t* smem) {
   if (L.real_is_double || L.vec != 4) return nullptr;
+  const int stages = L.stages ? L.stages : 2;
   switch (L.block) {
-    case 256:
-      *smem = sizeof(TmaRing<256, kStages>);
-      return pick_pass<256, kStages>(pass, L.acc);
-    case 512:
-      *smem = sizeof(TmaRing<512, kStages>);
-      return pick_pass<512, kStages>(pass, L.acc);
-    default:
-      return nullptr;
+    case 256: return pick_stages<256>(stages, pass, L.acc, smem);
+    case 512: return pick_stages<512>(stages, pass, L.acc, smem);
+    default: return nullptr;
   }
 }
 

@@ -117,18 +117,21 @@ def test_unaligned_buffers_take_the_scalar_path(precision):
     assert_stats_match(stats, ref_stats, precision, "unaligned")
 
 
-VARIANTS = [(1, 256), (1, 512), (2, 256), (2, 512)]
+# (kernel, block, blocks per SM, stages): vector loads with 1 / 3 / 4
+# guaranteed blocks per SM, bulk-copy ring with 2 / 3 / 4 stages
+VARIANTS = [(1, 256, 0, 0), (1, 256, 3, 0), (1, 256, 4, 0), (1, 512, 0, 0),
+            (2, 256, 0, 2), (2, 256, 0, 3), (2, 256, 0, 4), (2, 512, 0, 2), (2, 512, 0, 4)]
 
 
-@pytest.mark.parametrize("kernel,block", VARIANTS)
+@pytest.mark.parametrize("kernel,block,per_sm,stages", VARIANTS)
 @pytest.mark.parametrize("n", [1, 33, 2047, 2048, 2049, 4096 * 3 + 5, 1_000_003])
-def test_stream_kernel_variants(kernel, block, n):
-    """Every launch shape of the streaming pass (vector loads or bulk-copy
-    ring, 256 or 512 threads): whole tiles, a ragged tail, fewer tiles than
-    blocks."""
+def test_stream_kernel_variants(kernel, block, per_sm, stages, n):
+    """Every launch shape of the streaming pass: whole tiles, a ragged tail,
+    fewer tiles than blocks."""
     cfg = stream_cfg(n, 1234 + n, step=1.5, init_weight_mode=1)
     school = fsb.School.create(cfg)
-    fsb.fsb_set_tuning(school.handle, stream_kernel=kernel, stream_block=block)
+    fsb.fsb_set_tuning(school.handle, stream_kernel=kernel, stream_block=block,
+                       stream_blocks_per_sm=per_sm, stream_stages=stages)
     t = fsb.fsb_get_tuning(school.handle)
     assert (t["stream_kernel"], t["stream_block"]) == (kernel, block)
     stats = school.step(7, stats=True)
@@ -139,6 +142,26 @@ def test_stream_kernel_variants(kernel, block, n):
     ref_stats = oracle.run(ocfg, ref, 0, 7)
     assert_state_equal(got, ref, "variant %d/%d N=%d" % (kernel, block, n))
     assert_stats_match(stats, ref_stats, cfg.precision, "variant %d/%d N=%d" % (kernel, block, n))
+
+
+def test_autotuner_choice_reproduces_the_oracle():
+    """The native autotuner measures every launch shape of both paths; the
+    winner, applied to a new school, still gives the oracle's trajectory."""
+    n, steps = 300_000, 6
+    cfg = fsb.fsb_config_init(n, 5)
+    r = fsb.fsb_autotune(cfg, 10)
+    assert r["candidates"] >= 8 and r["fish_steps_per_s"] > 0
+    run = fsb.fsb_config_init(n, 5, path=r["path"])
+    s = fsb.School.create(run)
+    fsb.fsb_set_tuning(s.handle, **r["tuning"])
+    stats = s.step(steps, stats=True)
+    got = s.read()
+    s.destroy()
+    ocfg = oracle_config(cfg)
+    ref = oracle.init(ocfg)
+    ref_stats = oracle.run(ocfg, ref, 0, steps)
+    assert_state_equal(got, ref, "autotuned")
+    assert_stats_match(stats, ref_stats, cfg.precision, "autotuned")
 
 
 def test_bulk_copy_kernel_needs_binary32_aligned_state():
