@@ -223,6 +223,9 @@ __device__ __forceinline__ bool bounded_wait_geq(const unsigned* count, unsigned
   const unsigned long long t0 = global_ns();
   for (unsigned spins = 0;; ++spins) {
     if (ld_acquire_gpu(count) >= target) return true;
+    // back off so the spinning warp does not take issue slots from the
+    // block's other warps
+    if (spins > 4) __nanosleep(64);
     if ((spins & 15u) == 15u) {
       if (ld_relaxed_gpu(status) != 0) return false;
       if (global_ns() - t0 > timeout_ns) {

@@ -87,8 +87,12 @@ __global__ void __launch_bounds__(MAXB, 1) resident_kernel(ResidentArgs a) {
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   const bool multi = gridDim.x > 1;
-  const uint64_t lo = static_cast<uint64_t>(blockIdx.x) * a.slice;
-  const uint64_t hi = lo + a.slice < a.n ? lo + a.slice : a.n;
+  // a resident school holds at most ~2.5 million fish, so indices fit 32
+  // bits; this thread's fish are i0 + k * B for k < nk
+  const uint32_t lo = static_cast<uint32_t>(blockIdx.x * a.slice);
+  const uint32_t hi = static_cast<uint32_t>(lo + a.slice < a.n ? lo + a.slice : a.n);
+  const uint32_t i0 = lo + tid;
+  const int nk = i0 < hi ? static_cast<int>((hi - i0 + B - 1) / B) : 0;
   auto P = [&](uint32_t buf, int q, int k) -> float& {
     return pend[((buf * 3 + q) * FPT + k) * B + tid];
   };
@@ -96,8 +100,8 @@ __global__ void __launch_bounds__(MAXB, 1) resident_kernel(ResidentArgs a) {
   float x[FPT], y[FPT], w[FPT], f[FPT], pv[FPT];
 #pragma unroll
   for (int k = 0; k < FPT; ++k) {
-    const uint64_t i = lo + static_cast<uint64_t>(k) * B + tid;
-    if (i < hi) {
+    const uint32_t i = i0 + k * B;
+    if (k < nk) {
       x[k] = a.x[i];
       y[k] = a.y[i];
       w[k] = a.w[i];
@@ -117,8 +121,8 @@ __global__ void __launch_bounds__(MAXB, 1) resident_kernel(ResidentArgs a) {
     ek = 0;
 #pragma unroll
     for (int k = 0; k < FPT; ++k) {
-      const uint64_t i = lo + static_cast<uint64_t>(k) * B + tid;
-      if (i < hi) {
+      const uint32_t i = i0 + k * B;
+      if (k < nk) {
         pv[k] = f[k];
         const Words4 r = fish_draw(a.key, a.school, i, t, kDomainSwim);
         swim(x[k], y[k], r.v[0], r.v[1], a.ph);
@@ -204,8 +208,7 @@ __global__ void __launch_bounds__(MAXB, 1) resident_kernel(ResidentArgs a) {
     Acc acc;
 #pragma unroll
     for (int k = 0; k < FPT; ++k) {
-      const uint64_t i = lo + static_cast<uint64_t>(k) * B + tid;
-      if (i < hi) {
+      if (k < nk) {
         if (M > 0.f) w[k] = eat(w[k], P(u & 1u, 0, k), M, a.ph);
         acc.add(w[k], P(u & 1u, 1, k), P(u & 1u, 2, k));
       }
@@ -251,8 +254,8 @@ __global__ void __launch_bounds__(MAXB, 1) resident_kernel(ResidentArgs a) {
   // ---- write the state back
 #pragma unroll
   for (int k = 0; k < FPT; ++k) {
-    const uint64_t i = lo + static_cast<uint64_t>(k) * B + tid;
-    if (i < hi) {
+    const uint32_t i = i0 + k * B;
+    if (k < nk) {
       a.x[i] = x[k];
       a.y[i] = y[k];
       a.w[i] = w[k];
