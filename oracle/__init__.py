@@ -74,7 +74,8 @@ class _CConfig(ctypes.Structure):
                 ("school_id", ctypes.c_uint32), ("init_weight_mode", ctypes.c_int32),
                 ("pond_half", ctypes.c_double), ("step", ctypes.c_double),
                 ("w0", ctypes.c_double), ("w_min", ctypes.c_double),
-                ("w_max", ctypes.c_double)]
+                ("w_max", ctypes.c_double), ("swim_mode", ctypes.c_int32),
+                ("feed_mode", ctypes.c_int32)]
 
 
 @dataclass
@@ -89,11 +90,14 @@ class Config:
     w0: float = 1.0
     w_min: float = 0.0
     w_max: float = 2.0
+    swim_mode: int = 0     # 1: half-width s * (w / w0) (weight-scaled swim)
+    feed_mode: int = 0     # 1: normalise feeding by the paper's max(prev - cur)
 
     def c(self) -> _CConfig:
         return _CConfig(self.n_fish, self.seed, self.school_id,
                         self.init_weight_mode, self.pond_half, self.step,
-                        self.w0, self.w_min, self.w_max)
+                        self.w0, self.w_min, self.w_max, self.swim_mode,
+                        self.feed_mode)
 
 
 _lib = None

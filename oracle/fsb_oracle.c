@@ -36,6 +36,16 @@
  *                 positions after this step's swim and the weights after
  *                 this step's eat (reading: weighted centre of the school)
  *
+ * Variants (off by default; the paper says weight affects mobility,
+ * Sec. 2.1.1 / 2.1.2, and its eat() reduces max(prev - cur), Sec. 2.3.2):
+ *   swim_mode 1   the move's half-width is s * (w / w0) with the fish's
+ *                 weight before this step's eat: heavier fish swim farther,
+ *                 a fish of weight 0 stays put
+ *   feed_mode 1   feeding is normalised by the paper's eat() value
+ *                 E_t = max_i (prev_i - cur_i): if E_t > 0,
+ *                 w <- clamp(w + (prev - cur) / E_t, w_min, w_max); else no
+ *                 fish eats
+ *
  * Draws: u(r) = (r >> 8) * 2^-24 from Philox4x32-10 words (philox.c), so
  * 2u - 1 is exact in binary32.  Each arithmetic operation rounds once to
  * nearest-even in FSBO_REAL.
@@ -102,8 +112,9 @@ static void csum_add_product(csum* a, double p, double q)
     csum_add(a, lo);
 }
 
-/* Swim of one fish at step t with draw words r0, r1; updates the objective
- * fields and returns delta = currentObjective - prevObjective. */
+/* Swim of one fish at step t with draw words r0, r1 and half-width s;
+ * updates the objective fields and returns delta = currentObjective -
+ * prevObjective. */
 static real swim_one(FISH* f, uint32_t r0, uint32_t r1, real P, real s)
 {
     real nx = f->x + centred_uniform(r0) * s;
@@ -120,9 +131,19 @@ static real eat_one(real w, real delta, real M, real wmin, real wmax)
     return clamp_r(w + delta / M, wmin, wmax);
 }
 
+/* Half-width of one fish's move: s, or s * (w / w0) in swim_mode 1. */
+static real swim_width(const fsbo_config* cfg, real s, real w0, real w)
+{
+    if (cfg->swim_mode == 0) return s;
+    return (w / w0) * s;
+}
+
 static int config_ok(const fsbo_config* cfg)
 {
     if (!cfg || cfg->n_fish == 0) return 0;
+    if (cfg->swim_mode != 0 && cfg->swim_mode != 1) return 0;
+    if (cfg->feed_mode != 0 && cfg->feed_mode != 1) return 0;
+    if (cfg->swim_mode == 1 && !(cfg->w0 > 0.0)) return 0;
     if (!(cfg->pond_half > 0.0) || !(cfg->step >= 0.0)) return 0;
     if (!(cfg->w_min <= cfg->w_max)) return 0;
     if (cfg->init_weight_mode != 0 && cfg->init_weight_mode != 1) return 0;
@@ -160,6 +181,7 @@ int FN(fsbo_run)(const fsbo_config* cfg, uint64_t t0, uint32_t n_steps,
     const uint64_t N = cfg->n_fish;
     const real P = (real)cfg->pond_half;
     const real s = (real)cfg->step;
+    const real w0 = (real)cfg->w0;
     const real wmin = (real)cfg->w_min;
     const real wmax = (real)cfg->w_max;
 
@@ -178,7 +200,8 @@ int FN(fsbo_run)(const fsbo_config* cfg, uint64_t t0, uint32_t n_steps,
             } else {
                 fsbo_swim_words(cfg, i, t, r);
             }
-            delta[i] = swim_one(&school[i], r[0], r[1], P, s);
+            delta[i] = swim_one(&school[i], r[0], r[1], P,
+                                swim_width(cfg, s, w0, school[i].weight));
         }
 
         /* max |delta| and the paper's eat() statistic, initialised to
@@ -194,11 +217,18 @@ int FN(fsbo_run)(const fsbo_config* cfg, uint64_t t0, uint32_t n_steps,
         }
 
         /* eat */
-        if (M > 0.0) {
+        if (cfg->feed_mode == 0 && M > 0.0) {
             const real Mr = (real)M;   /* exact: M is one of the deltas */
             for (uint64_t i = 0; i < N; ++i)
                 school[i].weight = eat_one(school[i].weight, delta[i], Mr,
                                            wmin, wmax);
+        } else if (cfg->feed_mode == 1 && eat_max > 0.0) {
+            const real Er = (real)eat_max;  /* exact: one fish's prev - cur */
+            for (uint64_t i = 0; i < N; ++i)
+                school[i].weight = eat_one(school[i].weight,
+                                           school[i].prevObjective -
+                                               school[i].currentObjective,
+                                           Er, wmin, wmax);
         }
 
         /* barycentre sums */
@@ -228,6 +258,8 @@ int FN(fsbo_run)(const fsbo_config* cfg, uint64_t t0, uint32_t n_steps,
     return 0;
 }
 
+/* Positions do not depend on weights only in swim_mode 0; this helper
+ * follows one fish in that mode (the fish's weight is not touched). */
 void FN(fsbo_track_fish)(const fsbo_config* cfg, uint64_t i, uint64_t t0,
                          uint32_t n_steps, FISH* fish, real* out_x,
                          real* out_y, real* out_delta)

@@ -38,6 +38,9 @@ typedef struct {
     double   w0;              /* initial weight */
     double   w_min;           /* weight floor */
     double   w_max;           /* weight cap */
+    int32_t  swim_mode;       /* 0: move half-width s; 1: s * (w / w0) */
+    int32_t  feed_mode;       /* 0: w += delta / max|delta|;
+                                 1: w += (prev - cur) / max(prev - cur)  */
 } fsbo_config;
 
 /* Per-step statistics. */

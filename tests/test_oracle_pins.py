@@ -98,7 +98,9 @@ def parse_fixture(path):
         if tok[0] == "config":
             cfg = oracle.Config(n_fish=int(kv["n_fish"]), pond_half=float(kv["pond_half"]),
                                 step=float(kv["step"]), w0=float(kv["w0"]),
-                                w_min=float(kv["w_min"]), w_max=float(kv["w_max"]))
+                                w_min=float(kv["w_min"]), w_max=float(kv["w_max"]),
+                                swim_mode=int(kv.get("swim_mode", 0)),
+                                feed_mode=int(kv.get("feed_mode", 0)))
         elif tok[0] == "init":
             init[int(tok[1])] = kv
         elif tok[0] == "step":
@@ -170,7 +172,8 @@ def test_philox_words_are_uniform():
 
 @pytest.mark.parametrize("precision", ["f32", "f64"])
 @pytest.mark.parametrize("name", ["handworked_n3.txt", "handworked_bank.txt",
-                                  "handworked_mapping.txt"])
+                                  "handworked_mapping.txt", "handworked_weighted_swim.txt",
+                                  "handworked_paper_feeding.txt"])
 def test_handworked_fixture(name, precision):
     cfg, init, steps = parse_fixture(os.path.join(GOLDEN, name))
     dtype = oracle.FISH_F32 if precision == "f32" else oracle.FISH_F64
@@ -404,8 +407,53 @@ def test_binary32_and_binary64_trajectories_stay_close():
     assert np.max(np.abs(s32["weight"] - s64["weight"])) < 0.25
 
 
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_weighted_swim_bounds_each_move_by_its_weight(precision):
+    """Swim mode 1: each coordinate's move is at most s * w / w0 (plus one
+    rounding), a fish of weight 0 never moves, and positions stay in the
+    pond."""
+    cfg = oracle.Config(n_fish=2000, seed=13, step=2.0, swim_mode=1, init_weight_mode=1,
+                        w0=4.0, w_max=8.0)
+    school = oracle.init(cfg, precision)
+    for t in range(1, 31):
+        before = school.copy()
+        oracle.run(cfg, school, t - 1, 1)
+        lim = cfg.step * before["weight"].astype(np.float64) / cfg.w0
+        for c in ("x", "y"):
+            mv = np.abs(school[c].astype(np.float64) - before[c].astype(np.float64))
+            assert np.all(mv <= lim * (1 + 1e-6) + 1e-5)
+            assert np.all(np.abs(school[c]) <= cfg.pond_half)
+        # the largest moves use most of the allowed width (uniform draws)
+        assert np.max(np.abs(school["x"].astype(np.float64) - before["x"]) / lim) > 0.9
+        frozen = before["weight"] == 0
+        assert np.array_equal(school["x"][frozen], before["x"][frozen])
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_paper_feeding_normaliser_is_the_eat_statistic(precision):
+    """Feed mode 1: the normaliser is the reported eat() value; when it is
+    positive the best improver's weight rises by exactly 1 (or hits the cap),
+    otherwise no weight changes."""
+    cfg = oracle.Config(n_fish=500, seed=17, step=1.0, feed_mode=1, w_max=1e9)
+    school = oracle.init(cfg, precision)
+    for t in range(1, 21):
+        before = school["weight"].copy()
+        st = oracle.run(cfg, school, t - 1, 1)[0]
+        g = school["prevObjective"] - school["currentObjective"]
+        assert st["eat_max_diff"] == np.max(g)
+        if st["eat_max_diff"] > 0:
+            best = np.argmax(g)
+            assert school["weight"][best] == before[best] + 1
+        else:
+            assert np.array_equal(school["weight"], before)
+
+
 def test_bad_configuration_is_rejected():
     with pytest.raises(ValueError):
         oracle.init(oracle.Config(n_fish=0))
     with pytest.raises(ValueError):
         oracle.init(oracle.Config(n_fish=4, w_min=2.0, w_max=1.0))
+    with pytest.raises(ValueError):
+        oracle.init(oracle.Config(n_fish=4, swim_mode=2))
+    with pytest.raises(ValueError):
+        oracle.init(oracle.Config(n_fish=4, feed_mode=3))
