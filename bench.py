@@ -49,7 +49,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["stream", "small", "resident", "batch", "precision"],
+    ap.add_argument("--workload", choices=["stream", "small", "resident", "batch", "precision",
+                                           "eat"],
                     default="stream")
     ap.add_argument("--batch-schools", type=int, default=None,
                     help="use only the first N schools of the batched ensemble")
@@ -411,6 +412,47 @@ def run_precision(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_eat(args, world, rank, local):
+    """The GPU analogue of the paper's Experiment 3 (reduction vs critical):
+    the eat() reduction max(prev - cur) over a school's state under each
+    reduction construct, timed with CUDA events (median of 5)."""
+    import torch
+
+    import paper_2507_20173_gb300 as fsb
+    from paper_2507_20173_gb300 import build as fsb_build
+
+    torch.cuda.set_device(local)
+    fsb_build.build()
+    fsb.lib()
+    n = args.n_fish or (1 << 26)
+    cfg = fsb.fsb_config_init(n, 2, path=fsb.FSB_PATH_STREAM)
+    s = fsb.School.create(cfg)
+    s.step(1)
+    st = s.read()
+    s.destroy()
+    prev = torch.from_numpy(st["prev"]).cuda()
+    cur = torch.from_numpy(st["cur"]).cuda()
+    del st
+    out = {}
+    for name, c in (("reduction", fsb.FSB_EAT_REDUCTION), ("per_warp", fsb.FSB_EAT_PER_WARP),
+                    ("critical", fsb.FSB_EAT_CRITICAL)):
+        times, val = [], None
+        for _ in range(6):
+            val, ms = fsb.fsb_eat_max(prev.data_ptr(), cur.data_ptr(), n, c)
+            times.append(ms)
+        t = statistics.median(times[1:])
+        out[name] = {"ms": t, "value": val, "GB_per_s": 8 * n / (t * 1e-3) / 1e9}
+    if rank == 0:
+        line = {"metric": "eat() reduction time per construct (paper Experiment 3 analogue)",
+                "value": out["reduction"]["ms"], "unit": "ms", "n_gpus": 1, "steps": 5,
+                "warmup": 1, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "eat() over N=%d fish (prev, cur of step 1, seed 2)" % n},
+                "constructs": out,
+                "critical_over_reduction": out["critical"]["ms"] / out["reduction"]["ms"]}
+        print(json.dumps(line), flush=True)
+
+
 def run_reference(args, world, rank):
     """The oracle as it stands, each bench step a bounded sample of the
     workload (2^22 fish of the same school rule, one step)."""
@@ -597,6 +639,8 @@ def main():
         run_batch(args, world, rank, local, pg)
     elif args.workload == "precision":
         run_precision(args, world, rank, local)
+    elif args.workload == "eat":
+        run_eat(args, world, rank, local)
     else:
         run_ours(args, world, rank, local, pg)
     if pg is not None:

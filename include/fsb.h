@@ -86,7 +86,16 @@ typedef enum {
  *                     (default 0.1; the paper gives no step size)
  *   w0, w_min, w_max  initial weight 1, floor 0, cap 2 (cap = 2 w0)
  *   precision         fsb_precision
- *   path              fsb_path (ignored by fsb_run_batch)                  */
+ *   path              fsb_path (ignored by fsb_run_batch)
+ *   swim_mode         0 (default): each coordinate moves by (2u - 1) * s;
+ *                     1: by (2u - 1) * ((w / w0) * s) with the fish's weight
+ *                     before the step's eat -- the paper's weight that
+ *                     "affects mobility" (Sec. 2.1.1, 2.1.2); a fish of
+ *                     weight 0 stays put.  Not on the resident path.
+ *   feed_mode         0 (default): w += delta / max|delta|;
+ *                     1: w += (prev - cur) / E with E = max(prev - cur), the
+ *                     value the paper's eat() reduces (Sec. 2.3.2); nobody
+ *                     eats when E <= 0                                     */
 typedef struct {
     uint64_t n_fish;
     uint64_t seed;
@@ -99,6 +108,8 @@ typedef struct {
     double   w_max;
     int32_t  precision;
     int32_t  path;
+    int32_t  swim_mode;
+    int32_t  feed_mode;
 } fsb_config;
 
 /* Per-fish state arrays on the device, structure of arrays, n_fish elements
@@ -330,6 +341,23 @@ int fsb_autotune(const fsb_config* cfg, uint32_t n_steps, int* best_path,
 int fsb_autotune_batch(const fsb_config* tmpl, uint32_t n_schools, const uint64_t* offsets,
                        const uint64_t* seeds, const fsb_state_dev* state, uint32_t n_steps,
                        int* best_cluster, double* best_fish_steps_per_s);
+
+/* The paper's eat() reduction on its own: *result = max over i < n of
+ * (prev_objective[i] - current_objective[i]) (binary32 device arrays,
+ * 16-byte aligned), computed with the chosen reduction construct -- the GPU
+ * analogue of the paper's Experiment 3, which times eat() under OpenMP
+ * `reduction(max:)` and under `critical` (Sec. 2.3.2, Sec. 3.4):
+ *   FSB_EAT_REDUCTION  hierarchical: warp shuffles, shared memory, one atomic
+ *                      per block
+ *   FSB_EAT_PER_WARP   one atomic per warp
+ *   FSB_EAT_CRITICAL   one atomic per fish on a single word (every update
+ *                      serialises on one address)
+ * All three are exact (max on order-preserving keys).  *device_ms (may be
+ * NULL) receives the device time of the reduction (CUDA events).
+ * Synchronises cuda_stream. */
+enum { FSB_EAT_REDUCTION = 0, FSB_EAT_PER_WARP = 1, FSB_EAT_CRITICAL = 2 };
+int fsb_eat_max(const void* prev_objective, const void* current_objective, uint64_t n,
+                int construct, double* result, float* device_ms, void* cuda_stream);
 
 /* Which single-school path a handle runs (fsb_path value), after AUTO is
  * resolved. */

@@ -33,6 +33,10 @@ FSB_FP32_KAHAN = 1
 FSB_FP64_ACC = 2
 FSB_FP64_STATE = 3
 
+FSB_EAT_REDUCTION = 0
+FSB_EAT_PER_WARP = 1
+FSB_EAT_CRITICAL = 2
+
 FSB_PATH_AUTO = 0
 FSB_PATH_STREAM = 1
 FSB_PATH_RESIDENT = 2
@@ -44,7 +48,7 @@ EXPORTED = ("fsb_config_init", "fsb_create", "fsb_step", "fsb_read_state",
             "fsb_set_tuning", "fsb_get_tuning", "fsb_batch_create", "fsb_batch_step",
             "fsb_batch_set_cluster", "fsb_batch_info", "fsb_batch_set_timing",
             "fsb_batch_kernel_time", "fsb_batch_destroy", "fsb_autotune",
-            "fsb_autotune_batch")
+            "fsb_autotune_batch", "fsb_eat_max")
 
 
 class FsbError(RuntimeError):
@@ -59,7 +63,8 @@ class FsbConfig(ctypes.Structure):
                 ("pond_half", ctypes.c_double), ("step", ctypes.c_double),
                 ("w0", ctypes.c_double), ("w_min", ctypes.c_double),
                 ("w_max", ctypes.c_double), ("precision", ctypes.c_int32),
-                ("path", ctypes.c_int32)]
+                ("path", ctypes.c_int32), ("swim_mode", ctypes.c_int32),
+                ("feed_mode", ctypes.c_int32)]
 
 
 class FsbStateDev(ctypes.Structure):
@@ -127,6 +132,8 @@ def lib() -> ctypes.CDLL:
         "fsb_batch_set_timing": [P, i32],
         "fsb_batch_kernel_time": [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u64)],
         "fsb_batch_destroy": [P],
+        "fsb_eat_max": [P, P, u64, i32, ctypes.POINTER(ctypes.c_double),
+                        ctypes.POINTER(ctypes.c_float), P],
         "fsb_autotune": [cfgp, u32, ctypes.POINTER(i32), ctypes.POINTER(FsbTuning),
                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u32)],
         "fsb_autotune_batch": [cfgp, u32, P, P, ctypes.POINTER(FsbStateDev), u32,
@@ -296,6 +303,16 @@ def fsb_batch_kernel_time(handle: int) -> tuple[float, int]:
 
 def fsb_batch_destroy(handle: int) -> None:
     _check(lib().fsb_batch_destroy(ctypes.c_void_p(handle)), "fsb_batch_destroy")
+
+
+def fsb_eat_max(prev_ptr: int, cur_ptr: int, n: int, construct: int = FSB_EAT_REDUCTION,
+                stream: int | None = None) -> tuple[float, float]:
+    """max(prev - cur) over device arrays; returns (value, device ms)."""
+    out, ms = ctypes.c_double(), ctypes.c_float()
+    _check(lib().fsb_eat_max(ctypes.c_void_p(prev_ptr), ctypes.c_void_p(cur_ptr), n, construct,
+                             ctypes.byref(out), ctypes.byref(ms), ctypes.c_void_p(stream or 0)),
+           "fsb_eat_max")
+    return out.value, ms.value
 
 
 def fsb_autotune(cfg: FsbConfig, n_steps: int) -> dict:

@@ -59,6 +59,12 @@ int validate_config(const fsb_config* c) {
     return fail(FSB_ERR_INVALID_ARG, "unknown precision %d", c->precision);
   if (c->path < FSB_PATH_AUTO || c->path > FSB_PATH_RESIDENT)
     return fail(FSB_ERR_INVALID_ARG, "unknown path %d", c->path);
+  if (c->swim_mode != 0 && c->swim_mode != 1)
+    return fail(FSB_ERR_INVALID_ARG, "swim_mode must be 0 or 1");
+  if (c->feed_mode != 0 && c->feed_mode != 1)
+    return fail(FSB_ERR_INVALID_ARG, "feed_mode must be 0 or 1");
+  if (c->swim_mode == 1 && !(c->w0 > 0.0))
+    return fail(FSB_ERR_INVALID_ARG, "the weight-scaled swim needs w0 > 0");
   return FSB_OK;
 }
 
@@ -499,6 +505,8 @@ int fsb_create(const fsb_config* cfg, const fsb_state_dev* buffers, const fsb_st
     L.w0 = cfg->w0;
     L.w_min = cfg->w_min;
     L.w_max = cfg->w_max;
+    L.swim_mode = cfg->swim_mode;
+    L.feed_mode = cfg->feed_mode;
     L.ctl = h->ctl;
     int sms = 0;
     FSB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
@@ -508,9 +516,14 @@ int fsb_create(const fsb_config* cfg, const fsb_state_dev* buffers, const fsb_st
     int r0 = configure_stream(h, 0, 0, 0, 0);
     if (r0 != FSB_OK) return r0;
 
-    // resident path: binary32 state that fits in registers across the SMs
+    // resident path: binary32 state that fits in registers across the SMs;
+    // its pipelined step swims ahead of the eat, so it runs the default swim
+    // only (the weight-scaled swim needs the step's eat first)
     fsb::ResidentLaunch& R = h->res;
-    const bool fits = !dbl && resident_config(sms, h->launch.acc, cfg->n_fish, &R);
+    if (cfg->path == FSB_PATH_RESIDENT && cfg->swim_mode != 0)
+      return fail(FSB_ERR_UNSUPPORTED, "resident path: the weight-scaled swim runs streaming");
+    const bool fits = !dbl && cfg->swim_mode == 0 &&
+                      resident_config(sms, h->launch.acc, cfg->n_fish, &R);
     if (cfg->path == FSB_PATH_RESIDENT && !fits)
       return fail(FSB_ERR_UNSUPPORTED,
                   "resident path: school of %llu fish does not fit on chip (binary32 only)",
@@ -529,6 +542,7 @@ int fsb_create(const fsb_config* cfg, const fsb_state_dev* buffers, const fsb_st
       R.w0 = cfg->w0;
       R.w_min = cfg->w_min;
       R.w_max = cfg->w_max;
+      R.feed_mode = cfg->feed_mode;
       R.acc = h->launch.acc;
       h->tuning.resident_fpt = R.fpt;
       h->tuning.resident_block = R.block;
@@ -682,6 +696,48 @@ int fsb_set_fault_injection(fsb_handle h, int block, uint32_t step, uint64_t tim
 int fsb_handle_path(fsb_handle h, int* path_out) {
   if (!h || !path_out) return fail(FSB_ERR_INVALID_ARG, "NULL argument");
   *path_out = h->path;
+  return FSB_OK;
+}
+
+int fsb_eat_max(const void* prev_objective, const void* current_objective, uint64_t n,
+                int construct, double* result, float* device_ms, void* cuda_stream) {
+  if (!prev_objective || !current_objective || !result)
+    return fail(FSB_ERR_INVALID_ARG, "NULL argument");
+  if (n == 0) return fail(FSB_ERR_INVALID_ARG, "n must be >= 1");
+  if (construct < FSB_EAT_REDUCTION || construct > FSB_EAT_CRITICAL)
+    return fail(FSB_ERR_INVALID_ARG, "unknown reduction construct %d", construct);
+  if (!aligned(prev_objective, 16) || !aligned(current_objective, 16))
+    return fail(FSB_ERR_INVALID_ARG, "arrays must be 16-byte aligned");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  int dev = 0, sms = 0;
+  FSB_CUDA(cudaGetDevice(&dev));
+  FSB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  unsigned* key = nullptr;
+  double* value = nullptr;
+  FSB_CUDA(cudaMallocAsync(&key, sizeof(unsigned), s));
+  FSB_CUDA(cudaMallocAsync(&value, sizeof(double), s));
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (device_ms) {
+    FSB_CUDA(cudaEventCreate(&a));
+    FSB_CUDA(cudaEventCreate(&b));
+    FSB_CUDA(cudaEventRecord(a, s));
+  }
+  const uint64_t want = (n / 4 + 255) / 256;
+  const uint64_t full = static_cast<uint64_t>(sms) * 8;
+  const int grid = static_cast<int>(want < 1 ? 1 : (want < full ? want : full));
+  cudaError_t e = fsb::launch_eat_max(static_cast<const float*>(prev_objective),
+                                      static_cast<const float*>(current_objective), n, construct,
+                                      key, value, grid, s);
+  if (device_ms && e == cudaSuccess) e = cudaEventRecord(b, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(result, value, sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (device_ms && e == cudaSuccess) e = cudaEventElapsedTime(device_ms, a, b);
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  cudaFreeAsync(key, s);
+  cudaFreeAsync(value, s);
+  FSB_CUDA(e);
   return FSB_OK;
 }
 

@@ -173,7 +173,7 @@ __device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int r
           const float old = f[q];
           spv[q][tid] = old;
           const Words4 r = fish_draw(key, school, i, t, kDomainSwim);
-          swim(x[q], y[q], r.v[0], r.v[1], a.ph);
+          swim(x[q], y[q], r.v[0], r.v[1], swim_width(a.ph, w[q]), a.ph);
           f[q] = objective(x[q], y[q]);
           const uint32_t mm = abs_bits(__fsub_rn(f[q], old));
           const uint32_t ee = order_key(__fsub_rn(old, f[q]));
@@ -234,6 +234,8 @@ __device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int r
     }
     if (!swim_step) break;
     const float M = __uint_as_float(*s_M);
+    // feeding normaliser: M_u, or the paper's eat() value E_u
+    const float N = a.ph.feed_mode ? key_to_value(*s_E, 0.f) : M;
     if (rank == 0 && tid == 0) {
       fsb_step_stats* st = a.stats + static_cast<uint64_t>(k) * a.n_steps + (u - 1);
       st->max_abs_delta = static_cast<double>(M);
@@ -244,7 +246,10 @@ __device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int r
 #pragma unroll
     for (int q = 0; q < kBatchFpt; ++q) {
       if (q < nq) {
-        if (M > 0.f) w[q] = eat(w[q], __fsub_rn(f[q], spv[q][tid]), M, a.ph);
+        if (N > 0.f)
+          w[q] = eat(w[q],
+                     a.ph.feed_mode ? __fsub_rn(spv[q][tid], f[q]) : __fsub_rn(f[q], spv[q][tid]),
+                     N, a.ph);
         acc.add(w[q], x[q], y[q]);
       }
     }
@@ -383,6 +388,8 @@ cudaError_t launch_batch(const BatchLaunch& L, cudaStream_t s, cudaStream_t side
   a.ph.w0 = static_cast<float>(L.w0);
   a.ph.w_min = static_cast<float>(L.w_min);
   a.ph.w_max = static_cast<float>(L.w_max);
+  a.ph.swim_mode = L.swim_mode;
+  a.ph.feed_mode = L.feed_mode;
   a.init = L.init;
   a.weight_mode = L.weight_mode;
   a.base_step_ptr = L.base_step;

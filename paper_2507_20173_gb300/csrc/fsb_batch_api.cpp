@@ -218,7 +218,10 @@ int fsb_batch_create(const fsb_config* tmpl, uint32_t n_schools, const uint64_t*
   if (tmpl->precision < FSB_FP32 || tmpl->precision > FSB_FP64_STATE)
     return bfail(FSB_ERR_INVALID_ARG, "unknown precision");
   if (!(tmpl->pond_half > 0.0) || !(tmpl->step >= 0.0) || !(tmpl->w_min <= tmpl->w_max) ||
-      (tmpl->init_weight_mode != 0 && tmpl->init_weight_mode != 1))
+      (tmpl->init_weight_mode != 0 && tmpl->init_weight_mode != 1) ||
+      (tmpl->swim_mode != 0 && tmpl->swim_mode != 1) ||
+      (tmpl->feed_mode != 0 && tmpl->feed_mode != 1) ||
+      (tmpl->swim_mode == 1 && !(tmpl->w0 > 0.0)))
     return bfail(FSB_ERR_INVALID_ARG, "invalid physics in the template configuration");
   if (offsets[0] != 0) return bfail(FSB_ERR_INVALID_ARG, "offsets[0] must be 0");
   uint64_t max_school = 0;
@@ -282,6 +285,8 @@ int fsb_batch_create(const fsb_config* tmpl, uint32_t n_schools, const uint64_t*
     L.w0 = tmpl->w0;
     L.w_min = tmpl->w_min;
     L.w_max = tmpl->w_max;
+    L.swim_mode = tmpl->swim_mode;
+    L.feed_mode = tmpl->feed_mode;
     L.acc = tmpl->precision == FSB_FP32 ? fsb::kAccPlain32
             : tmpl->precision == FSB_FP32_KAHAN ? fsb::kAccKahan32 : fsb::kAccF64;
     L.weight_mode = tmpl->init_weight_mode;

@@ -116,7 +116,17 @@ struct Physics {
   Real pond_half;  // P
   Real step;       // s
   Real w0, w_min, w_max;
+  int swim_mode;   // 0: half-width s; 1: (w / w0) * s
+  int feed_mode;   // 0: delta / max|delta|; 1: (prev - cur) / max(prev - cur)
 };
+
+// Half-width of one fish's move: s, or (w / w0) * s when the swim is
+// weight-scaled (the paper's weight that affects mobility).
+template <typename Real>
+__device__ __forceinline__ Real swim_width(const Physics<Real>& ph, Real w) {
+  using A = Arith<Real>;
+  return ph.swim_mode == 0 ? ph.step : A::mul(A::div(w, ph.w0), ph.step);
+}
 
 // Objective (Sec. 2.1.1): Euclidean distance to the pond centre (origin).
 template <typename Real>
@@ -125,20 +135,23 @@ __device__ __forceinline__ Real objective(Real x, Real y) {
   return A::sqrt(A::add(A::mul(x, x), A::mul(y, y)));
 }
 
-// Swim (Sec. 2.1.2): move each coordinate by (2u - 1) s, clamp to [-P, P].
+// Swim (Sec. 2.1.2): move each coordinate by (2u - 1) * width, clamp to
+// [-P, P].
 template <typename Real>
-__device__ __forceinline__ void swim(Real& x, Real& y, uint32_t r0, uint32_t r1,
+__device__ __forceinline__ void swim(Real& x, Real& y, uint32_t r0, uint32_t r1, Real width,
                                      const Physics<Real>& ph) {
   using A = Arith<Real>;
-  x = A::clamp(A::add(x, A::mul(A::centred(r0), ph.step)), -ph.pond_half, ph.pond_half);
-  y = A::clamp(A::add(y, A::mul(A::centred(r1), ph.step)), -ph.pond_half, ph.pond_half);
+  x = A::clamp(A::add(x, A::mul(A::centred(r0), width)), -ph.pond_half, ph.pond_half);
+  y = A::clamp(A::add(y, A::mul(A::centred(r1), width)), -ph.pond_half, ph.pond_half);
 }
 
-// Feeding: w <- clamp(w + delta / M, w_min, w_max) for M > 0.
+// Feeding: w <- clamp(w + g / N, w_min, w_max) for N > 0, with
+// (g, N) = (delta, max|delta|) or, when feeding follows the paper's eat()
+// value, (prev - cur, max(prev - cur)).
 template <typename Real>
-__device__ __forceinline__ Real eat(Real w, Real delta, Real M, const Physics<Real>& ph) {
+__device__ __forceinline__ Real eat(Real w, Real g, Real N, const Physics<Real>& ph) {
   using A = Arith<Real>;
-  return A::clamp(A::add(w, A::div(delta, M)), ph.w_min, ph.w_max);
+  return A::clamp(A::add(w, A::div(g, N)), ph.w_min, ph.w_max);
 }
 
 // Initial fish (Sec. 2.1.1): position uniform over the pond from init draw

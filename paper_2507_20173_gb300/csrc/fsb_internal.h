@@ -55,6 +55,7 @@ struct StreamLaunch {
   int min_blocks;   // vector kernel: blocks per SM its register budget guarantees
   int stages;       // bulk-copy kernel: tiles in flight per block (2, 3, 4; 0 = 2)
   double pond_half, step, w0, w_min, w_max;
+  int swim_mode, feed_mode;
   Ctl* ctl;
   BlockPartial* partials;
   fsb_step_stats* ring;
@@ -80,6 +81,7 @@ struct ResidentLaunch {
   uint64_t seed;
   uint32_t school;
   double pond_half, step, w0, w_min, w_max;
+  int feed_mode;    // the resident kernel runs only the default swim
   int acc;          // AccMode
   int fpt;          // fish per thread: 4, 8, 12 or 16
   int block;        // threads per block (<= resident_max_block(fpt))
@@ -119,6 +121,7 @@ struct BatchLaunch {
   uint32_t n_big;
   uint32_t n_schools;
   double pond_half, step, w0, w_min, w_max;
+  int swim_mode, feed_mode;
   int acc;
   int init;
   int weight_mode;
@@ -141,6 +144,11 @@ int batch_max_clusters(int cluster, int acc);
 uint64_t batch_block_capacity();
 int batch_threads();
 cudaError_t launch_bump_step(unsigned long long* base_step, uint32_t n, cudaStream_t s);
+
+// Reduction constructs of the stand-alone eat() reduction.
+enum EatConstruct : int { kEatHierarchical = 0, kEatPerWarp = 1, kEatPerFish = 2 };
+cudaError_t launch_eat_max(const float* prev, const float* cur, uint64_t n, int construct,
+                           unsigned* key, double* value, int grid, cudaStream_t s);
 
 // Record `msg` as the calling thread's fsb_last_error() detail; returns status.
 int record_error(int status, const char* msg);

@@ -97,7 +97,9 @@ extern "C" int fsb_step_static(const fsb_config* cfg, const fsb_state_dev* state
   if (!cfg || !state) return fail(FSB_ERR_INVALID_ARG, "fsb_step_static: NULL argument");
   if (cfg->n_fish == 0) return fail(FSB_ERR_INVALID_ARG, "fsb_step_static: n_fish must be >= 1");
   if (!(cfg->pond_half > 0.0) || !(cfg->step >= 0.0) || !(cfg->w_min <= cfg->w_max) ||
-      cfg->precision < FSB_FP32 || cfg->precision > FSB_FP64_STATE)
+      cfg->precision < FSB_FP32 || cfg->precision > FSB_FP64_STATE ||
+      (cfg->swim_mode != 0 && cfg->swim_mode != 1) || (cfg->feed_mode != 0 && cfg->feed_mode != 1) ||
+      (cfg->swim_mode == 1 && !(cfg->w0 > 0.0)))
     return fail(FSB_ERR_INVALID_ARG, "fsb_step_static: invalid configuration");
   if (n_steps == 0) return fail(FSB_ERR_INVALID_ARG, "fsb_step_static: n_steps must be >= 1");
   if (n_steps > kStaticMaxSteps)
@@ -141,6 +143,8 @@ extern "C" int fsb_step_static(const fsb_config* cfg, const fsb_state_dev* state
   L.w0 = cfg->w0;
   L.w_min = cfg->w_min;
   L.w_max = cfg->w_max;
+  L.swim_mode = cfg->swim_mode;
+  L.feed_mode = cfg->feed_mode;
   L.ctl = reinterpret_cast<Ctl*>(scratch);
   L.partials = reinterpret_cast<BlockPartial*>(scratch + kCtlBytes);
   L.ring = reinterpret_cast<fsb_step_stats*>(scratch + kCtlBytes + kPartialBytes);

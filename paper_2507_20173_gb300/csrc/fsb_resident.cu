@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(MAXB, 1) resident_kernel(ResidentArgs a) {
       if (k < nk) {
         pv[k] = f[k];
         const Words4 r = fish_draw(a.key, a.school, i, t, kDomainSwim);
-        swim(x[k], y[k], r.v[0], r.v[1], a.ph);
+        swim(x[k], y[k], r.v[0], r.v[1], a.ph.step, a.ph);
         f[k] = objective(x[k], y[k]);
         const float d = __fsub_rn(f[k], pv[k]);
         const uint32_t m = abs_bits(d);
@@ -202,14 +202,20 @@ __global__ void __launch_bounds__(MAXB, 1) resident_kernel(ResidentArgs a) {
     }
     __syncthreads();
     if (s_abort) return;
-    const float M = __uint_as_float(s_M);
+    // feeding normaliser: M_u, or the paper's eat() value E_u (then the
+    // numerator is prev - cur = -delta, exactly, and a zero delta gives the
+    // same weight either sign)
+    const float M = a.ph.feed_mode ? key_to_value(s_E, 0.f) : __uint_as_float(s_M);
 
     // ---- C: eat of step u and its barycentre partials
     Acc acc;
 #pragma unroll
     for (int k = 0; k < FPT; ++k) {
       if (k < nk) {
-        if (M > 0.f) w[k] = eat(w[k], P(u & 1u, 0, k), M, a.ph);
+        if (M > 0.f) {
+          const float d = P(u & 1u, 0, k);
+          w[k] = eat(w[k], a.ph.feed_mode ? -d : d, M, a.ph);
+        }
         acc.add(w[k], P(u & 1u, 1, k), P(u & 1u, 2, k));
       }
     }
@@ -395,6 +401,8 @@ cudaError_t launch_resident(const ResidentLaunch& L, cudaStream_t s) {
   a.ph.w0 = static_cast<float>(L.w0);
   a.ph.w_min = static_cast<float>(L.w_min);
   a.ph.w_max = static_cast<float>(L.w_max);
+  a.ph.swim_mode = 0;
+  a.ph.feed_mode = L.feed_mode;
   a.base_step = L.base_step;
   a.n_steps = L.n_steps;
   a.ctl = L.ctl;

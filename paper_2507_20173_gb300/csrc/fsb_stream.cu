@@ -55,10 +55,11 @@ __device__ __forceinline__ void vstore(Real* p, uint64_t g, const Real (&v)[VEC]
   reinterpret_cast<T*>(p)[g] = *reinterpret_cast<const T*>(v);
 }
 
-template <typename Real, int VEC, int PASS, int ACC, int BLOCK, int MINB>
+template <typename Real, int VEC, int PASS, int ACC, int BLOCK, int MINB, bool VAR>
 __global__ void __launch_bounds__(BLOCK, MINB) stream_pass_kernel(StreamArgs<Real> a) {
   using B = typename Bits<Real>::type;
   using Acc = SumAcc<ACC>;
+  const Physics<Real> ph = kernel_physics<VAR>(a.ph);
 
   uint32_t j;
   uint64_t base;
@@ -66,7 +67,9 @@ __global__ void __launch_bounds__(BLOCK, MINB) stream_pass_kernel(StreamArgs<Rea
   // a value that does not fit this call's sequence.
   if (!pass_prologue<PASS>(a.ctl, a.ctl, a.ring_cap, j, base)) return;
   Real M = Real(0);
-  if (PASS != kSwimOnly) M = static_cast<Real>(a.ring[j - 1].max_abs_delta);
+  if (PASS != kSwimOnly) M = feed_normaliser(a.ring[j - 1], ph);
+  // the weight-scaled swim needs the weights in the swim-only pass too
+  const bool load_w = PASS != kSwimOnly || ph.swim_mode != 0;
   const uint32_t t = static_cast<uint32_t>(base + j + 1);
 
   Acc acc;
@@ -79,16 +82,14 @@ __global__ void __launch_bounds__(BLOCK, MINB) stream_pass_kernel(StreamArgs<Rea
     Real x[VEC], y[VEC], w[VEC], pv[VEC];
     vload<Real, VEC>(x, a.x, g);
     vload<Real, VEC>(y, a.y, g);
-    if (PASS != kSwimOnly) {
-      vload<Real, VEC>(w, a.w, g);
-      vload<Real, VEC>(pv, a.pv, g);
-    }
+    if (load_w) vload<Real, VEC>(w, a.w, g);
+    if (PASS != kSwimOnly) vload<Real, VEC>(pv, a.pv, g);
     if constexpr (VEC == 4) {
-      fish_pass4<Real, PASS>(x, y, w, pv, g * VEC, M, t, a.key, a.school, a.ph, acc, maxb, ekey);
+      fish_pass4<Real, PASS>(x, y, w, pv, g * VEC, M, t, a.key, a.school, ph, acc, maxb, ekey);
     } else {
 #pragma unroll
       for (int v = 0; v < VEC; ++v)
-        fish_pass<Real, PASS>(x[v], y[v], w[v], pv[v], g * VEC + v, M, t, a.key, a.school, a.ph,
+        fish_pass<Real, PASS>(x[v], y[v], w[v], pv[v], g * VEC + v, M, t, a.key, a.school, ph,
                               acc, maxb, ekey);
     }
     if (PASS != kSettle) {
@@ -102,11 +103,9 @@ __global__ void __launch_bounds__(BLOCK, MINB) stream_pass_kernel(StreamArgs<Rea
     const uint64_t i = ngroups * VEC + tid;
     if (i < a.n) {
       Real x = a.x[i], y = a.y[i], w = Real(0), pv = Real(0);
-      if (PASS != kSwimOnly) {
-        w = a.w[i];
-        pv = a.pv[i];
-      }
-      fish_pass<Real, PASS>(x, y, w, pv, i, M, t, a.key, a.school, a.ph, acc, maxb, ekey);
+      if (load_w) w = a.w[i];
+      if (PASS != kSwimOnly) pv = a.pv[i];
+      fish_pass<Real, PASS>(x, y, w, pv, i, M, t, a.key, a.school, ph, acc, maxb, ekey);
       if (PASS != kSettle) {
         a.x[i] = x;
         a.y[i] = y;
@@ -145,53 +144,56 @@ __global__ void objective_kernel(const Real* __restrict__ x, const Real* __restr
 }
 
 template <typename Real, int VEC, int PASS, int ACC, int BLOCK, int MINB>
-const void* kernel_ptr() {
-  return reinterpret_cast<const void*>(&stream_pass_kernel<Real, VEC, PASS, ACC, BLOCK, MINB>);
+const void* kernel_ptr(bool var) {
+  if (var)
+    return reinterpret_cast<const void*>(&stream_pass_kernel<Real, VEC, PASS, ACC, BLOCK, MINB, true>);
+  return reinterpret_cast<const void*>(&stream_pass_kernel<Real, VEC, PASS, ACC, BLOCK, MINB, false>);
 }
 
 // Launch shapes: (256 threads, 1 / 3 / 4 blocks per SM guaranteed by the
 // register budget) for the binary32 vector kernel, (256 or 512, 1) otherwise.
 template <typename Real, int VEC, int PASS, int ACC>
-const void* pick_block(int block, int minb) {
+const void* pick_block(int block, int minb, bool var) {
   constexpr bool kHot = sizeof(Real) == 4 && VEC == 4;
   if (block == 256) {
-    if (minb <= 1) return kernel_ptr<Real, VEC, PASS, ACC, 256, 1>();
-    if (kHot && minb == 3) return kernel_ptr<Real, VEC, PASS, ACC, 256, kHot ? 3 : 1>();
-    if (kHot && minb == 4) return kernel_ptr<Real, VEC, PASS, ACC, 256, kHot ? 4 : 1>();
+    if (minb <= 1) return kernel_ptr<Real, VEC, PASS, ACC, 256, 1>(var);
+    if (kHot && minb == 3) return kernel_ptr<Real, VEC, PASS, ACC, 256, kHot ? 3 : 1>(var);
+    if (kHot && minb == 4) return kernel_ptr<Real, VEC, PASS, ACC, 256, kHot ? 4 : 1>(var);
     return nullptr;
   }
-  if (block == 512 && minb <= 1) return kernel_ptr<Real, VEC, PASS, ACC, 512, 1>();
+  if (block == 512 && minb <= 1) return kernel_ptr<Real, VEC, PASS, ACC, 512, 1>(var);
   return nullptr;
 }
 
 template <typename Real, int VEC, int PASS>
-const void* pick_acc(int acc, int block, int minb) {
-  if (sizeof(Real) == 8) return pick_block<Real, VEC, PASS, kAccF64>(block, minb);
+const void* pick_acc(int acc, int block, int minb, bool var) {
+  if (sizeof(Real) == 8) return pick_block<Real, VEC, PASS, kAccF64>(block, minb, var);
   switch (acc) {
-    case kAccPlain32: return pick_block<Real, VEC, PASS, kAccPlain32>(block, minb);
-    case kAccKahan32: return pick_block<Real, VEC, PASS, kAccKahan32>(block, minb);
-    case kAccF64: return pick_block<Real, VEC, PASS, kAccF64>(block, minb);
+    case kAccPlain32: return pick_block<Real, VEC, PASS, kAccPlain32>(block, minb, var);
+    case kAccKahan32: return pick_block<Real, VEC, PASS, kAccKahan32>(block, minb, var);
+    case kAccF64: return pick_block<Real, VEC, PASS, kAccF64>(block, minb, var);
     default: return nullptr;
   }
 }
 
 template <typename Real, int VEC>
-const void* pick_pass(int pass, int acc, int block, int minb) {
+const void* pick_pass(int pass, int acc, int block, int minb, bool var) {
   switch (pass) {
-    case kSwimOnly: return pick_acc<Real, VEC, kSwimOnly>(acc, block, minb);
-    case kFused: return pick_acc<Real, VEC, kFused>(acc, block, minb);
-    case kSettle: return pick_acc<Real, VEC, kSettle>(acc, block, minb);
+    case kSwimOnly: return pick_acc<Real, VEC, kSwimOnly>(acc, block, minb, var);
+    case kFused: return pick_acc<Real, VEC, kFused>(acc, block, minb, var);
+    case kSettle: return pick_acc<Real, VEC, kSettle>(acc, block, minb, var);
     default: return nullptr;
   }
 }
 
 const void* pick_kernel(const StreamLaunch& L, int pass) {
+  const bool var = L.swim_mode != 0 || L.feed_mode != 0;
   if (L.real_is_double) {
-    if (L.vec == 2) return pick_pass<double, 2>(pass, L.acc, L.block, L.min_blocks);
-    if (L.vec == 1) return pick_pass<double, 1>(pass, L.acc, L.block, L.min_blocks);
+    if (L.vec == 2) return pick_pass<double, 2>(pass, L.acc, L.block, L.min_blocks, var);
+    if (L.vec == 1) return pick_pass<double, 1>(pass, L.acc, L.block, L.min_blocks, var);
   } else {
-    if (L.vec == 4) return pick_pass<float, 4>(pass, L.acc, L.block, L.min_blocks);
-    if (L.vec == 1) return pick_pass<float, 1>(pass, L.acc, L.block, L.min_blocks);
+    if (L.vec == 4) return pick_pass<float, 4>(pass, L.acc, L.block, L.min_blocks, var);
+    if (L.vec == 1) return pick_pass<float, 1>(pass, L.acc, L.block, L.min_blocks, var);
   }
   return nullptr;
 }

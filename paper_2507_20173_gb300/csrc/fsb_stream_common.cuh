@@ -44,6 +44,8 @@ StreamArgs<Real> make_stream_args(const StreamLaunch& L) {
   a.ph.w0 = static_cast<Real>(L.w0);
   a.ph.w_min = static_cast<Real>(L.w_min);
   a.ph.w_max = static_cast<Real>(L.w_max);
+  a.ph.swim_mode = L.swim_mode;
+  a.ph.feed_mode = L.feed_mode;
   a.ctl = L.ctl;
   a.partials = L.partials;
   a.ring = L.ring;
@@ -65,27 +67,51 @@ __device__ __forceinline__ bool pass_prologue(const Ctl* ctl, Ctl* wctl, uint32_
   return true;
 }
 
+// The physics a pass kernel runs with.  The model variants (weight-scaled
+// swim, feeding normalised by max(prev - cur)) are read from the arguments
+// only by the kernels compiled for them (VAR); the default model's kernels
+// see constant zero modes, so their per-fish body carries no branch on them.
+template <bool VAR, typename Real>
+__device__ __forceinline__ Physics<Real> kernel_physics(const Physics<Real>& p) {
+  Physics<Real> ph = p;
+  if (!VAR) {
+    ph.swim_mode = 0;
+    ph.feed_mode = 0;
+  }
+  return ph;
+}
+
+// The feeding normaliser of step j from its statistics record: M_j, or the
+// paper's eat() value E_j when feeding follows it.
+template <typename Real>
+__device__ __forceinline__ Real feed_normaliser(const fsb_step_stats& rec,
+                                                const Physics<Real>& ph) {
+  return static_cast<Real>(ph.feed_mode ? rec.eat_max_diff : rec.max_abs_delta);
+}
+
 // One fish through one pass, without the barycentre accumulation: eat of
-// step j (kinds kFused / kSettle, with M = M_j), then swim + objective +
-// delta of the step `t` (kinds kSwimOnly / kFused).  The caller adds (w, x,
-// y) of step j to its sums between the two halves; see fish_pass below.
+// step j (kinds kFused / kSettle, with N = its feeding normaliser), then
+// swim + objective + delta of the step `t` (kinds kSwimOnly / kFused).  The
+// caller adds (w, x, y) of step j to its sums between the two halves; see
+// fish_pass below.
 template <typename Real, int PASS>
-__device__ __forceinline__ Real fish_eat(Real x, Real y, Real& w, Real pv, Real M,
+__device__ __forceinline__ Real fish_eat(Real x, Real y, Real& w, Real pv, Real N,
                                          const Physics<Real>& ph) {
   using A = Arith<Real>;
   const Real cur = objective(x, y);
-  if (PASS != kSwimOnly && M > Real(0)) w = eat(w, A::sub(cur, pv), M, ph);
+  if (PASS != kSwimOnly && N > Real(0))
+    w = eat(w, ph.feed_mode ? A::sub(pv, cur) : A::sub(cur, pv), N, ph);
   return cur;
 }
 
 template <typename Real, int PASS, typename B>
-__device__ __forceinline__ void fish_swim(Real& x, Real& y, Real& pv, Real cur, uint64_t i,
-                                          uint32_t t, Key key, uint32_t school,
+__device__ __forceinline__ void fish_swim(Real& x, Real& y, Real w, Real& pv, Real cur,
+                                          uint64_t i, uint32_t t, Key key, uint32_t school,
                                           const Physics<Real>& ph, B& maxb, B& ekey) {
   using A = Arith<Real>;
   if (PASS != kSettle) {
     const Words4 r = fish_draw(key, school, i, t, kDomainSwim);
-    swim(x, y, r.v[0], r.v[1], ph);
+    swim(x, y, r.v[0], r.v[1], swim_width(ph, w), ph);
     const Real ncur = objective(x, y);
     const B mb = abs_bits(A::sub(ncur, cur));
     const B ek = order_key(A::sub(cur, ncur));
@@ -103,7 +129,7 @@ __device__ __forceinline__ void fish_pass(Real& x, Real& y, Real& w, Real& pv, u
                                           const Physics<Real>& ph, Acc& acc, B& maxb, B& ekey) {
   const Real cur = fish_eat<Real, PASS>(x, y, w, pv, M, ph);
   if (PASS != kSwimOnly) acc.add(w, x, y);
-  fish_swim<Real, PASS>(x, y, pv, cur, i, t, key, school, ph, maxb, ekey);
+  fish_swim<Real, PASS>(x, y, w, pv, cur, i, t, key, school, ph, maxb, ekey);
 }
 
 // Four consecutive fish (one 16-byte vector of each array) through one
@@ -119,7 +145,8 @@ __device__ __forceinline__ void fish_pass4(Real (&x)[4], Real (&y)[4], Real (&w)
   if (PASS != kSwimOnly) acc.add4(w, x, y);
 #pragma unroll
   for (int q = 0; q < 4; ++q)
-    fish_swim<Real, PASS>(x[q], y[q], pv[q], cur[q], i0 + q, t, key, school, ph, maxb, ekey);
+    fish_swim<Real, PASS>(x[q], y[q], w[q], pv[q], cur[q], i0 + q, t, key, school, ph, maxb,
+                          ekey);
 }
 
 // Block reduction of the pass's maxima and sums into one partial per block;

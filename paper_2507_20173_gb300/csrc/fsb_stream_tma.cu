@@ -94,14 +94,15 @@ struct TmaRing {
   unsigned long long full[STAGES];  // one mbarrier per stage
 };
 
-template <int THREADS, int STAGES, int PASS, int ACC>
+template <int THREADS, int STAGES, int PASS, int ACC, bool VAR>
 __global__ void __launch_bounds__(THREADS) stream_pass_tma_kernel(StreamArgs<float> a) {
   using B = uint32_t;
   using Acc = SumAcc<ACC>;
+  const Physics<float> ph = kernel_physics<VAR>(a.ph);
   using Ring = TmaRing<THREADS, STAGES>;
   constexpr int kTile = THREADS * 4;
   constexpr unsigned kTileBytes = kTile * sizeof(float);
-  constexpr int kArrays = PASS == kSwimOnly ? 2 : 4;
+  // the swim-only pass needs x, y (and w for the weight-scaled swim)
 
   extern __shared__ __align__(128) unsigned char smem_raw[];
   Ring& R = *reinterpret_cast<Ring*>(smem_raw);
@@ -110,7 +111,8 @@ __global__ void __launch_bounds__(THREADS) stream_pass_tma_kernel(StreamArgs<flo
   uint64_t base;
   if (!pass_prologue<PASS>(a.ctl, a.ctl, a.ring_cap, j, base)) return;
   float M = 0.f;
-  if (PASS != kSwimOnly) M = static_cast<float>(a.ring[j - 1].max_abs_delta);
+  if (PASS != kSwimOnly) M = feed_normaliser(a.ring[j - 1], ph);
+  const int kArrays = PASS != kSwimOnly ? 4 : (ph.swim_mode != 0 ? 3 : 2);
   const uint32_t t = static_cast<uint32_t>(base + j + 1);
 
   const uint64_t n_tiles = a.n / kTile;
@@ -158,11 +160,13 @@ __global__ void __launch_bounds__(THREADS) stream_pass_tma_kernel(StreamArgs<flo
     float x[4] = {v[0].x, v[0].y, v[0].z, v[0].w};
     float y[4] = {v[1].x, v[1].y, v[1].z, v[1].w};
     float w[4], pv[4];
-    if (PASS != kSwimOnly) {
+    if (kArrays >= 3) {
       w[0] = v[2].x; w[1] = v[2].y; w[2] = v[2].z; w[3] = v[2].w;
+    }
+    if (PASS != kSwimOnly) {
       pv[0] = v[3].x; pv[1] = v[3].y; pv[2] = v[3].z; pv[3] = v[3].w;
     }
-    fish_pass4<float, PASS>(x, y, w, pv, g * 4, M, t, a.key, a.school, a.ph, acc, maxb, ekey);
+    fish_pass4<float, PASS>(x, y, w, pv, g * 4, M, t, a.key, a.school, ph, acc, maxb, ekey);
     if (PASS != kSettle) {
       reinterpret_cast<float4*>(a.x)[g] = make_float4(x[0], x[1], x[2], x[3]);
       reinterpret_cast<float4*>(a.y)[g] = make_float4(y[0], y[1], y[2], y[3]);
@@ -193,11 +197,9 @@ __global__ void __launch_bounds__(THREADS) stream_pass_tma_kernel(StreamArgs<flo
       const uint64_t i = n_tiles * kTile + threadIdx.x + static_cast<uint64_t>(q) * THREADS;
       if (i < a.n) {
         float x = a.x[i], y = a.y[i], w = 0.f, pv = 0.f;
-        if (PASS != kSwimOnly) {
-          w = a.w[i];
-          pv = a.pv[i];
-        }
-        fish_pass<float, PASS>(x, y, w, pv, i, M, t, a.key, a.school, a.ph, acc, maxb, ekey);
+        if (kArrays >= 3) w = a.w[i];
+        if (PASS != kSwimOnly) pv = a.pv[i];
+        fish_pass<float, PASS>(x, y, w, pv, i, M, t, a.key, a.school, ph, acc, maxb, ekey);
         if (PASS != kSettle) {
           a.x[i] = x;
           a.y[i] = y;
@@ -211,42 +213,45 @@ __global__ void __launch_bounds__(THREADS) stream_pass_tma_kernel(StreamArgs<flo
   pass_epilogue<float, PASS, ACC, THREADS>(a, acc, maxb, ekey, j, base);
 }
 
+template <int THREADS, int STAGES, int PASS, int ACC>
+const void* kernel_ptr(bool var) {
+  if (var)
+    return reinterpret_cast<const void*>(&stream_pass_tma_kernel<THREADS, STAGES, PASS, ACC, true>);
+  return reinterpret_cast<const void*>(&stream_pass_tma_kernel<THREADS, STAGES, PASS, ACC, false>);
+}
+
 template <int THREADS, int STAGES, int PASS>
-const void* pick_acc(int acc) {
+const void* pick_acc(int acc, bool var) {
   switch (acc) {
-    case kAccPlain32:
-      return reinterpret_cast<const void*>(&stream_pass_tma_kernel<THREADS, STAGES, PASS, kAccPlain32>);
-    case kAccKahan32:
-      return reinterpret_cast<const void*>(&stream_pass_tma_kernel<THREADS, STAGES, PASS, kAccKahan32>);
-    case kAccF64:
-      return reinterpret_cast<const void*>(&stream_pass_tma_kernel<THREADS, STAGES, PASS, kAccF64>);
-    default:
-      return nullptr;
+    case kAccPlain32: return kernel_ptr<THREADS, STAGES, PASS, kAccPlain32>(var);
+    case kAccKahan32: return kernel_ptr<THREADS, STAGES, PASS, kAccKahan32>(var);
+    case kAccF64: return kernel_ptr<THREADS, STAGES, PASS, kAccF64>(var);
+    default: return nullptr;
   }
 }
 
 template <int THREADS, int STAGES>
-const void* pick_pass(int pass, int acc) {
+const void* pick_pass(int pass, int acc, bool var) {
   switch (pass) {
-    case kSwimOnly: return pick_acc<THREADS, STAGES, kSwimOnly>(acc);
-    case kFused: return pick_acc<THREADS, STAGES, kFused>(acc);
-    case kSettle: return pick_acc<THREADS, STAGES, kSettle>(acc);
+    case kSwimOnly: return pick_acc<THREADS, STAGES, kSwimOnly>(acc, var);
+    case kFused: return pick_acc<THREADS, STAGES, kFused>(acc, var);
+    case kSettle: return pick_acc<THREADS, STAGES, kSettle>(acc, var);
     default: return nullptr;
   }
 }
 
 template <int THREADS>
-const void* pick_stages(int stages, int pass, int acc, size_t* smem) {
+const void* pick_stages(int stages, int pass, int acc, bool var, size_t* smem) {
   switch (stages) {
     case 2:
       *smem = sizeof(TmaRing<THREADS, 2>);
-      return pick_pass<THREADS, 2>(pass, acc);
+      return pick_pass<THREADS, 2>(pass, acc, var);
     case 3:
       *smem = sizeof(TmaRing<THREADS, 3>);
-      return pick_pass<THREADS, 3>(pass, acc);
+      return pick_pass<THREADS, 3>(pass, acc, var);
     case 4:
       *smem = sizeof(TmaRing<THREADS, 4>);
-      return pick_pass<THREADS, 4>(pass, acc);
+      return pick_pass<THREADS, 4>(pass, acc, var);
     default:
       return nullptr;
   }
@@ -255,9 +260,10 @@ const void* pick_stages(int stages, int pass, int acc, size_t* smem) {
 const void* pick(const StreamLaunch& L, int pass, size_t* smem) {
   if (L.real_is_double || L.vec != 4) return nullptr;
   const int stages = L.stages ? L.stages : 2;
+  const bool var = L.swim_mode != 0 || L.feed_mode != 0;
   switch (L.block) {
-    case 256: return pick_stages<256>(stages, pass, L.acc, smem);
-    case 512: return pick_stages<512>(stages, pass, L.acc, smem);
+    case 256: return pick_stages<256>(stages, pass, L.acc, var, smem);
+    case 512: return pick_stages<512>(stages, pass, L.acc, var, smem);
     default: return nullptr;
   }
 }

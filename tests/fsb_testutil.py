@@ -17,7 +17,8 @@ BARY_TOL = {fsb.FSB_FP32: 1e-3, fsb.FSB_FP32_KAHAN: 1e-5, fsb.FSB_FP64_ACC: 1e-1
 def oracle_config(cfg) -> oracle.Config:
     return oracle.Config(n_fish=cfg.n_fish, seed=cfg.seed, school_id=cfg.school_id,
                          init_weight_mode=cfg.init_weight_mode, pond_half=cfg.pond_half,
-                         step=cfg.step, w0=cfg.w0, w_min=cfg.w_min, w_max=cfg.w_max)
+                         step=cfg.step, w0=cfg.w0, w_min=cfg.w_min, w_max=cfg.w_max,
+                         swim_mode=cfg.swim_mode, feed_mode=cfg.feed_mode)
 
 
 def oracle_precision(cfg) -> str:

@@ -37,7 +37,8 @@ def read_state(ts):
 def oracle_school(tmpl, n, seed, school_id, steps, **kw):
     cfg = oracle.Config(n_fish=int(n), seed=int(seed), school_id=int(school_id),
                         init_weight_mode=tmpl.init_weight_mode, pond_half=tmpl.pond_half,
-                        step=tmpl.step, w0=tmpl.w0, w_min=tmpl.w_min, w_max=tmpl.w_max)
+                        step=tmpl.step, w0=tmpl.w0, w_min=tmpl.w_min, w_max=tmpl.w_max,
+                        swim_mode=tmpl.swim_mode, feed_mode=tmpl.feed_mode)
     school = oracle.init(cfg)
     stats = oracle.run(cfg, school, 0, steps) if steps else None
     return school, stats
