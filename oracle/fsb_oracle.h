@@ -59,8 +59,9 @@ typedef struct {
 void fsbo_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
                         uint32_t out[4]);
 
-/* The raw swim words (r0, r1) of fish i at step t (t >= 1), and the raw
- * init words (r0, r1, r2) of fish i. */
+/* The raw swim words (r0, r1) of fish i at step t (t >= 1): words
+ * 2 (i % 2) and 2 (i % 2) + 1 of the block of fish pair i / 2.  The raw
+ * init words (r0, r1, r2) of fish i: words 0, 1, 2 of its own block. */
 void fsbo_swim_words(const fsbo_config* cfg, uint64_t i, uint32_t t,
                      uint32_t out[2]);
 void fsbo_init_words(const fsbo_config* cfg, uint64_t i, uint32_t out[3]);

@@ -10,8 +10,8 @@
  *
  * The counter and key layout used by the fish school (which words carry the
  * fish index, school, step and domain) is the reading taken for the paper's
- * unnamed random number generator (Sec. 2.1.1, Sec. 2.1.2); it lives in
- * fsb_oracle.c.
+ * unnamed random number generator (Sec. 2.1.1, Sec. 2.1.2); it is
+ * fish_counter below.
  */
 #include "fsb_oracle.h"
 
@@ -39,9 +39,10 @@ void fsbo_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-/* Counter layout (reading of the unnamed RNG): word 0 = fish index low 32
- * bits, word 1 = fish index high 32 bits XOR school id, word 2 = step,
- * word 3 = domain (0 = swim, 1 = initialisation).  Key = seed. */
+/* Counter layout (reading of the unnamed RNG): word 0 = index low 32 bits,
+ * word 1 = index high 32 bits XOR school id, word 2 = step, word 3 = domain
+ * (0 = swim, 1 = initialisation).  Key = seed.  The index is the fish for
+ * the initialisation draws and the fish pair i / 2 for the swim draws. */
 static void fish_counter(const fsbo_config* cfg, uint64_t i, uint32_t step,
                          uint32_t domain, uint32_t ctr[4], uint32_t key[2])
 {
@@ -53,14 +54,17 @@ static void fish_counter(const fsbo_config* cfg, uint64_t i, uint32_t step,
     key[1] = (uint32_t)(cfg->seed >> 32);
 }
 
+/* One swim draw serves a pair of neighbouring fish: fish 2p moves with
+ * words 0 and 1 of the pair's block, fish 2p + 1 with words 2 and 3. */
 void fsbo_swim_words(const fsbo_config* cfg, uint64_t i, uint32_t t,
                      uint32_t out[2])
 {
     uint32_t ctr[4], key[2], r[4];
-    fish_counter(cfg, i, t, 0u, ctr, key);
+    const unsigned half = (unsigned)(i & 1u);
+    fish_counter(cfg, i >> 1, t, 0u, ctr, key);
     fsbo_philox4x32_10(ctr, key, r);
-    out[0] = r[0];
-    out[1] = r[1];
+    out[0] = r[2 * half];
+    out[1] = r[2 * half + 1];
 }
 
 void fsbo_init_words(const fsbo_config* cfg, uint64_t i, uint32_t out[3])
