@@ -284,7 +284,8 @@ bool resident_config(int sms, int acc, uint64_t n, fsb::ResidentLaunch* R, int w
     uint64_t grid = (n + per_block - 1) / per_block;
     if (grid > static_cast<uint64_t>(sms)) continue;
     if (grid < 1) grid = 1;
-    const uint64_t slice = (n + grid - 1) / grid;
+    // even, so no fish pair (one swim block) straddles two blocks
+    const uint64_t slice = ((n + grid - 1) / grid + 1) & ~1ull;
     const uint64_t threads = (slice + fpt - 1) / fpt;
     const int block = static_cast<int>(((threads + 31) / 32) * 32);
     if (block > maxb) continue;

@@ -115,7 +115,7 @@ __device__ __forceinline__ void block_reduce(BlockReduce<ACC>& R, uint32_t& m, u
 // Runs one school on `nb` blocks (this block is rank `rank`): load or
 // initialise, all steps, write back.  For nb > 1 the caller's cluster must
 // contain exactly nb blocks that all call this with the same school.
-template <int ACC>
+template <int ACC, bool VAR>
 __device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int rank, int nb,
                                            BlockReduce<ACC>& R,
                                            ClusterPartial<typename SumAcc<ACC>::Part> (*xchg)[kMaxCluster],
@@ -127,14 +127,23 @@ __device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int r
   const uint64_t s_lo = a.offsets[k];
   // in-school fish indices fit 32 bits (schools hold at most C * 8192 fish)
   const uint32_t n = static_cast<uint32_t>(a.offsets[k + 1] - s_lo);
-  const uint32_t slice = (n + nb - 1) / nb;
+  // an even slice keeps each fish pair (one swim block) in one thread
+  const uint32_t slice = ((n + nb - 1) / nb + 1) & ~1u;
   const uint32_t lo = static_cast<uint32_t>(rank) * slice;
   const uint32_t hi = lo + slice < n ? lo + slice : n;
-  // this thread's fish are i0 + q * kBatchThreads for q < nq
-  const uint32_t i0 = lo + tid;
-  const int nq = i0 < hi ? static_cast<int>((hi - i0 + kBatchThreads - 1) / kBatchThreads) : 0;
+  // slot q of this thread is fish lo + 2 (tid + (q / 2) kBatchThreads) + q % 2
+  // (in-school index); slots q < nq are in the school
+  auto fish = [&](int q) -> uint32_t {
+    return lo + 2u * (static_cast<uint32_t>(tid) + static_cast<uint32_t>(q >> 1) * kBatchThreads) +
+           static_cast<uint32_t>(q & 1);
+  };
+  int nq = 0;
+#pragma unroll
+  for (int q = 0; q < kBatchFpt; ++q)
+    if (fish(q) < hi) nq = q + 1;
   const Key key{static_cast<uint32_t>(a.seeds[k]), static_cast<uint32_t>(a.seeds[k] >> 32)};
   const uint32_t school = k;
+  const Physics<float> ph = kernel_physics<VAR>(a.ph);
   cg::cluster_group cluster = cg::this_cluster();
 
   // prevObjective of each fish waits in shared memory (spv[q][tid]); the
@@ -142,10 +151,10 @@ __device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int r
   float x[kBatchFpt], y[kBatchFpt], w[kBatchFpt], f[kBatchFpt];
 #pragma unroll
   for (int q = 0; q < kBatchFpt; ++q) {
-    const uint32_t i = i0 + q * kBatchThreads;  // index in school
+    const uint32_t i = fish(q);  // index in school
     if (q < nq) {
       if (a.init) {
-        init_fish(key, school, i, a.weight_mode, a.ph, x[q], y[q], w[q]);
+        init_fish(key, school, i, a.weight_mode, ph, x[q], y[q], w[q]);
       } else {
         x[q] = a.x[s_lo + i];
         y[q] = a.y[s_lo + i];
@@ -166,14 +175,14 @@ __device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int r
     uint32_t mb = 0, ek = 0;
     if (swim_step) {
       const uint32_t t = static_cast<uint32_t>(*a.base_step_ptr + u);
+      Words4 r{};
 #pragma unroll
       for (int q = 0; q < kBatchFpt; ++q) {
-        const uint32_t i = i0 + q * kBatchThreads;
         if (q < nq) {
           const float old = f[q];
           spv[q][tid] = old;
-          const Words4 r = fish_draw(key, school, i, t, kDomainSwim);
-          swim(x[q], y[q], r.v[0], r.v[1], swim_width(a.ph, w[q]), a.ph);
+          if ((q & 1) == 0) r = pair_draw(key, school, fish(q) >> 1, t);
+          swim(x[q], y[q], r.v[2 * (q & 1)], r.v[2 * (q & 1) + 1], swim_width(ph, w[q]), ph);
           f[q] = objective(x[q], y[q]);
           const uint32_t mm = abs_bits(__fsub_rn(f[q], old));
           const uint32_t ee = order_key(__fsub_rn(old, f[q]));
@@ -235,7 +244,7 @@ __device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int r
     if (!swim_step) break;
     const float M = __uint_as_float(*s_M);
     // feeding normaliser: M_u, or the paper's eat() value E_u
-    const float N = a.ph.feed_mode ? key_to_value(*s_E, 0.f) : M;
+    const float N = ph.feed_mode ? key_to_value(*s_E, 0.f) : M;
     if (rank == 0 && tid == 0) {
       fsb_step_stats* st = a.stats + static_cast<uint64_t>(k) * a.n_steps + (u - 1);
       st->max_abs_delta = static_cast<double>(M);
@@ -248,8 +257,8 @@ __device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int r
       if (q < nq) {
         if (N > 0.f)
           w[q] = eat(w[q],
-                     a.ph.feed_mode ? __fsub_rn(spv[q][tid], f[q]) : __fsub_rn(f[q], spv[q][tid]),
-                     N, a.ph);
+                     ph.feed_mode ? __fsub_rn(spv[q][tid], f[q]) : __fsub_rn(f[q], spv[q][tid]),
+                     N, ph);
         acc.add(w[q], x[q], y[q]);
       }
     }
@@ -261,7 +270,7 @@ __device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int r
 
 #pragma unroll
   for (int q = 0; q < kBatchFpt; ++q) {
-    const uint32_t i = i0 + q * kBatchThreads;
+    const uint32_t i = fish(q);
     if (q < nq) {
       a.x[s_lo + i] = x[q];
       a.y[s_lo + i] = y[q];
@@ -271,7 +280,7 @@ __device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int r
   }
 }
 
-template <int CLUSTER, int ACC>
+template <int CLUSTER, int ACC, bool VAR>
 __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs a) {
   __shared__ BlockReduce<ACC> R;
   __shared__ ClusterPartial<typename SumAcc<ACC>::Part> xchg[2][kMaxCluster];
@@ -302,27 +311,35 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs a) {
       __syncthreads();
       if (idx >= a.n_schools) break;
     }
-    run_school<ACC>(a, a.order[idx], whole_cluster ? rank : 0, whole_cluster ? CLUSTER : 1, R,
+    run_school<ACC, VAR>(a, a.order[idx], whole_cluster ? rank : 0, whole_cluster ? CLUSTER : 1, R,
                     xchg, &s_M, &s_E, spv);
   }
 }
 
+template <int CLUSTER, int ACC>
+const void* kernel_ptr(bool var) {
+  if (var) return reinterpret_cast<const void*>(&batch_kernel<CLUSTER, ACC, true>);
+  return reinterpret_cast<const void*>(&batch_kernel<CLUSTER, ACC, false>);
+}
+
 template <int CLUSTER>
-const void* pick_acc(int acc) {
+const void* pick_acc(int acc, bool var) {
   switch (acc) {
-    case kAccPlain32: return reinterpret_cast<const void*>(&batch_kernel<CLUSTER, kAccPlain32>);
-    case kAccKahan32: return reinterpret_cast<const void*>(&batch_kernel<CLUSTER, kAccKahan32>);
-    case kAccF64: return reinterpret_cast<const void*>(&batch_kernel<CLUSTER, kAccF64>);
+    case kAccPlain32: return kernel_ptr<CLUSTER, kAccPlain32>(var);
+    case kAccKahan32: return kernel_ptr<CLUSTER, kAccKahan32>(var);
+    case kAccF64: return kernel_ptr<CLUSTER, kAccF64>(var);
     default: return nullptr;
   }
 }
 
-const void* pick(int cluster, int acc) {
+// The variant kernels (var) share the default ones' block, register bound
+// and shared memory, hence their occupancy.
+const void* pick(int cluster, int acc, bool var = false) {
   switch (cluster) {
-    case 1: return pick_acc<1>(acc);
-    case 2: return pick_acc<2>(acc);
-    case 4: return pick_acc<4>(acc);
-    case 8: return pick_acc<8>(acc);
+    case 1: return pick_acc<1>(acc, var);
+    case 2: return pick_acc<2>(acc, var);
+    case 4: return pick_acc<4>(acc, var);
+    case 8: return pick_acc<8>(acc, var);
     default: return nullptr;
   }
 }
@@ -370,8 +387,9 @@ int batch_max_clusters(int cluster, int acc) {
 
 cudaError_t launch_batch(const BatchLaunch& L, cudaStream_t s, cudaStream_t side,
                          cudaEvent_t fork, cudaEvent_t join) {
-  const void* fn = pick(L.cluster, L.acc);
-  const void* fill = pick(1, L.acc);
+  const bool var = L.swim_mode != 0 || L.feed_mode != 0;
+  const void* fn = pick(L.cluster, L.acc, var);
+  const void* fill = pick(1, L.acc, var);
   if (!fn || !fill || L.n_clusters < 1) return cudaErrorInvalidValue;
   BatchArgs a;
   a.x = static_cast<float*>(L.x);

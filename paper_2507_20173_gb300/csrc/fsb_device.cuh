@@ -52,9 +52,11 @@ __device__ __forceinline__ Words4 philox4x32_10(uint32_t c0, uint32_t c1, uint32
 }
 
 // Counter layout of the school's draws (reading of the paper's unnamed
-// generator, Sec. 2.1.1 / Sec. 2.1.2): word 0 = fish index low 32 bits,
-// word 1 = fish index high 32 bits XOR school id, word 2 = step t,
-// word 3 = domain (0 swim, 1 initialisation).  Key = seed.
+// generator, Sec. 2.1.1 / Sec. 2.1.2): word 0 = index low 32 bits, word 1 =
+// index high 32 bits XOR school id, word 2 = step t, word 3 = domain (0
+// swim, 1 initialisation).  Key = seed.  The initialisation index is the
+// fish; the swim index is the fish pair i / 2, whose block of four words
+// moves both fish (words 0, 1 for fish 2p, words 2, 3 for fish 2p + 1).
 constexpr uint32_t kDomainSwim = 0u;
 constexpr uint32_t kDomainInit = 1u;
 
@@ -66,6 +68,22 @@ __device__ __forceinline__ Words4 fish_draw(Key key, uint32_t school, uint64_t i
                                             uint32_t domain) {
   return philox4x32_10(static_cast<uint32_t>(i), static_cast<uint32_t>(i >> 32) ^ school, t,
                        domain, key.k0, key.k1);
+}
+
+// The swim block of fish pair p at step t.
+__device__ __forceinline__ Words4 pair_draw(Key key, uint32_t school, uint64_t p, uint32_t t) {
+  return fish_draw(key, school, p, t, kDomainSwim);
+}
+
+// The two swim words of one fish, from its pair's block.
+struct Words2 {
+  uint32_t r0, r1;
+};
+
+__device__ __forceinline__ Words2 fish_swim_words(Key key, uint32_t school, uint64_t i,
+                                                  uint32_t t) {
+  const Words4 r = pair_draw(key, school, i >> 1, t);
+  return (i & 1u) ? Words2{r.v[2], r.v[3]} : Words2{r.v[0], r.v[1]};
 }
 
 // ------------------------------------------------------- real arithmetic --
@@ -119,6 +137,20 @@ struct Physics {
   int swim_mode;   // 0: half-width s; 1: (w / w0) * s
   int feed_mode;   // 0: delta / max|delta|; 1: (prev - cur) / max(prev - cur)
 };
+
+// The physics a kernel runs with.  The model variants (weight-scaled
+// swim, feeding normalised by max(prev - cur)) are read from the arguments
+// only by the kernels compiled for them (VAR); the default model's kernels
+// see constant zero modes, so their per-fish body carries no branch on them.
+template <bool VAR, typename Real>
+__device__ __forceinline__ Physics<Real> kernel_physics(const Physics<Real>& p) {
+  Physics<Real> ph = p;
+  if (!VAR) {
+    ph.swim_mode = 0;
+    ph.feed_mode = 0;
+  }
+  return ph;
+}
 
 // Half-width of one fish's move: s, or (w / w0) * s when the swim is
 // weight-scaled (the paper's weight that affects mobility).

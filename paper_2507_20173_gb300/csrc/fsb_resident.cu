@@ -88,11 +88,19 @@ __global__ void __launch_bounds__(MAXB, 1) resident_kernel(ResidentArgs a) {
   const int lane = tid & 31, warp = tid >> 5;
   const bool multi = gridDim.x > 1;
   // a resident school holds at most ~2.5 million fish, so indices fit 32
-  // bits; this thread's fish are i0 + k * B for k < nk
+  // bits.  The thread owns fish pairs (one swim block moves a pair): slot k
+  // is fish lo + 2 (tid + (k / 2) B) + k % 2, and slots k < nk are in the
+  // school (the slice, hence lo, is even)
   const uint32_t lo = static_cast<uint32_t>(blockIdx.x * a.slice);
   const uint32_t hi = static_cast<uint32_t>(lo + a.slice < a.n ? lo + a.slice : a.n);
-  const uint32_t i0 = lo + tid;
-  const int nk = i0 < hi ? static_cast<int>((hi - i0 + B - 1) / B) : 0;
+  auto fish = [&](int k) -> uint32_t {
+    return lo + 2u * (static_cast<uint32_t>(tid) + static_cast<uint32_t>(k >> 1) * B) +
+           static_cast<uint32_t>(k & 1);
+  };
+  int nk = 0;
+#pragma unroll
+  for (int k = 0; k < FPT; ++k)
+    if (fish(k) < hi) nk = k + 1;
   auto P = [&](uint32_t buf, int q, int k) -> float& {
     return pend[((buf * 3 + q) * FPT + k) * B + tid];
   };
@@ -100,7 +108,7 @@ __global__ void __launch_bounds__(MAXB, 1) resident_kernel(ResidentArgs a) {
   float x[FPT], y[FPT], w[FPT], f[FPT], pv[FPT];
 #pragma unroll
   for (int k = 0; k < FPT; ++k) {
-    const uint32_t i = i0 + k * B;
+    const uint32_t i = fish(k);
     if (k < nk) {
       x[k] = a.x[i];
       y[k] = a.y[i];
@@ -119,13 +127,13 @@ __global__ void __launch_bounds__(MAXB, 1) resident_kernel(ResidentArgs a) {
     const uint32_t t = static_cast<uint32_t>(a.base_step + u);
     mb = 0;
     ek = 0;
+    Words4 r{};
 #pragma unroll
     for (int k = 0; k < FPT; ++k) {
-      const uint32_t i = i0 + k * B;
       if (k < nk) {
         pv[k] = f[k];
-        const Words4 r = fish_draw(a.key, a.school, i, t, kDomainSwim);
-        swim(x[k], y[k], r.v[0], r.v[1], a.ph.step, a.ph);
+        if ((k & 1) == 0) r = pair_draw(a.key, a.school, fish(k) >> 1, t);
+        swim(x[k], y[k], r.v[2 * (k & 1)], r.v[2 * (k & 1) + 1], a.ph.step, a.ph);
         f[k] = objective(x[k], y[k]);
         const float d = __fsub_rn(f[k], pv[k]);
         const uint32_t m = abs_bits(d);
@@ -260,7 +268,7 @@ __global__ void __launch_bounds__(MAXB, 1) resident_kernel(ResidentArgs a) {
   // ---- write the state back
 #pragma unroll
   for (int k = 0; k < FPT; ++k) {
-    const uint32_t i = i0 + k * B;
+    const uint32_t i = fish(k);
     if (k < nk) {
       a.x[i] = x[k];
       a.y[i] = y[k];

@@ -86,6 +86,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) stream_pass_kernel(StreamArgs<Rea
     if (PASS != kSwimOnly) vload<Real, VEC>(pv, a.pv, g);
     if constexpr (VEC == 4) {
       fish_pass4<Real, PASS>(x, y, w, pv, g * VEC, M, t, a.key, a.school, ph, acc, maxb, ekey);
+    } else if constexpr (VEC == 2) {
+      fish_pass2<Real, PASS>(x, y, w, pv, g * VEC, M, t, a.key, a.school, ph, acc, maxb, ekey);
     } else {
 #pragma unroll
       for (int v = 0; v < VEC; ++v)

@@ -67,20 +67,6 @@ __device__ __forceinline__ bool pass_prologue(const Ctl* ctl, Ctl* wctl, uint32_
   return true;
 }
 
-// The physics a pass kernel runs with.  The model variants (weight-scaled
-// swim, feeding normalised by max(prev - cur)) are read from the arguments
-// only by the kernels compiled for them (VAR); the default model's kernels
-// see constant zero modes, so their per-fish body carries no branch on them.
-template <bool VAR, typename Real>
-__device__ __forceinline__ Physics<Real> kernel_physics(const Physics<Real>& p) {
-  Physics<Real> ph = p;
-  if (!VAR) {
-    ph.swim_mode = 0;
-    ph.feed_mode = 0;
-  }
-  return ph;
-}
-
 // The feeding normaliser of step j from its statistics record: M_j, or the
 // paper's eat() value E_j when feeding follows it.
 template <typename Real>
@@ -106,12 +92,11 @@ __device__ __forceinline__ Real fish_eat(Real x, Real y, Real& w, Real pv, Real 
 
 template <typename Real, int PASS, typename B>
 __device__ __forceinline__ void fish_swim(Real& x, Real& y, Real w, Real& pv, Real cur,
-                                          uint64_t i, uint32_t t, Key key, uint32_t school,
-                                          const Physics<Real>& ph, B& maxb, B& ekey) {
+                                          uint32_t r0, uint32_t r1, const Physics<Real>& ph,
+                                          B& maxb, B& ekey) {
   using A = Arith<Real>;
   if (PASS != kSettle) {
-    const Words4 r = fish_draw(key, school, i, t, kDomainSwim);
-    swim(x, y, r.v[0], r.v[1], swim_width(ph, w), ph);
+    swim(x, y, r0, r1, swim_width(ph, w), ph);
     const Real ncur = objective(x, y);
     const B mb = abs_bits(A::sub(ncur, cur));
     const B ek = order_key(A::sub(cur, ncur));
@@ -129,11 +114,34 @@ __device__ __forceinline__ void fish_pass(Real& x, Real& y, Real& w, Real& pv, u
                                           const Physics<Real>& ph, Acc& acc, B& maxb, B& ekey) {
   const Real cur = fish_eat<Real, PASS>(x, y, w, pv, M, ph);
   if (PASS != kSwimOnly) acc.add(w, x, y);
-  fish_swim<Real, PASS>(x, y, w, pv, cur, i, t, key, school, ph, maxb, ekey);
+  Words2 r{0u, 0u};
+  if (PASS != kSettle) r = fish_swim_words(key, school, i, t);
+  fish_swim<Real, PASS>(x, y, w, pv, cur, r.r0, r.r1, ph, maxb, ekey);
 }
 
-// Four consecutive fish (one 16-byte vector of each array) through one
-// pass, with their barycentre contributions added as one group.
+// Two fish of one pair (i0 even) through one pass: one swim block moves both.
+template <typename Real, int PASS, typename Acc, typename B>
+__device__ __forceinline__ void fish_pass2(Real (&x)[2], Real (&y)[2], Real (&w)[2],
+                                           Real (&pv)[2], uint64_t i0, Real M, uint32_t t,
+                                           Key key, uint32_t school, const Physics<Real>& ph,
+                                           Acc& acc, B& maxb, B& ekey) {
+  Real cur[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    cur[q] = fish_eat<Real, PASS>(x[q], y[q], w[q], pv[q], M, ph);
+    if (PASS != kSwimOnly) acc.add(w[q], x[q], y[q]);
+  }
+  Words4 r{};
+  if (PASS != kSettle) r = pair_draw(key, school, i0 >> 1, t);
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+    fish_swim<Real, PASS>(x[q], y[q], w[q], pv[q], cur[q], r.v[2 * q], r.v[2 * q + 1], ph, maxb,
+                          ekey);
+}
+
+// Four consecutive fish (one 16-byte vector of each array, i0 a multiple of
+// four) through one pass, with their barycentre contributions added as one
+// group; two swim blocks move the two pairs.
 template <typename Real, int PASS, typename Acc, typename B>
 __device__ __forceinline__ void fish_pass4(Real (&x)[4], Real (&y)[4], Real (&w)[4],
                                            Real (&pv)[4], uint64_t i0, Real M, uint32_t t,
@@ -143,10 +151,15 @@ __device__ __forceinline__ void fish_pass4(Real (&x)[4], Real (&y)[4], Real (&w)
 #pragma unroll
   for (int q = 0; q < 4; ++q) cur[q] = fish_eat<Real, PASS>(x[q], y[q], w[q], pv[q], M, ph);
   if (PASS != kSwimOnly) acc.add4(w, x, y);
+  Words4 r[2] = {};
+  if (PASS != kSettle) {
+    r[0] = pair_draw(key, school, i0 >> 1, t);
+    r[1] = pair_draw(key, school, (i0 >> 1) + 1, t);
+  }
 #pragma unroll
   for (int q = 0; q < 4; ++q)
-    fish_swim<Real, PASS>(x[q], y[q], w[q], pv[q], cur[q], i0 + q, t, key, school, ph, maxb,
-                          ekey);
+    fish_swim<Real, PASS>(x[q], y[q], w[q], pv[q], cur[q], r[q >> 1].v[2 * (q & 1)],
+                          r[q >> 1].v[2 * (q & 1) + 1], ph, maxb, ekey);
 }
 
 // Block reduction of the pass's maxima and sums into one partial per block;

@@ -40,6 +40,14 @@ __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// Orders this thread's earlier shared-memory accesses (generic proxy) before
+// later accesses through the async proxy, such as a bulk copy that refills
+// the stage the thread has just read.  A CTA barrier alone orders generic
+// accesses among the CTA's threads, not against the copy engine.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 __device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                "r"(bytes)
@@ -150,7 +158,9 @@ __global__ void __launch_bounds__(THREADS) stream_pass_tma_kernel(StreamArgs<flo
     for (int q = 0; q < 4; ++q)
       if (q < kArrays) v[q] = R.buf[s][q][threadIdx.x];
     // every thread has its data (or the block gives up together): release
-    // the stage and refill it with the tile STAGES ahead
+    // the stage and refill it with the tile STAGES ahead.  The proxy fence
+    // keeps the refill's writes behind this thread's reads of the stage.
+    fence_proxy_async_smem();
     ok = __syncthreads_and(mine) != 0;
     if (!ok) break;
     if (threadIdx.x == 0 && k + STAGES < my_tiles) issue(k + STAGES);
