@@ -61,8 +61,10 @@ def parse_args():
     ap.add_argument("--n-fish", type=int, default=None,
                     help="override the school size (profiling on a smaller case)")
     ap.add_argument("--stream-kernel", type=int, default=0,
-                    help="0 library choice, 1 vector loads, 2 bulk-copy ring")
+                    help="0 library choice, 1 vector loads, 2 bulk-copy ring, "
+                         "3 warp-specialised bulk-copy ring")
     ap.add_argument("--stream-block", type=int, default=0)
+    ap.add_argument("--stream-stages", type=int, default=0)
     ap.add_argument("--reference-fish", type=int, default=1 << 22,
                     help="fish per bench step of the CPU reference arm")
     ap.add_argument("--no-e2e", action="store_true")
@@ -112,33 +114,48 @@ def measured_peaks():
 def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2507_20173_gb300", "csrc")
-    for name in ("fsb_stream.cu", "fsb_stream_tma.cu", "fsb_stream_common.cuh",
-                 "fsb_device.cuh", "fsb_reduce.cuh"):
+    for name in ("fsb_stream.cu", "fsb_stream_tma.cu", "fsb_stream_ws.cu", "fsb_bulk_copy.cuh",
+                 "fsb_stream_common.cuh", "fsb_device.cuh", "fsb_reduce.cuh"):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def resident_source_hash():
+# Sources of the two on-chip kernels, whose roofline is instruction issue.
+ALU_KERNEL_SOURCES = {
+    "resident": ("fsb_resident.cu", "fsb_device.cuh", "fsb_reduce.cuh"),
+    "batch": ("fsb_batch.cu", "fsb_device.cuh", "fsb_reduce.cuh"),
+}
+
+
+def alu_source_hash(kernel):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2507_20173_gb300", "csrc")
-    for name in ("fsb_resident.cu", "fsb_device.cuh", "fsb_reduce.cuh"):
+    for name in ALU_KERNEL_SOURCES[kernel]:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def resident_instr_per_fish_step(precision):
-    """Lane instructions per fish-step of the resident kernel from the
-    committed ncu summary; None if the kernel changed since."""
-    p = os.path.join(ROOT, "profiles", "resident_instr.json")
+def alu_instr_per_fish_step(kernel, precision):
+    """Lane instructions per fish-step of the resident or batch kernel from
+    the committed ncu summary (profiles/<kernel>_instr.json); None if the
+    kernel changed since or the precision differs."""
+    p = os.path.join(ROOT, "profiles", "%s_instr.json" % kernel)
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
-    if d.get("kernel_source_hash") != resident_source_hash() or d.get("precision") != precision:
+    if d.get("kernel_source_hash") != alu_source_hash(kernel) or d.get("precision") != precision:
         return None
     return float(d["lane_instr_per_fish_step"])
+
+
+def issue_peak(sms, clocks):
+    """Lane-instructions per second the SMs can issue: 4 schedulers x 32
+    lanes per SM per clock, at the median SM clock seen in the timed region."""
+    mhz = clocks.get("sm_mhz") or 2070.0
+    return sms * 4 * 32 * mhz * 1e6 / 1e9
 
 
 def ncu_traffic(n_fish, precision):
@@ -307,6 +324,16 @@ def run_batch(args, world, rank, local, pg):
                       "what": "one fsb_step(T) launch per school on the single-school "
                               "path (library's choice: resident), serially on one stream"}
     clocks = clk.summary()
+    ipfs = alu_instr_per_fish_step("batch", args.precision)
+    avg_s = (kms / kl) / 1e3 if kl else None
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    roof = {"bound": "alu", "kernel": "batch_kernel", "launches": kl,
+            "avg_launch_ms": avg_s * 1e3 if avg_s else None,
+            "fish_steps_per_launch": total * steps, "lane_instr_per_fish_step": ipfs,
+            "achieved": total * steps / avg_s * ipfs / 1e9 if (avg_s and ipfs) else None,
+            "peak": issue_peak(sms, clocks), "unit": "Glane-instr/s", "traffic": None,
+            "peak_source": "issue peak %d SMs x 128 lanes x measured median SM clock" % sms}
+    roof["frac"] = roof["achieved"] / roof["peak"] if roof["achieved"] else None
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": steps, "warmup": warmup, "ms_per_step": ms_max / steps,
@@ -319,10 +346,7 @@ def run_batch(args, world, rank, local, pg):
                            "l2": "state %.2f GB; each school's state stays on chip for the call"
                                  % (16 * total / 1e9),
                            "parallelism": "replicas x%d" % world},
-                "roofline": {"bound": "alu", "kernel": "batch_kernel", "launches": kl,
-                             "avg_launch_ms": kms / kl if kl else None, "achieved": None,
-                             "peak": None, "frac": None, "traffic": None,
-                             "unit": "Glane-instr/s"},
+                "roofline": roof,
                 "per_school": per_school,
                 "batched_over_per_school": (value / world) / per_school["value"]
                 if per_school else None,
@@ -510,7 +534,8 @@ def run_ours(args, world, rank, local, pg):
             pg.barrier()
         torch.cuda.synchronize()
 
-    tuning = {"stream_kernel": args.stream_kernel, "stream_block": args.stream_block}
+    tuning = {"stream_kernel": args.stream_kernel, "stream_block": args.stream_block,
+              "stream_stages": args.stream_stages}
 
     # ---- device-resident timing
     school = fsb.School.create(cfg, stream=stream)
@@ -542,7 +567,7 @@ def run_ours(args, world, rank, local, pg):
     if path == fsb.FSB_PATH_RESIDENT:
         # one launch advances all `steps` steps with the state on chip: bound
         # by instruction issue, 152 SMs x 4 schedulers x 32 lanes per clock
-        ipfs = resident_instr_per_fish_step(args.precision)
+        ipfs = alu_instr_per_fish_step("resident", args.precision)
         fish_steps_per_launch = n * steps
         rate = fish_steps_per_launch / avg_fused_s if avg_fused_s else None
         roof = {"bound": "alu", "unit": "Glane-instr/s", "kernel": "resident_kernel",
@@ -559,8 +584,9 @@ def run_ours(args, world, rank, local, pg):
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
                 "peak_source": peak_kind + " hbm_gbs (STREAM copy)",
-                "kernel": ("stream_pass_tma_kernel<fused>" if tuning["stream_kernel"] == 2
-                           else "stream_pass_kernel<fused>"), "launches": fused_n,
+                "kernel": {1: "stream_pass_kernel<fused>", 2: "stream_pass_tma_kernel<fused>",
+                           3: "stream_pass_ws_kernel<fused>"}[tuning["stream_kernel"]],
+                "launches": fused_n,
                 "avg_launch_ms": avg_fused_s * 1e3 if avg_fused_s else None,
                 "algorithmic_bytes_per_launch": bytes_per_fish_step * n}
 
@@ -582,8 +608,9 @@ def run_ours(args, world, rank, local, pg):
         barrier()
         t0 = time.perf_counter()
         h = fsb.fsb_create(cfg, bufs, host, 0, stream.cuda_stream)
-        if args.stream_kernel or args.stream_block:
-            fsb.fsb_set_tuning(h, stream_kernel=args.stream_kernel, stream_block=args.stream_block)
+        if args.stream_kernel or args.stream_block or args.stream_stages:
+            fsb.fsb_set_tuning(h, stream_kernel=args.stream_kernel, stream_block=args.stream_block,
+                               stream_stages=args.stream_stages)
         fsb.fsb_step(h, steps, stats)
         fsb.fsb_read_state(h, *(outs[k].numpy() for k in ("x", "y", "w", "prev", "cur")))
         e2e_s = time.perf_counter() - t0
@@ -608,8 +635,7 @@ def run_ours(args, world, rank, local, pg):
     clocks = clk.summary()
     if roof.get("bound") == "alu":
         sms = roof.pop("_sms")
-        mhz = clocks.get("sm_mhz") or 2070.0
-        roof["peak"] = sms * 4 * 32 * mhz * 1e6 / 1e9
+        roof["peak"] = issue_peak(sms, clocks)
         roof["frac"] = roof["achieved"] / roof["peak"] if roof.get("achieved") else None
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,

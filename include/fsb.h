@@ -298,15 +298,18 @@ int fsb_set_fault_injection(fsb_handle h, int block, uint32_t step, uint64_t tim
  * results do not depend on it except for the rounding of the barycentre
  * sums, whose reduction tree follows the grid.
  *   stream_kernel        1: vector loads; 2: bulk asynchronous copies into a
- *                        shared-memory ring (binary32, 16-byte aligned state)
+ *                        shared-memory ring (binary32, 16-byte aligned state);
+ *                        3: the same ring run by its own producer warp, stages
+ *                        released per consumer warp (binary32, aligned state)
  *   stream_block         threads per block of the streaming pass: 256 or 512
+ *                        (kernel 3: consumer threads; the block has 32 more)
  *   stream_blocks_per_sm blocks per SM of the streaming grid (capped by
  *                        occupancy)
  *   resident_fpt         fish per thread of the resident kernel: 4, 8, 12, 16
  *   resident_block       threads per block of the resident kernel (multiple
  *                        of 32, at most the variant's compiled maximum)
- *   stream_stages        bulk-copy kernel: shared-memory tiles in flight per
- *                        block, 2, 3 or 4
+ *   stream_stages        bulk-copy kernels: shared-memory tiles in flight per
+ *                        block, 2, 3 or 4 (kernel 3: 2 or 3)
  * A combination that cannot run returns FSB_ERR_INVALID_ARG and leaves the
  * handle unchanged.  Synchronises the handle's stream. */
 typedef struct {

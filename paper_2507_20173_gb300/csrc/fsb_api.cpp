@@ -153,7 +153,9 @@ int ensure_ring(fsb_school* h, uint32_t n) {
 }
 
 int launch_pass(fsb_school* h, int kind, cudaStream_t s) {
-  if (h->launch.tma)
+  if (h->launch.tma == 2)
+    FSB_CUDA(fsb::launch_stream_pass_ws(h->launch, kind, s));
+  else if (h->launch.tma)
     FSB_CUDA(fsb::launch_stream_pass_tma(h->launch, kind, s));
   else
     FSB_CUDA(fsb::launch_stream_pass(h->launch, kind, s));
@@ -310,13 +312,15 @@ int configure_stream(fsb_school* h, int kernel, int block, int blocks_per_sm, in
   if (kernel == 0) kernel = tma_ok ? 2 : 1;
   if (stages == 0) stages = 2;
   if (stages < 2 || stages > 4) return fail(FSB_ERR_INVALID_ARG, "stream stages must be 2..4");
-  if (kernel == 2 && !tma_ok)
-    return fail(FSB_ERR_INVALID_ARG, "bulk-copy kernel needs binary32, 16-byte aligned state");
-  if (kernel != 1 && kernel != 2) return fail(FSB_ERR_INVALID_ARG, "unknown stream kernel");
-  if (block == 0) block = kernel == 2 ? 512 : 256;
+  if ((kernel == 2 || kernel == 3) && !tma_ok)
+    return fail(FSB_ERR_INVALID_ARG, "bulk-copy kernels need binary32, 16-byte aligned state");
+  if (kernel < 1 || kernel > 3) return fail(FSB_ERR_INVALID_ARG, "unknown stream kernel");
+  if (kernel == 3 && stages > 3)
+    return fail(FSB_ERR_INVALID_ARG, "warp-specialised ring: stages must be 2 or 3");
+  if (block == 0) block = kernel == 1 ? 256 : 512;
   if (blocks_per_sm == 0 && kernel == 1 && block == 256) blocks_per_sm = 4;
   if (block != 256 && block != 512) return fail(FSB_ERR_INVALID_ARG, "stream block must be 256/512");
-  L.tma = kernel == 2 ? 1 : 0;
+  L.tma = kernel - 1;
   L.block = block;
   L.stages = stages;
   // the vector kernel is compiled for 1, 3 or 4 guaranteed blocks per SM
@@ -326,7 +330,10 @@ int configure_stream(fsb_school* h, int kernel, int block, int blocks_per_sm, in
       (blocks_per_sm == 3 || blocks_per_sm == 4))
     L.min_blocks = blocks_per_sm;
   int per_sm = 0;
-  if (L.tma) {
+  if (L.tma == 2) {
+    FSB_CUDA(fsb::stream_ws_prepare(L));
+    per_sm = fsb::stream_ws_blocks_per_sm(L);
+  } else if (L.tma) {
     FSB_CUDA(fsb::stream_tma_prepare(L));
     per_sm = fsb::stream_tma_blocks_per_sm(L);
   } else {

@@ -81,15 +81,16 @@ extern "C" int fsb_autotune(const fsb_config* cfg, uint32_t n_steps, int* best_p
       cands.push_back(c);
     }
   if (!dbl)
-    for (int b : blocks)
-      for (int st = 2; st <= 4; ++st) {  // bulk-copy ring
-        Candidate c{};
-        c.path = FSB_PATH_STREAM;
-        c.t.stream_kernel = 2;
-        c.t.stream_block = b;
-        c.t.stream_stages = st;
-        cands.push_back(c);
-      }
+    for (int k = 2; k <= 3; ++k)  // bulk-copy ring, block-synchronised or warp-specialised
+      for (int b : blocks)
+        for (int st = 2; st <= (k == 2 ? 4 : 3); ++st) {
+          Candidate c{};
+          c.path = FSB_PATH_STREAM;
+          c.t.stream_kernel = k;
+          c.t.stream_block = b;
+          c.t.stream_stages = st;
+          cands.push_back(c);
+        }
   if (!dbl) {
     const int fpts[] = {4, 8, 12, 16};
     for (int f : fpts) {

@@ -51,7 +51,8 @@ struct StreamLaunch {
   int vec;          // 1 or vector width
   int block;        // threads per block
   int grid;         // blocks
-  int tma;          // 1: bulk-copy ring kernel (fsb_stream_tma.cu)
+  int tma;          // 1: bulk-copy ring (fsb_stream_tma.cu); 2: warp-specialised
+                    //    ring (fsb_stream_ws.cu)
   int min_blocks;   // vector kernel: blocks per SM its register budget guarantees
   int stages;       // bulk-copy kernel: tiles in flight per block (2, 3, 4; 0 = 2)
   double pond_half, step, w0, w_min, w_max;
@@ -68,6 +69,11 @@ bool stream_tma_supported(const StreamLaunch& L);
 cudaError_t stream_tma_prepare(const StreamLaunch& L);
 int stream_tma_blocks_per_sm(const StreamLaunch& L);
 cudaError_t launch_stream_pass_tma(const StreamLaunch& L, int pass_kind, cudaStream_t s);
+// Warp-specialised ring (fsb_stream_ws.cu): L.block consumer threads plus one
+// producer warp per block; stages 2 or 3.
+cudaError_t stream_ws_prepare(const StreamLaunch& L);
+int stream_ws_blocks_per_sm(const StreamLaunch& L);
+cudaError_t launch_stream_pass_ws(const StreamLaunch& L, int pass_kind, cudaStream_t s);
 cudaError_t launch_init(const StreamLaunch& L, int weight_mode, cudaStream_t s);
 cudaError_t launch_objective(const StreamLaunch& L, void* cur, cudaStream_t s);
 // Launch description of the resident single-school kernel (binary32 state).

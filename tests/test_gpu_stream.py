@@ -120,7 +120,8 @@ def test_unaligned_buffers_take_the_scalar_path(precision):
 # (kernel, block, blocks per SM, stages): vector loads with 1 / 3 / 4
 # guaranteed blocks per SM, bulk-copy ring with 2 / 3 / 4 stages
 VARIANTS = [(1, 256, 0, 0), (1, 256, 3, 0), (1, 256, 4, 0), (1, 512, 0, 0),
-            (2, 256, 0, 2), (2, 256, 0, 3), (2, 256, 0, 4), (2, 512, 0, 2), (2, 512, 0, 4)]
+            (2, 256, 0, 2), (2, 256, 0, 3), (2, 256, 0, 4), (2, 512, 0, 2), (2, 512, 0, 4),
+            (3, 256, 0, 2), (3, 256, 0, 3), (3, 512, 0, 2), (3, 512, 0, 3), (3, 512, 1, 2)]
 
 
 @pytest.mark.parametrize("kernel,block,per_sm,stages", VARIANTS)
@@ -164,12 +165,24 @@ def test_autotuner_choice_reproduces_the_oracle():
     assert_stats_match(stats, ref_stats, cfg.precision, "autotuned")
 
 
-def test_bulk_copy_kernel_needs_binary32_aligned_state():
+@pytest.mark.parametrize("kernel", [2, 3])
+def test_bulk_copy_kernel_needs_binary32_aligned_state(kernel):
     s = fsb.School.create(stream_cfg(1000, 1, precision=fsb.FSB_FP64_STATE))
     with pytest.raises(fsb.FsbError) as e:
-        fsb.fsb_set_tuning(s.handle, stream_kernel=2)
+        fsb.fsb_set_tuning(s.handle, stream_kernel=kernel)
     assert e.value.status == fsb.FSB_ERR_INVALID_ARG
     assert fsb.fsb_get_tuning(s.handle)["stream_kernel"] == 1
+    s.destroy()
+
+
+def test_warp_specialised_ring_takes_two_or_three_stages():
+    s = fsb.School.create(stream_cfg(5000, 1))
+    with pytest.raises(fsb.FsbError) as e:
+        fsb.fsb_set_tuning(s.handle, stream_kernel=3, stream_stages=4)
+    assert e.value.status == fsb.FSB_ERR_INVALID_ARG
+    fsb.fsb_set_tuning(s.handle, stream_kernel=3, stream_stages=3)
+    t = fsb.fsb_get_tuning(s.handle)
+    assert (t["stream_kernel"], t["stream_stages"]) == (3, 3)
     s.destroy()
 
 
@@ -312,10 +325,10 @@ def test_full_size_stream_school_sampled():
     assert abs(stats["sum_wx"][-1] - ref_x) / abs_x <= BARY_TOL[cfg.precision]
 
 
-@pytest.mark.parametrize("stages", [2, 3])
-def test_full_size_launch_shapes_agree_bitwise(stages):
+@pytest.mark.parametrize("kernel,stages", [(2, 2), (2, 3), (3, 2), (3, 3)])
+def test_full_size_launch_shapes_agree_bitwise(kernel, stages):
     """The per-fish state is exact whatever the launch shape, so at the
-    benchmark's size (N = 2^28, seed 2) the bulk-copy ring kernel and the
+    benchmark's size (N = 2^28, seed 2) the bulk-copy ring kernels and the
     vector-load kernel must leave the same bits in every fish after 100
     steps, with the same exact maxima; a stage refilled before all of its
     reads were performed would show up here as a handful of moved fish."""
@@ -324,9 +337,9 @@ def test_full_size_launch_shapes_agree_bitwise(stages):
     if free < 12 * (1 << 30):
         pytest.skip("needs ~12 GB of free device memory")
     out = []
-    for kernel, block, st in ((2, 512, stages), (1, 256, 2)):
+    for k, block, st in ((kernel, 512, stages), (1, 256, 2)):
         s = fsb.School.create(stream_cfg(n, seed))
-        fsb.fsb_set_tuning(s.handle, stream_kernel=kernel, stream_block=block, stream_stages=st)
+        fsb.fsb_set_tuning(s.handle, stream_kernel=k, stream_block=block, stream_stages=st)
         stats = s.step(steps, stats=True)
         state = [t.clone() for t in s.tensors]
         s.destroy()

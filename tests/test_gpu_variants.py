@@ -44,7 +44,7 @@ def run_and_compare(cfg, steps, tuning=None, calls=None):
 
 
 @pytest.mark.parametrize("swim_mode,feed_mode", MODES)
-@pytest.mark.parametrize("kernel,block", [(1, 256), (2, 512), (2, 256)])
+@pytest.mark.parametrize("kernel,block", [(1, 256), (2, 512), (2, 256), (3, 512)])
 @pytest.mark.parametrize("n", [7, 4099, 100_003])
 def test_streaming_variants(swim_mode, feed_mode, kernel, block, n):
     cfg = fsb.fsb_config_init(n, 77 + n, path=fsb.FSB_PATH_STREAM, swim_mode=swim_mode,
