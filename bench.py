@@ -68,6 +68,8 @@ def parse_args():
     ap.add_argument("--reference-fish", type=int, default=1 << 22,
                     help="fish per bench step of the CPU reference arm")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-runs", type=int, default=3,
+                    help="end-to-end runs; the median is reported")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
 
@@ -605,22 +607,33 @@ def run_ours(args, world, rank, local, pg):
         bufs = fsb.FsbStateDev(*(d.data_ptr() for d in dev))
         host = fsb.FsbStateHost(*(pin[k].data_ptr() for k in ("x", "y", "w", "prev")))
         stats = np.zeros(steps, fsb.STATS_DTYPE)
-        barrier()
-        t0 = time.perf_counter()
-        h = fsb.fsb_create(cfg, bufs, host, 0, stream.cuda_stream)
-        if args.stream_kernel or args.stream_block or args.stream_stages:
-            fsb.fsb_set_tuning(h, stream_kernel=args.stream_kernel, stream_block=args.stream_block,
-                               stream_stages=args.stream_stages)
-        fsb.fsb_step(h, steps, stats)
-        fsb.fsb_read_state(h, *(outs[k].numpy() for k in ("x", "y", "w", "prev", "cur")))
-        e2e_s = time.perf_counter() - t0
-        fsb.fsb_destroy(h)
-        e2e_s = reduce_max(e2e_s, pg)
-        e2e = {"value": world * n * steps / e2e_s, "unit": UNIT,
+        runs = []
+        for _ in range(args.e2e_runs):
+            barrier()
+            t0 = time.perf_counter()
+            h = fsb.fsb_create(cfg, bufs, host, 0, stream.cuda_stream)
+            if args.stream_kernel or args.stream_block or args.stream_stages:
+                fsb.fsb_set_tuning(h, stream_kernel=args.stream_kernel,
+                                   stream_block=args.stream_block,
+                                   stream_stages=args.stream_stages)
+            stream.synchronize()  # the state's host->device copies are in
+            t1 = time.perf_counter()
+            fsb.fsb_step(h, steps, stats)
+            t2 = time.perf_counter()
+            fsb.fsb_read_state(h, *(outs[k].numpy() for k in ("x", "y", "w", "prev", "cur")))
+            t3 = time.perf_counter()
+            fsb.fsb_destroy(h)
+            runs.append((reduce_max(t3 - t0, pg), 1e3 * (t1 - t0), 1e3 * (t2 - t1),
+                         1e3 * (t3 - t2)))
+        med = sorted(runs)[len(runs) // 2]
+        e2e = {"value": world * n * steps / med[0], "unit": UNIT,
                "h2d_bytes_per_step": int(4 * elem * n / steps),
                "d2h_bytes_per_step": int((5 * elem * n + 40 * steps) / steps),
                "what": "fsb_create from pinned host state + fsb_step(K) with host stats + "
-                       "fsb_read_state to pinned host, wall clock"}
+                       "fsb_read_state to pinned host, wall clock; median of %d runs"
+                       % len(runs),
+               "runs_s": [r[0] for r in runs],
+               "phases_ms": {"create_h2d": med[1], "step": med[2], "read_d2h": med[3]}}
         del pin, outs, dev
 
     # ---- CPU oracle baseline (rank 0, N = 1 only)

@@ -119,6 +119,8 @@ struct fsb_school {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
   double fused_ms = 0.0;
   uint64_t fused_launches = 0;
+  void* cur_stage = nullptr;       // two chunks of currentObjective for fsb_read_state
+  uint64_t cur_chunk = 0;          // fish per chunk
 };
 
 namespace {
@@ -302,6 +304,8 @@ bool resident_config(int sms, int acc, uint64_t n, fsb::ResidentLaunch* R, int w
 }
 
 constexpr int kMaxPartialsPerSm = 8;
+// fsb_read_state computes currentObjective in chunks of this many fish
+constexpr uint64_t kCurChunk = 1ull << 22;
 
 // Streaming launch shape: kernel variant, block, grid.  Invalidates graphs.
 int configure_stream(fsb_school* h, int kernel, int block, int blocks_per_sm, int stages) {
@@ -413,6 +417,7 @@ void release(fsb_school* h) {
   cudaFree(h->sums);
   cudaFree(h->partials);
   cudaFree(h->ring);
+  cudaFree(h->cur_stage);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
 }
@@ -619,13 +624,21 @@ int fsb_read_state(fsb_handle h, void* x, void* y, void* w, void* prev_objective
   if (prev_objective)
     FSB_CUDA(cudaMemcpyAsync(prev_objective, h->pv, bytes, cudaMemcpyDeviceToHost, h->stream));
   if (current_objective) {
-    void* cur = nullptr;
-    FSB_CUDA(cudaMallocAsync(&cur, bytes, h->stream));
-    cudaError_t e = fsb::launch_objective(h->launch, cur, h->stream);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(current_objective, cur, bytes, cudaMemcpyDeviceToHost, h->stream);
-    cudaFreeAsync(cur, h->stream);
-    FSB_CUDA(e);
+    // computed chunk by chunk into two alternating device buffers, each chunk
+    // copied out behind its kernel (stream order keeps a buffer's copy ahead
+    // of its next kernel), so the read needs no full-size scratch
+    const uint64_t n = h->cfg.n_fish;
+    if (!h->cur_stage) {
+      h->cur_chunk = n < kCurChunk ? n : kCurChunk;
+      FSB_CUDA(cudaMalloc(&h->cur_stage, 2 * h->cur_chunk * h->elem));
+    }
+    for (uint64_t first = 0, c = 0; first < n; first += h->cur_chunk, ++c) {
+      const uint64_t count = n - first < h->cur_chunk ? n - first : h->cur_chunk;
+      char* stage = static_cast<char*>(h->cur_stage) + (c & 1) * h->cur_chunk * h->elem;
+      FSB_CUDA(fsb::launch_objective(h->launch, first, count, stage, h->stream));
+      FSB_CUDA(cudaMemcpyAsync(static_cast<char*>(current_objective) + first * h->elem, stage,
+                               count * h->elem, cudaMemcpyDeviceToHost, h->stream));
+    }
   }
   if (step_out) *step_out = h->step;
   return check_status_word(h);

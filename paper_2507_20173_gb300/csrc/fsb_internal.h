@@ -75,7 +75,9 @@ cudaError_t stream_ws_prepare(const StreamLaunch& L);
 int stream_ws_blocks_per_sm(const StreamLaunch& L);
 cudaError_t launch_stream_pass_ws(const StreamLaunch& L, int pass_kind, cudaStream_t s);
 cudaError_t launch_init(const StreamLaunch& L, int weight_mode, cudaStream_t s);
-cudaError_t launch_objective(const StreamLaunch& L, void* cur, cudaStream_t s);
+// currentObjective of fish [first, first + count) into cur[0, count).
+cudaError_t launch_objective(const StreamLaunch& L, uint64_t first, uint64_t count, void* cur,
+                             cudaStream_t s);
 // Launch description of the resident single-school kernel (binary32 state).
 struct ResidentLaunch {
   void* x;

@@ -239,18 +239,20 @@ cudaError_t launch_init(const StreamLaunch& L, int weight_mode, cudaStream_t s) 
   return cudaGetLastError();
 }
 
-cudaError_t launch_objective(const StreamLaunch& L, void* cur, cudaStream_t s) {
+cudaError_t launch_objective(const StreamLaunch& L, uint64_t first, uint64_t count, void* cur,
+                             cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
   const int block = 256;
-  const uint64_t want = (L.n + block - 1) / block;
+  const uint64_t want = (count + block - 1) / block;
   const int grid = static_cast<int>(want < 4096 ? want : 4096);
   if (L.real_is_double)
-    objective_kernel<double><<<grid, block, 0, s>>>(static_cast<const double*>(L.x),
-                                                    static_cast<const double*>(L.y),
-                                                    static_cast<double*>(cur), L.n);
+    objective_kernel<double><<<grid, block, 0, s>>>(static_cast<const double*>(L.x) + first,
+                                                    static_cast<const double*>(L.y) + first,
+                                                    static_cast<double*>(cur), count);
   else
-    objective_kernel<float><<<grid, block, 0, s>>>(static_cast<const float*>(L.x),
-                                                   static_cast<const float*>(L.y),
-                                                   static_cast<float*>(cur), L.n);
+    objective_kernel<float><<<grid, block, 0, s>>>(static_cast<const float*>(L.x) + first,
+                                                   static_cast<const float*>(L.y) + first,
+                                                   static_cast<float*>(cur), count);
   return cudaGetLastError();
 }
 

@@ -350,3 +350,22 @@ def test_full_size_launch_shapes_agree_bitwise(kernel, stages):
         assert bad == 0, "%s differs in %d fish between launch shapes" % (name, bad)
     assert np.array_equal(sa["max_abs_delta"], sb["max_abs_delta"])
     assert np.array_equal(sa["eat_max_diff"], sb["eat_max_diff"])
+
+
+@pytest.mark.parametrize("precision", [fsb.FSB_FP32_KAHAN, fsb.FSB_FP64_STATE])
+def test_read_state_objective_over_chunks(precision):
+    """fsb_read_state derives currentObjective chunk by chunk (2^22 fish per
+    chunk).  With a ragged last chunk every fish must still hold the
+    correctly rounded sqrt(x*x + y*y) of its read-back position (Sec. 2.1.1),
+    which numpy computes here in the state's precision, one rounding per
+    operation."""
+    n = 2 * (1 << 22) + 12345
+    s = fsb.School.create(stream_cfg(n, 31, precision=precision))
+    s.step(3)
+    got = s.read()
+    s.destroy()
+    x, y = got["x"], got["y"]
+    want = np.sqrt(x * x + y * y)
+    assert want.dtype == x.dtype
+    bad = np.nonzero(got["cur"] != want)[0]
+    assert bad.size == 0, "cur differs at %d fish, first %d" % (bad.size, bad[0])
