@@ -298,6 +298,7 @@ def run_batch(args, world, rank, local, pg):
     ms = start.elapsed_time(stop)
     kms, kl = fsb.fsb_batch_kernel_time(b)
     info = fsb.fsb_batch_info(b)
+    plan = fsb.fsb_batch_plan(b)
     fsb.fsb_batch_destroy(b)
     ms_max = reduce_max(ms, pg)
     value = world * total * steps / (ms_max / 1e3)
@@ -345,6 +346,7 @@ def run_batch(args, world, rank, local, pg):
                            "%s (first %d schools)" % (wl.name, n_schools),
                            "n_schools": n_schools, "total_fish": total,
                            "precision": args.precision, "batch": info,
+                           "launch_plan": plan,
                            "l2": "state %.2f GB; each school's state stays on chip for the call"
                                  % (16 * total / 1e9),
                            "parallelism": "replicas x%d" % world},
@@ -352,7 +354,8 @@ def run_batch(args, world, rank, local, pg):
                 "per_school": per_school,
                 "batched_over_per_school": (value / world) / per_school["value"]
                 if per_school else None,
-                "cpu_baseline": None, "e2e": None, "gpu_launches": 3, "clocks": clocks}
+                "cpu_baseline": None, "e2e": None,
+                "gpu_launches": len(plan["launches"]) + 1, "clocks": clocks}
         print(json.dumps(line), flush=True)
 
 

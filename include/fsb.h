@@ -249,17 +249,41 @@ int fsb_batch_create(const fsb_config* tmpl, uint32_t n_schools, const uint64_t*
  * batch's stream unless stats is given (then synchronises and fills it). */
 int fsb_batch_step(fsb_batch_handle b, uint32_t n_steps, fsb_step_stats* stats);
 
-/* Blocks per cluster of the batch launch: 0 (the library's choice: the
- * smallest of 1, 2, 4, 8 that holds the largest school), 1, 2, 4 or 8.
+/* Cluster size of the batch's schools.
+ *   0 (default): each school runs on the smallest cluster of 1, 2, 4 or 8
+ *     blocks (8192 fish per block) that holds it.  One persistent launch per
+ *     cluster size in use runs concurrently with the others, each on a share
+ *     of the SMs proportional to its schools' fish; single-block schools
+ *     take the SMs left over, and every launch helps with the schools of
+ *     smaller clusters once its own are done.
+ *   1, 2, 4, 8: every school larger than one block runs on clusters of this
+ *     size (one launch on every SM it can hold, single blocks beside it).
  * Too small for the largest school -> FSB_ERR_UNSUPPORTED.  Synchronises. */
 int fsb_batch_set_cluster(fsb_batch_handle b, int cluster);
 
-/* Launch shape and step counter of a batch (any pointer may be NULL):
- * blocks per cluster, resident clusters, single-block filler blocks that run
- * beside the clusters on the SMs they leave idle, schools in the
- * whole-cluster queue, step counter. */
+/* Launch shape and step counter of a batch (any pointer may be NULL): the
+ * largest cluster size in use, its resident clusters, the blocks of the
+ * single-block launch beside the clusters (0 if none), the schools that run
+ * on clusters of more than one block, the step counter. */
 int fsb_batch_info(fsb_batch_handle b, int* cluster, int* n_clusters, int* filler_blocks,
                    uint32_t* n_big, uint64_t* step);
+
+/* The batch's launch plan (any pointer may be NULL): n_launches (1 to 4)
+ * concurrent persistent launches, launch i running clusters of cluster[i]
+ * blocks on a grid of blocks[i] blocks (arrays of 4; entries past
+ * n_launches are 0), and queue_schools[t] (array of 4) schools in the work
+ * queue of clusters of 8, 4, 2 and 1 block(s). */
+int fsb_batch_plan(fsb_batch_handle b, int* n_launches, int* cluster, int* blocks,
+                   uint32_t* queue_schools);
+
+/* Replace the batch's launches, keeping its work queues (set by
+ * fsb_batch_set_cluster): n_launches (1 to 4) launches in decreasing cluster
+ * size, launch i running clusters of cluster[i] (1, 2, 4 or 8) blocks on a
+ * grid of blocks[i] (a positive multiple of cluster[i]).  The widest launch
+ * must be at least as wide as the widest non-empty queue.  Any other
+ * combination -> FSB_ERR_INVALID_ARG, handle unchanged.  Synchronises. */
+int fsb_batch_set_plan(fsb_batch_handle b, int n_launches, const int* cluster,
+                       const int* blocks);
 
 /* Device time of the batch launches since timing was enabled (CUDA events
  * on the batch's stream around each launch). */
@@ -338,9 +362,11 @@ int fsb_autotune(const fsb_config* cfg, uint32_t n_steps, int* best_path,
                  uint32_t* candidates_tried);
 
 /* Batch autotuner: times the batch of fsb_batch_create's arguments with
- * clusters of 1, 2, 4 and 8 blocks (those that hold the largest school) and
- * reports the fastest.  OVERWRITES `state` (every school is initialised and
- * stepped).  Synchronous. */
+ * each school on the smallest cluster that holds it (cluster 0, the
+ * default) and with every school on clusters of 1, 2, 4 and 8 blocks (those
+ * that hold the largest school), and reports the fastest as the value for
+ * fsb_batch_set_cluster.  OVERWRITES `state` (every school is initialised
+ * and stepped).  Synchronous. */
 int fsb_autotune_batch(const fsb_config* tmpl, uint32_t n_schools, const uint64_t* offsets,
                        const uint64_t* seeds, const fsb_state_dev* state, uint32_t n_steps,
                        int* best_cluster, double* best_fish_steps_per_s);

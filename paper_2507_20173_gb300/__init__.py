@@ -48,7 +48,7 @@ EXPORTED = ("fsb_config_init", "fsb_create", "fsb_step", "fsb_read_state",
             "fsb_set_tuning", "fsb_get_tuning", "fsb_batch_create", "fsb_batch_step",
             "fsb_batch_set_cluster", "fsb_batch_info", "fsb_batch_set_timing",
             "fsb_batch_kernel_time", "fsb_batch_destroy", "fsb_autotune",
-            "fsb_autotune_batch", "fsb_eat_max")
+            "fsb_autotune_batch", "fsb_eat_max", "fsb_batch_plan", "fsb_batch_set_plan")
 
 
 class FsbError(RuntimeError):
@@ -129,6 +129,9 @@ def lib() -> ctypes.CDLL:
         "fsb_batch_set_cluster": [P, i32],
         "fsb_batch_info": [P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
                            ctypes.POINTER(u32), ctypes.POINTER(u64)],
+        "fsb_batch_plan": [P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                           ctypes.POINTER(u32)],
+        "fsb_batch_set_plan": [P, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)],
         "fsb_batch_set_timing": [P, i32],
         "fsb_batch_kernel_time": [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u64)],
         "fsb_batch_destroy": [P],
@@ -287,6 +290,26 @@ def fsb_batch_info(handle: int) -> dict:
            "fsb_batch_info")
     return {"cluster": c.value, "n_clusters": nc.value, "filler_blocks": fb.value,
             "n_big": nb.value, "step": st.value}
+
+
+def fsb_batch_plan(handle: int) -> dict:
+    """The batch's concurrent launches (cluster size, grid) and the schools
+    in each work queue (clusters of 8, 4, 2, 1 blocks)."""
+    n = ctypes.c_int()
+    c, b = (ctypes.c_int * 4)(), (ctypes.c_int * 4)()
+    q = (ctypes.c_uint32 * 4)()
+    _check(lib().fsb_batch_plan(ctypes.c_void_p(handle), ctypes.byref(n), c, b, q),
+           "fsb_batch_plan")
+    return {"launches": [{"cluster": c[i], "blocks": b[i]} for i in range(n.value)],
+            "queue_schools": {8: q[0], 4: q[1], 2: q[2], 1: q[3]}}
+
+
+def fsb_batch_set_plan(handle: int, launches) -> None:
+    """Replace the batch's launches: a sequence of (cluster, blocks)."""
+    n = len(launches)
+    c = (ctypes.c_int * max(n, 1))(*[int(l[0]) for l in launches])
+    b = (ctypes.c_int * max(n, 1))(*[int(l[1]) for l in launches])
+    _check(lib().fsb_batch_set_plan(ctypes.c_void_p(handle), n, c, b), "fsb_batch_set_plan")
 
 
 def fsb_batch_set_timing(handle: int, enable: bool) -> None:

@@ -139,7 +139,7 @@ extern "C" int fsb_autotune_batch(const fsb_config* tmpl, uint32_t n_schools,
   if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
     return fsb::record_error(FSB_ERR_CUDA, "fsb_autotune_batch: stream creation failed");
   double best_ms = -1.0;
-  const int clusters[] = {1, 2, 4, 8};
+  const int clusters[] = {0, 1, 2, 4, 8};  // 0: each school on the smallest cluster that holds it
   for (int c : clusters) {
     fsb_batch_handle b = nullptr;
     int rc = fsb_batch_create(tmpl, n_schools, offsets, seeds, state, 1, 0, s, &b);

@@ -1,17 +1,19 @@
 // fsb_batch.cu -- many independent fish schools of uneven size in one
 // persistent launch.
 //
-// Thread-block clusters of C blocks pop schools from a work list sorted by
-// size, largest first (longest-processing-time order), through an atomic
-// counter over a ragged offset table, and run all n_steps of a school on
+// Thread-block clusters of C blocks pop schools from work queues sorted by
+// size, largest first (longest-processing-time order), through atomic
+// counters over a ragged offset table, and run all n_steps of a school on
 // chip: each thread keeps FPT fish (x, y, weight, currentObjective,
-// prevObjective) in registers.  Two queues:
-//   - schools larger than one block's capacity use the whole cluster; the
-//     per-step maxima and barycentre partials of the C blocks meet in rank
-//     0's shared memory through distributed shared memory, with one cluster
-//     barrier per step (partials double-buffered by step parity);
-//   - when those run out, every block pops the smaller schools on its own and
-//     reduces with __syncthreads only.
+// prevObjective) in registers.  A school goes to the queue of the smallest
+// cluster that holds it (8, 4, 2 or 1 blocks):
+//   - a cluster first takes schools from the queue of its own size, then
+//     from the queues of smaller multi-block clusters; the per-step maxima
+//     and barycentre partials of its C blocks meet in rank 0's shared memory
+//     through distributed shared memory, with one cluster barrier per step
+//     (partials double-buffered by step parity);
+//   - when those run out, every block pops single-block schools on its own
+//     and reduces with __syncthreads only.
 // The per-step order within a school is the paper's (Sec. 2.1.2 swim,
 // Sec. 2.1.1 objective, delta, the Sec. 2.3.2 max, feeding, barycentre).
 // School k uses key seeds[k] and school id k, so it reproduces the
@@ -19,10 +21,10 @@
 // control flow (every decision a cluster takes is broadcast from rank 0),
 // so no block can be left waiting for another.
 //
-// Clusters of eight blocks cannot tile every SM (they must sit inside one
-// GPC), so a second, single-block launch of the same kernel runs beside the
-// cluster launch on the SMs left over; it only pops from the per-block
-// queue, which both launches share.
+// One persistent launch per cluster size in use runs concurrently with the
+// others, each on a share of the SMs in proportion to its queue's fish (a
+// launch of single blocks takes the SMs the clusters leave over); all of
+// them share the queues, so the launches that finish first help the rest.
 #include <cstdint>
 
 #include <cooperative_groups.h>
@@ -43,8 +45,9 @@ struct BatchArgs {
   float* __restrict__ pv;
   const unsigned long long* __restrict__ offsets;  // n_schools + 1
   const unsigned long long* __restrict__ seeds;    // n_schools
-  const uint32_t* __restrict__ order;              // big schools, then small, each largest first
-  uint32_t n_big;                                  // order[0 .. n_big) use whole clusters
+  const uint32_t* __restrict__ order;              // queues 0..3, each largest first
+  uint32_t queue_lo[kBatchQueues + 1];             // queue t: order[queue_lo[t] .. queue_lo[t+1])
+  int first_queue;                                 // whole-cluster queue this launch starts at
   uint32_t n_schools;
   Physics<float> ph;
   int init;                                        // initialise each school before stepping
@@ -289,30 +292,34 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs a) {
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = static_cast<int>(cluster.block_rank());
 
-  // Phase 1 (whole cluster per school) while the big queue lasts, then
-  // phase 2 (each block on its own).  One call site keeps one inlined copy
-  // of the per-school loop.
-  bool whole_cluster = CLUSTER > 1;
+  // Phase 1 (whole cluster per school) through the multi-block queues from
+  // this launch's own on, then phase 2 (each block on its own) through the
+  // single-block queue.  The queue index is uniform across the cluster
+  // (every pick is broadcast from rank 0).  One call site keeps one inlined
+  // copy of the per-school loop.
+  constexpr int kSingle = kBatchQueues - 1;
+  int t = CLUSTER > 1 ? a.first_queue : kSingle;
   for (;;) {
+    const bool whole_cluster = t < kSingle;
     uint32_t idx;
     if (whole_cluster) {
-      if (rank == 0 && threadIdx.x == 0) s_pick = atomicAdd(&a.bctl->next_big, 1u);
+      if (rank == 0 && threadIdx.x == 0) s_pick = atomicAdd(&a.bctl->next[t], 1u);
       cluster.sync();
       idx = *cluster.map_shared_rank(&s_pick, 0);
       cluster.sync();  // every block has read rank 0's pick
-      if (idx >= a.n_big) {
-        whole_cluster = false;
-        continue;
-      }
     } else {
-      if (threadIdx.x == 0) s_pick = atomicAdd(&a.bctl->next_small, 1u);
+      if (threadIdx.x == 0) s_pick = atomicAdd(&a.bctl->next[kSingle], 1u);
       __syncthreads();
-      idx = s_pick + a.n_big;
+      idx = s_pick;
       __syncthreads();
-      if (idx >= a.n_schools) break;
     }
-    run_school<ACC, VAR>(a, a.order[idx], whole_cluster ? rank : 0, whole_cluster ? CLUSTER : 1, R,
-                    xchg, &s_M, &s_E, spv);
+    if (idx >= a.queue_lo[t + 1] - a.queue_lo[t]) {
+      if (t == kSingle) break;
+      ++t;
+      continue;
+    }
+    run_school<ACC, VAR>(a, a.order[a.queue_lo[t] + idx], whole_cluster ? rank : 0,
+                         whole_cluster ? CLUSTER : 1, R, xchg, &s_M, &s_E, spv);
   }
 }
 
@@ -385,12 +392,17 @@ int batch_max_clusters(int cluster, int acc) {
   return n;
 }
 
-cudaError_t launch_batch(const BatchLaunch& L, cudaStream_t s, cudaStream_t side,
-                         cudaEvent_t fork, cudaEvent_t join) {
+cudaError_t launch_batch(const BatchLaunch& L, cudaStream_t s, const cudaStream_t* side,
+                         cudaEvent_t fork, const cudaEvent_t* join) {
   const bool var = L.swim_mode != 0 || L.feed_mode != 0;
-  const void* fn = pick(L.cluster, L.acc, var);
-  const void* fill = pick(1, L.acc, var);
-  if (!fn || !fill || L.n_clusters < 1) return cudaErrorInvalidValue;
+  if (L.n_launches < 1 || L.n_launches > kBatchMaxLaunches) return cudaErrorInvalidValue;
+  if (L.n_launches > 1 && (!side || !fork || !join)) return cudaErrorInvalidValue;
+  const void* fn[kBatchMaxLaunches];
+  for (int i = 0; i < L.n_launches; ++i) {
+    fn[i] = pick(L.cluster[i], L.acc, var);
+    if (!fn[i] || L.blocks[i] < L.cluster[i] || L.blocks[i] % L.cluster[i])
+      return cudaErrorInvalidValue;
+  }
   BatchArgs a;
   a.x = static_cast<float*>(L.x);
   a.y = static_cast<float*>(L.y);
@@ -399,7 +411,7 @@ cudaError_t launch_batch(const BatchLaunch& L, cudaStream_t s, cudaStream_t side
   a.offsets = L.offsets;
   a.seeds = L.seeds;
   a.order = L.order;
-  a.n_big = L.n_big;
+  for (int t = 0; t <= kBatchQueues; ++t) a.queue_lo[t] = L.queue_lo[t];
   a.n_schools = L.n_schools;
   a.ph.pond_half = static_cast<float>(L.pond_half);
   a.ph.step = static_cast<float>(L.step);
@@ -414,23 +426,25 @@ cudaError_t launch_batch(const BatchLaunch& L, cudaStream_t s, cudaStream_t side
   a.n_steps = L.n_steps;
   a.bctl = L.bctl;
   a.stats = L.stats;
-  void* args[] = {&a};
   cudaError_t e = cudaMemsetAsync(L.bctl, 0, sizeof(BatchCtl), s);
   if (e != cudaSuccess) return e;
-  const bool filler = L.filler_blocks > 0 && L.cluster > 1 && side && fork && join;
-  if (filler) {
+  if (L.n_launches > 1) {
     if ((e = cudaEventRecord(fork, s)) != cudaSuccess) return e;
-    if ((e = cudaStreamWaitEvent(side, fork, 0)) != cudaSuccess) return e;
+    for (int i = 1; i < L.n_launches; ++i)
+      if ((e = cudaStreamWaitEvent(side[i - 1], fork, 0)) != cudaSuccess) return e;
   }
-  cudaLaunchAttribute attr[1];
-  cudaLaunchConfig_t cfg = make_config(L.cluster, L.n_clusters * L.cluster, s, attr);
-  if ((e = cudaLaunchKernelExC(&cfg, fn, args)) != cudaSuccess) return e;
-  if (filler) {
-    cudaLaunchAttribute attr2[1];
-    cudaLaunchConfig_t cfg2 = make_config(1, L.filler_blocks, side, attr2);
-    if ((e = cudaLaunchKernelExC(&cfg2, fill, args)) != cudaSuccess) return e;
-    if ((e = cudaEventRecord(join, side)) != cudaSuccess) return e;
-    if ((e = cudaStreamWaitEvent(s, join, 0)) != cudaSuccess) return e;
+  // largest clusters first, so they are placed before the smaller launches
+  for (int i = 0; i < L.n_launches; ++i) {
+    BatchArgs ai = a;
+    ai.first_queue = batch_queue_of(L.cluster[i]);
+    void* args[] = {&ai};
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = make_config(L.cluster[i], L.blocks[i], i == 0 ? s : side[i - 1], attr);
+    if ((e = cudaLaunchKernelExC(&cfg, fn[i], args)) != cudaSuccess) return e;
+  }
+  for (int i = 1; i < L.n_launches; ++i) {
+    if ((e = cudaEventRecord(join[i - 1], side[i - 1])) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(s, join[i - 1], 0)) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }

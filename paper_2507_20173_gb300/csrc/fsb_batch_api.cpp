@@ -3,6 +3,7 @@
 // buffer, cached CUDA graph per call length) and the one-shot fsb_run_batch.
 // All arithmetic runs in fsb_batch.cu.
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -48,8 +49,10 @@ struct fsb_batch {
   uint64_t max_school = 0;
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
-  cudaStream_t side_stream = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaStream_t side_stream[fsb::kBatchMaxLaunches - 1] = {};
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[fsb::kBatchMaxLaunches - 1] = {};
+  int forced_cluster = 0;              // 0: each school on the smallest cluster that holds it
   int sms = 0;
   unsigned long long* d_offsets = nullptr;
   unsigned long long* d_seeds = nullptr;
@@ -73,56 +76,88 @@ struct fsb_batch {
 
 namespace {
 
-// Whole-cluster queue: schools larger than one block holds (when the
-// cluster has more than one block), then every other school; each queue
-// largest first (longest-processing-time order).
-int build_order(fsb_batch* b, int cluster) {
+// Work queues and launches of a batch.  A school one block holds goes to
+// the single-block queue; a larger one to the queue of the smallest cluster
+// that holds it (or, with a forced cluster size, to that size's queue).
+// Each queue is largest first (longest-processing-time order).  One
+// persistent launch per multi-block cluster size in use gets a share of the
+// SMs in proportion to its queue's fish (with a forced size: every SM it
+// can hold), largest cluster first; a launch of single blocks takes the SMs
+// left over.
+int plan_batch(fsb_batch* b, int forced) {
   const uint64_t cap = fsb::batch_block_capacity();
-  std::vector<uint32_t> order;
-  order.reserve(b->n_schools);
-  std::vector<uint32_t> big, small;
-  for (uint32_t k : b->sizes_sorted) {
-    const uint64_t n = b->offsets[k + 1] - b->offsets[k];
-    if (cluster > 1 && n > cap)
-      big.push_back(k);
-    else
-      small.push_back(k);
-  }
-  const uint32_t n_big = static_cast<uint32_t>(big.size());
-  order.insert(order.end(), big.begin(), big.end());
-  order.insert(order.end(), small.begin(), small.end());
-  BCUDA(cudaMemcpy(b->d_order, order.data(), sizeof(uint32_t) * order.size(),
-                   cudaMemcpyHostToDevice));
-  b->L.n_big = n_big;
-  return FSB_OK;
-}
-
-int configure_cluster(fsb_batch* b, int cluster) {
-  const uint64_t cap = fsb::batch_block_capacity();
-  if (cluster == 0) {
-    cluster = 1;
-    while (static_cast<uint64_t>(cluster) * cap < b->max_school && cluster < 8) cluster *= 2;
-  }
-  if (cluster != 1 && cluster != 2 && cluster != 4 && cluster != 8)
+  if (forced != 0 && forced != 1 && forced != 2 && forced != 4 && forced != 8)
     return bfail(FSB_ERR_INVALID_ARG, "batch cluster size must be 1, 2, 4 or 8");
-  if (static_cast<uint64_t>(cluster) * cap < b->max_school)
+  const int widest = forced ? forced : 8;
+  if (static_cast<uint64_t>(widest) * cap < b->max_school)
     return bfail(FSB_ERR_UNSUPPORTED,
                  "largest school (%llu fish) exceeds a cluster of %d blocks (%llu fish)",
-                 static_cast<unsigned long long>(b->max_school), cluster,
-                 static_cast<unsigned long long>(cluster * cap));
-  const int n_clusters = fsb::batch_max_clusters(cluster, b->L.acc);
-  if (n_clusters < 1)
-    return bfail(FSB_ERR_UNSUPPORTED, "clusters of %d blocks cannot be resident", cluster);
-  b->L.cluster = cluster;
-  b->L.n_clusters = n_clusters;
-  b->L.filler_blocks = 0;
-  if (cluster > 1) {
-    const int left = b->sms - n_clusters * cluster;
-    const int per_sm = fsb::batch_max_clusters(1, b->L.acc) / (b->sms > 0 ? b->sms : 1);
-    b->L.filler_blocks = left > 0 ? left * (per_sm > 0 ? per_sm : 1) : 0;
+                 static_cast<unsigned long long>(b->max_school), widest,
+                 static_cast<unsigned long long>(widest * cap));
+  std::vector<uint32_t> queue[fsb::kBatchQueues];
+  uint64_t fish[fsb::kBatchQueues] = {0, 0, 0, 0};
+  for (uint32_t k : b->sizes_sorted) {
+    const uint64_t n = b->offsets[k + 1] - b->offsets[k];
+    int need = 1;
+    while (static_cast<uint64_t>(need) * cap < n) need *= 2;
+    const int t = fsb::batch_queue_of(need == 1 ? 1 : (forced ? forced : need));
+    queue[t].push_back(k);
+    fish[t] += n;
   }
-  int rc = build_order(b, cluster);
-  if (rc != FSB_OK) return rc;
+  std::vector<uint32_t> order;
+  order.reserve(b->n_schools);
+  fsb::BatchLaunch& L = b->L;
+  for (int t = 0; t < fsb::kBatchQueues; ++t) {
+    L.queue_lo[t] = static_cast<uint32_t>(order.size());
+    order.insert(order.end(), queue[t].begin(), queue[t].end());
+  }
+  L.queue_lo[fsb::kBatchQueues] = static_cast<uint32_t>(order.size());
+
+  const int slots = fsb::batch_max_clusters(1, L.acc);  // resident single blocks
+  if (slots < 1) return bfail(FSB_ERR_UNSUPPORTED, "batch kernel cannot be resident");
+  // Work of a queue: its fish times the relative cost per fish-step of its
+  // cluster width, measured on GB300 for each width alone (the per-step
+  // cluster barrier costs more across 8 blocks; single blocks carry the
+  // smallest schools, whose steps are latency-bound).
+  const double cost[fsb::kBatchQueues] = {1.15, 1.0, 1.0, 1.05};
+  double work[fsb::kBatchQueues], total = 0.0;
+  for (int t = 0; t < fsb::kBatchQueues; ++t) {
+    work[t] = cost[t] * static_cast<double>(fish[t]);
+    total += work[t];
+  }
+  int n = 0, used = 0;
+  for (int c = 8; c >= 2; c /= 2) {
+    const int t = fsb::batch_queue_of(c);
+    if (queue[t].empty()) continue;
+    const int max_clusters = fsb::batch_max_clusters(c, L.acc);
+    if (max_clusters < 1)
+      return bfail(FSB_ERR_UNSUPPORTED, "clusters of %d blocks cannot be resident", c);
+    int clusters = max_clusters;
+    if (!forced) {
+      // the widest launch rounds up: no other launch can take its schools,
+      // while the narrower ones hand their spare time down to smaller queues
+      const double share = static_cast<double>(slots) * work[t] / total / c;
+      clusters = n == 0 ? static_cast<int>(std::ceil(share)) : static_cast<int>(share);
+      clusters = clusters < 1 ? 1 : (clusters > max_clusters ? max_clusters : clusters);
+    }
+    L.cluster[n] = c;
+    L.blocks[n] = clusters * c;
+    used += L.blocks[n];
+    ++n;
+  }
+  if (n == 0) {
+    L.cluster[n] = 1;
+    L.blocks[n] = slots;
+    ++n;
+  } else if (used < slots) {
+    L.cluster[n] = 1;  // the SMs the clusters leave over
+    L.blocks[n] = slots - used;
+    ++n;
+  }
+  L.n_launches = n;
+  BCUDA(cudaMemcpy(b->d_order, order.data(), sizeof(uint32_t) * order.size(),
+                   cudaMemcpyHostToDevice));
+  b->forced_cluster = forced;
   for (auto& g : b->graphs) cudaGraphExecDestroy(g.exec);
   b->graphs.clear();
   return FSB_OK;
@@ -195,9 +230,11 @@ void release(fsb_batch* b) {
   cudaFree(b->d_bctl);
   cudaFree(b->d_stats);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
-  if (b->side_stream) cudaStreamDestroy(b->side_stream);
+  for (int i = 0; i < fsb::kBatchMaxLaunches - 1; ++i) {
+    if (b->side_stream[i]) cudaStreamDestroy(b->side_stream[i]);
+    if (b->ev_join[i]) cudaEventDestroy(b->ev_join[i]);
+  }
   if (b->ev_fork) cudaEventDestroy(b->ev_fork);
-  if (b->ev_join) cudaEventDestroy(b->ev_join);
   delete b;
 }
 
@@ -254,9 +291,11 @@ int fsb_batch_create(const fsb_config* tmpl, uint32_t n_schools, const uint64_t*
   });
   auto body = [&]() -> int {
     BCUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
-    BCUDA(cudaStreamCreateWithFlags(&b->side_stream, cudaStreamNonBlocking));
+    for (int i = 0; i < fsb::kBatchMaxLaunches - 1; ++i) {
+      BCUDA(cudaStreamCreateWithFlags(&b->side_stream[i], cudaStreamNonBlocking));
+      BCUDA(cudaEventCreateWithFlags(&b->ev_join[i], cudaEventDisableTiming));
+    }
     BCUDA(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
-    BCUDA(cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming));
     int dev = 0;
     BCUDA(cudaGetDevice(&dev));
     BCUDA(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev));
@@ -292,7 +331,7 @@ int fsb_batch_create(const fsb_config* tmpl, uint32_t n_schools, const uint64_t*
     L.weight_mode = tmpl->init_weight_mode;
     L.base_step = b->d_base;
     L.bctl = b->d_bctl;
-    int rc = configure_cluster(b, 0);
+    int rc = plan_batch(b, 0);
     if (rc != FSB_OK) return rc;
     return ensure_stats(b, 1);
   };
@@ -342,23 +381,72 @@ int fsb_batch_step(fsb_batch_handle b, uint32_t n_steps, fsb_step_stats* host_st
 int fsb_batch_set_cluster(fsb_batch_handle b, int cluster) {
   if (!b) return bfail(FSB_ERR_INVALID_ARG, "batch handle is NULL");
   BCUDA(cudaStreamSynchronize(b->stream));
-  const fsb::BatchLaunch saved = b->L;
-  const int rc = configure_cluster(b, cluster);
-  if (rc != FSB_OK) {
-    b->L = saved;
-    build_order(b, saved.cluster);
-  }
+  const int saved = b->forced_cluster;
+  const int rc = plan_batch(b, cluster);
+  if (rc != FSB_OK) plan_batch(b, saved);
   return rc;
 }
 
 int fsb_batch_info(fsb_batch_handle b, int* cluster, int* n_clusters, int* filler_blocks,
                    uint32_t* n_big, uint64_t* step) {
   if (!b) return bfail(FSB_ERR_INVALID_ARG, "batch handle is NULL");
-  if (cluster) *cluster = b->L.cluster;
-  if (filler_blocks) *filler_blocks = b->L.filler_blocks;
-  if (n_clusters) *n_clusters = b->L.n_clusters;
-  if (n_big) *n_big = b->L.n_big;
+  const fsb::BatchLaunch& L = b->L;
+  const bool single_only = L.n_launches == 1 && L.cluster[0] == 1;
+  if (cluster) *cluster = L.cluster[0];
+  if (n_clusters) *n_clusters = L.blocks[0] / L.cluster[0];
+  if (filler_blocks)
+    *filler_blocks = !single_only && L.cluster[L.n_launches - 1] == 1 ? L.blocks[L.n_launches - 1] : 0;
+  if (n_big) *n_big = L.queue_lo[fsb::kBatchQueues - 1];
   if (step) *step = b->step;
+  return FSB_OK;
+}
+
+int fsb_batch_set_plan(fsb_batch_handle b, int n_launches, const int* cluster,
+                       const int* blocks) {
+  if (!b || !cluster || !blocks) return bfail(FSB_ERR_INVALID_ARG, "NULL argument");
+  if (n_launches < 1 || n_launches > fsb::kBatchMaxLaunches)
+    return bfail(FSB_ERR_INVALID_ARG, "n_launches must be 1 to %d", fsb::kBatchMaxLaunches);
+  fsb::BatchLaunch& L = b->L;
+  for (int i = 0; i < n_launches; ++i) {
+    const int c = cluster[i];
+    if (c != 1 && c != 2 && c != 4 && c != 8)
+      return bfail(FSB_ERR_INVALID_ARG, "launch %d: cluster size must be 1, 2, 4 or 8", i);
+    if (i > 0 && c >= cluster[i - 1])
+      return bfail(FSB_ERR_INVALID_ARG, "launches must be in decreasing cluster size");
+    if (blocks[i] < c || blocks[i] % c)
+      return bfail(FSB_ERR_INVALID_ARG, "launch %d: blocks must be a positive multiple of %d",
+                   i, c);
+    if (c > 1 && fsb::batch_max_clusters(c, L.acc) < 1)
+      return bfail(FSB_ERR_UNSUPPORTED, "clusters of %d blocks cannot be resident", c);
+  }
+  // every multi-block queue needs a launch of at least its cluster size (a
+  // launch serves its own queue, then the smaller ones)
+  for (int t = 0; t < fsb::kBatchQueues - 1; ++t)
+    if (L.queue_lo[t + 1] > L.queue_lo[t] && cluster[0] < (8 >> t))
+      return bfail(FSB_ERR_INVALID_ARG, "schools need clusters of %d blocks; the widest launch "
+                   "has %d", 8 >> t, cluster[0]);
+  BCUDA(cudaStreamSynchronize(b->stream));
+  L.n_launches = n_launches;
+  for (int i = 0; i < n_launches; ++i) {
+    L.cluster[i] = cluster[i];
+    L.blocks[i] = blocks[i];
+  }
+  for (auto& g : b->graphs) cudaGraphExecDestroy(g.exec);
+  b->graphs.clear();
+  return FSB_OK;
+}
+
+int fsb_batch_plan(fsb_batch_handle b, int* n_launches, int* cluster, int* blocks,
+                   uint32_t* queue_schools) {
+  if (!b) return bfail(FSB_ERR_INVALID_ARG, "batch handle is NULL");
+  const fsb::BatchLaunch& L = b->L;
+  if (n_launches) *n_launches = L.n_launches;
+  for (int i = 0; i < fsb::kBatchMaxLaunches; ++i) {
+    if (cluster) cluster[i] = i < L.n_launches ? L.cluster[i] : 0;
+    if (blocks) blocks[i] = i < L.n_launches ? L.blocks[i] : 0;
+  }
+  if (queue_schools)
+    for (int t = 0; t < fsb::kBatchQueues; ++t) queue_schools[t] = L.queue_lo[t + 1] - L.queue_lo[t];
   return FSB_OK;
 }
 

@@ -110,12 +110,17 @@ int resident_max_block(int fpt);
 int resident_blocks_per_sm(int fpt, int acc, int block);
 size_t resident_smem_bytes(int fpt, int block);
 
-// Work-list counters of one batch launch; zeroed before every launch.
+// Work queues of a batch: queue t (t = 0, 1, 2) holds the schools run on
+// whole clusters of 8 >> t blocks, queue 3 the schools one block runs; each
+// queue largest first.  One counter per queue, zeroed before every call.
+constexpr int kBatchQueues = 4;
+constexpr int kBatchMaxLaunches = 4;
 struct alignas(16) BatchCtl {
-  unsigned next_big;    // next index into the whole-cluster queue
-  unsigned next_small;  // next index into the per-block queue
-  unsigned spare[2];
+  unsigned next[kBatchQueues];
 };
+
+// Queue of the schools that need clusters of c blocks (c = 1, 2, 4, 8).
+inline int batch_queue_of(int c) { return c >= 8 ? 0 : c >= 4 ? 1 : c >= 2 ? 2 : 3; }
 
 // Launch description of the batched (many schools) kernel, binary32 state.
 struct BatchLaunch {
@@ -125,8 +130,8 @@ struct BatchLaunch {
   void* pv;
   const unsigned long long* offsets;  // device, n_schools + 1
   const unsigned long long* seeds;    // device, n_schools
-  const uint32_t* order;              // device, whole-cluster queue then per-block queue
-  uint32_t n_big;
+  const uint32_t* order;              // device, queues 0..3 back to back
+  uint32_t queue_lo[kBatchQueues + 1];  // queue t is order[queue_lo[t] .. queue_lo[t + 1])
   uint32_t n_schools;
   double pond_half, step, w0, w_min, w_max;
   int swim_mode, feed_mode;
@@ -137,17 +142,21 @@ struct BatchLaunch {
   uint32_t n_steps;
   BatchCtl* bctl;
   fsb_step_stats* stats;              // device, n_schools * n_steps
-  int cluster;                        // blocks per cluster: 1, 2, 4, 8
-  int n_clusters;                     // resident clusters (persistent grid)
-  int filler_blocks;                  // single-block launch beside it on the SMs the
-                                      // clusters leave idle (per-block queue only)
+  // Concurrent persistent launches, largest cluster first.  Launch i runs
+  // clusters of cluster[i] blocks on a grid of blocks[i]: it takes whole-
+  // cluster schools from queue batch_queue_of(cluster[i]) and then from the
+  // queues of smaller clusters, and finally single-block schools one block
+  // at a time (queue 3).
+  int n_launches;
+  int cluster[kBatchMaxLaunches];
+  int blocks[kBatchMaxLaunches];
 };
 
-// Zeroes the work-list counters, then launches the cluster kernel on `s` and,
-// if L.filler_blocks > 0, the single-block filler on `side` (forked from and
-// joined back into `s` through the two events).
-cudaError_t launch_batch(const BatchLaunch& L, cudaStream_t s, cudaStream_t side,
-                         cudaEvent_t fork, cudaEvent_t join);
+// Zeroes the work-list counters, then enqueues launch 0 on `s` and launches
+// 1.. on side[0..] (forked from and joined back into `s` through `fork` and
+// join[0..]).
+cudaError_t launch_batch(const BatchLaunch& L, cudaStream_t s, const cudaStream_t* side,
+                         cudaEvent_t fork, const cudaEvent_t* join);
 int batch_max_clusters(int cluster, int acc);
 uint64_t batch_block_capacity();
 int batch_threads();

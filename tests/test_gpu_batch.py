@@ -174,3 +174,54 @@ def test_batch_argument_errors():
     assert e.value.status == fsb.FSB_ERR_UNSUPPORTED
     fsb.fsb_batch_step(b, 2)
     fsb.fsb_batch_destroy(b)
+
+
+def test_default_plan_runs_each_school_on_the_cluster_that_holds_it():
+    """With no forced cluster size every school goes to the queue of the
+    smallest cluster (1, 2, 4 or 8 blocks of 8192 fish) that holds it, one
+    concurrent launch per size, largest first, single blocks on the SMs left
+    over; the result is still every school's single-school trajectory."""
+    sizes = np.array([65536, 40000, 33000, 32768, 20000, 16385, 16384, 9000, 8193, 8192, 5000,
+                      700, 31, 1, 2, 64000, 12000, 30000, 4096], dtype=np.uint64)
+    offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    seeds = (3000 + np.arange(sizes.size)).astype(np.uint64)
+    tmpl = fsb.fsb_config_init(1, 0, step=1.5, init_weight_mode=1)
+    ts, state = make_state(offsets[-1])
+    b = fsb.fsb_batch_create(tmpl, offsets, seeds, state, init=True)
+    plan = fsb.fsb_batch_plan(b)
+    need = [1 if n <= 8192 else 2 if n <= 16384 else 4 if n <= 32768 else 8 for n in sizes]
+    assert plan["queue_schools"] == {c: need.count(c) for c in (8, 4, 2, 1)}
+    clusters = [l["cluster"] for l in plan["launches"]]
+    assert clusters[:3] == [8, 4, 2] and clusters == sorted(clusters, reverse=True)
+    for l in plan["launches"]:
+        assert l["blocks"] >= l["cluster"] and l["blocks"] % l["cluster"] == 0
+    info = fsb.fsb_batch_info(b)
+    assert info["cluster"] == 8 and info["n_big"] == sum(c > 1 for c in need)
+    steps = 5
+    stats = np.zeros(sizes.size * steps, fsb.STATS_DTYPE)
+    fsb.fsb_batch_step(b, steps, stats)
+    fsb.fsb_batch_destroy(b)
+    check_batch(tmpl, offsets, seeds, read_state(ts), stats, steps, tmpl.precision)
+
+
+def test_forced_cluster_size_and_back_to_the_default_plan():
+    sizes = np.array([20000, 9000, 100, 30000], dtype=np.uint64)
+    offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    seeds = (40 + np.arange(sizes.size)).astype(np.uint64)
+    tmpl = fsb.fsb_config_init(1, 0)
+    ts, state = make_state(offsets[-1])
+    b = fsb.fsb_batch_create(tmpl, offsets, seeds, state, init=True)
+    assert [l["cluster"] for l in fsb.fsb_batch_plan(b)["launches"]][:2] == [4, 2]
+    fsb.fsb_batch_set_cluster(b, 8)
+    plan = fsb.fsb_batch_plan(b)
+    assert plan["launches"][0]["cluster"] == 8 and plan["queue_schools"][8] == 3
+    with pytest.raises(fsb.FsbError) as e:
+        fsb.fsb_batch_set_cluster(b, 2)          # 30000 fish do not fit 2 blocks
+    assert e.value.status == fsb.FSB_ERR_UNSUPPORTED
+    assert fsb.fsb_batch_plan(b)["launches"][0]["cluster"] == 8   # unchanged
+    fsb.fsb_batch_set_cluster(b, 0)
+    assert fsb.fsb_batch_plan(b)["queue_schools"] == {8: 0, 4: 2, 2: 1, 1: 1}
+    stats = np.zeros(sizes.size * 4, fsb.STATS_DTYPE)
+    fsb.fsb_batch_step(b, 4, stats)
+    fsb.fsb_batch_destroy(b)
+    check_batch(tmpl, offsets, seeds, read_state(ts), stats, 4, tmpl.precision)
