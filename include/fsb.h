@@ -306,15 +306,24 @@ int fsb_run_batch(const fsb_config* tmpl, uint32_t n_schools, const uint64_t* of
 int fsb_set_kernel_timing(fsb_handle h, int enable);
 int fsb_kernel_time(fsb_handle h, double* fused_ms, uint64_t* fused_launches);
 
-/* Test hook for failure detection, resident path only (no counterpart in
- * the paper).  On the next fsb_step call, block `block` (>= 0; -1 clears)
- * skips its arrival at the grid barrier of step index `step` of that call,
- * so every block's bounded wait runs out; the call then reports
- * FSB_ERR_TIMEOUT at its next synchronising point, no block hangs, and the
- * school's state is left as it was before the call.  `timeout_ns` (0 keeps
- * the current value, default 1 s) bounds every device-side wait of the
- * handle from then on.  Nothing faults on the GPU: the failure is made on the
- * host side by withholding one arrival. */
+/* Test hook for failure detection (no counterpart in the paper).
+ * Nothing faults on the GPU: the failure is made by withholding one
+ * arrival or one copy.  `block` >= 0 arms the hook and -1 clears it.
+ * `timeout_ns` (0 keeps the current value, default 1 s) bounds every
+ * device-side wait of the handle from then on.
+ *   Resident path: on later fsb_step calls, block `block` skips its arrival
+ *     at the grid barrier of step index `step` of the call, so every block's
+ *     bounded wait runs out.  The school's state is left as it was before
+ *     the call.
+ *   Streaming path, copy-ring kernels (stream kernel 2 or 3): in pass
+ *     `step` of later calls, block `block` withholds the first bulk copy of
+ *     its ring, so its wait runs out and the others give up.  Pass 0 swims
+ *     only, passes 1 .. n-1 are fused, pass n settles.  The school's state is
+ *     then undefined, since passes update it in place.  Any other stream
+ *     kernel -> FSB_ERR_UNSUPPORTED.
+ * Either way the call reports FSB_ERR_TIMEOUT at its next synchronising
+ * point and no block hangs. The status stays latched: later calls and
+ * reads on the handle report it, so destroy the handle. */
 int fsb_set_fault_injection(fsb_handle h, int block, uint32_t step, uint64_t timeout_ns);
 
 /* Launch shape of a handle's kernels (0 in a field = the library's choice).

@@ -705,12 +705,25 @@ int fsb_get_tuning(fsb_handle h, fsb_tuning* t) {
 
 int fsb_set_fault_injection(fsb_handle h, int block, uint32_t step, uint64_t timeout_ns) {
   if (!h) return fail(FSB_ERR_INVALID_ARG, "handle is NULL");
-  if (h->path != FSB_PATH_RESIDENT)
-    return fail(FSB_ERR_UNSUPPORTED, "fault injection applies to the resident path only");
-  if (block >= h->res.grid) return fail(FSB_ERR_INVALID_ARG, "block out of range");
-  h->res.inject_cta = block < 0 ? -1 : block;
-  h->res.inject_step = step;
-  if (timeout_ns) h->res.timeout_ns = timeout_ns;
+  if (h->path == FSB_PATH_RESIDENT) {
+    if (block >= h->res.grid) return fail(FSB_ERR_INVALID_ARG, "block out of range");
+    h->res.inject_cta = block < 0 ? -1 : block;
+    h->res.inject_step = step;
+    if (timeout_ns) h->res.timeout_ns = timeout_ns;
+    return FSB_OK;
+  }
+  StreamLaunch& L = h->launch;
+  if (!L.tma)
+    return fail(FSB_ERR_UNSUPPORTED,
+                "fault injection needs the resident path or a copy-ring stream kernel");
+  if (block >= L.grid) return fail(FSB_ERR_INVALID_ARG, "block out of range");
+  FSB_CUDA(cudaStreamSynchronize(h->stream));
+  L.inject_block = block < 0 ? -1 : block;
+  L.inject_pass = step;
+  if (timeout_ns) L.timeout_ns = timeout_ns;
+  // launch arguments are baked into the cached graphs
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+  h->graphs.clear();
   return FSB_OK;
 }
 

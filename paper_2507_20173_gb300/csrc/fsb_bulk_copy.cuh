@@ -1,9 +1,10 @@
 // fsb_bulk_copy.cuh -- bulk asynchronous copies into shared memory and the
 // mbarriers they complete on, for the streaming kernels' copy rings.
 //
-// Every wait is bounded by a %globaltimer deadline; a thread that gives up
-// latches FSB_ERR_TIMEOUT in the control word (once per call) and returns
-// false, so a copy that never lands cannot hang the GPU.
+// Every wait is bounded by a %globaltimer deadline (the handle's timeout,
+// 1 s by default); a thread that gives up latches FSB_ERR_TIMEOUT in the
+// control word (once per call) and returns false, so a copy that never
+// lands cannot hang the GPU.
 #pragma once
 
 #include <cstdint>
@@ -12,8 +13,6 @@
 #include "fsb_reduce.cuh"
 
 namespace fsb {
-
-constexpr unsigned long long kTmaWaitNs = 1000000000ull;  // 1 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -68,14 +67,14 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
 // Bounded wait for phase `parity` of *bar.  Returns false (status latched)
 // when the deadline passes or another block has already failed.
 __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity,
-                                                  Ctl* ctl) {
+                                                  Ctl* ctl, unsigned long long timeout_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
   for (unsigned spins = 0;; ++spins) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((spins & 63u) == 63u) {
       if (ld_relaxed_gpu(&ctl->status) != 0) return false;
-      if (global_ns() - t0 > kTmaWaitNs) {
+      if (global_ns() - t0 > timeout_ns) {
         if (atomicCAS(&ctl->status, 0, static_cast<int>(FSB_ERR_TIMEOUT)) == 0)
           atomicExch(&ctl->timeout_site, 0x7A000000u | blockIdx.x);
         return false;

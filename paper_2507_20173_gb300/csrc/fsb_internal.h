@@ -61,6 +61,9 @@ struct StreamLaunch {
   BlockPartial* partials;
   fsb_step_stats* ring;
   uint32_t ring_cap;
+  unsigned long long timeout_ns = 0;  // bound of the copy rings' waits (0: 1 s)
+  int inject_block = -1;               // test hook (copy-ring kernels): block that withholds
+  uint32_t inject_pass = 0;            //   its first copy in this pass of a call; -1 = none
 };
 
 cudaError_t launch_stream_pass(const StreamLaunch& L, int pass_kind, cudaStream_t s);

@@ -26,6 +26,9 @@ struct StreamArgs {
   BlockPartial* partials;
   fsb_step_stats* ring;
   uint32_t ring_cap;
+  unsigned long long timeout_ns;  // bound of every wait in the copy rings
+  int inject_block;               // test hook: this block withholds the first copy
+  uint32_t inject_pass;           //   of its ring in this pass of a call (-1: none)
 };
 
 template <typename Real>
@@ -50,6 +53,9 @@ StreamArgs<Real> make_stream_args(const StreamLaunch& L) {
   a.partials = L.partials;
   a.ring = L.ring;
   a.ring_cap = L.ring_cap;
+  a.timeout_ns = L.timeout_ns ? L.timeout_ns : 1000000000ull;
+  a.inject_block = L.inject_block;
+  a.inject_pass = L.inject_pass;
   return a;
 }
 
@@ -58,6 +64,10 @@ StreamArgs<Real> make_stream_args(const StreamLaunch& L) {
 template <int PASS>
 __device__ __forceinline__ bool pass_prologue(const Ctl* ctl, Ctl* wctl, uint32_t ring_cap,
                                               uint32_t& j, uint64_t& base) {
+  // a pass of a call that already failed does nothing.  The status word can
+  // be latched by another block while this one starts, so the block takes
+  // one decision for all its threads (every thread calls the prologue).
+  if (__syncthreads_or(ld_relaxed_gpu(&ctl->status) != 0)) return false;
   j = ctl->pass;
   base = ctl->base_step;
   if ((PASS != kSwimOnly && (j == 0 || j > ring_cap)) || (PASS != kSettle && j >= ring_cap)) {

@@ -65,7 +65,10 @@ __global__ void __launch_bounds__(THREADS) stream_pass_tma_kernel(StreamArgs<flo
   __syncthreads();
 
   float* const src[4] = {a.x, a.y, a.w, a.pv};
+  // test hook: this block withholds the first copy of its ring in pass j
+  const bool withhold = static_cast<int>(blockIdx.x) == a.inject_block && j == a.inject_pass;
   auto issue = [&](uint64_t k) {  // elected thread only
+    if (withhold && k == 0) return;
     const int s = static_cast<int>(k % STAGES);
     const uint64_t off = (blockIdx.x + k * gridDim.x) * static_cast<uint64_t>(kTile);
     mbar_expect_tx(&R.full[s], kArrays * kTileBytes);
@@ -82,7 +85,7 @@ __global__ void __launch_bounds__(THREADS) stream_pass_tma_kernel(StreamArgs<flo
   for (; k < my_tiles; ++k) {
     const int s = static_cast<int>(k % STAGES);
     const unsigned parity = static_cast<unsigned>((k / STAGES) & 1);
-    bool mine = mbar_wait_bounded(&R.full[s], parity, a.ctl);
+    bool mine = mbar_wait_bounded(&R.full[s], parity, a.ctl, a.timeout_ns);
     float4 v[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q)
@@ -122,7 +125,7 @@ __global__ void __launch_bounds__(THREADS) stream_pass_tma_kernel(StreamArgs<flo
         const int s = static_cast<int>(q % STAGES);
         const unsigned long long t0 = global_ns();
         while (!mbar_try_wait(&R.full[s], static_cast<unsigned>((q / STAGES) & 1)) &&
-               global_ns() - t0 < kTmaWaitNs) {
+               global_ns() - t0 < a.timeout_ns) {
         }
       }
     }

@@ -96,22 +96,26 @@ __global__ void __launch_bounds__(THREADS + 32, WsMinBlocks<THREADS>::value)
         // the stage's previous tile (k - STAGES) must be released by every
         // consumer warp: completion number k / STAGES - 1 of empty[s]
         if (k >= static_cast<uint64_t>(STAGES) &&
-            !mbar_wait_bounded(&R.empty[s], static_cast<unsigned>((k / STAGES - 1) & 1), a.ctl)) {
+            !mbar_wait_bounded(&R.empty[s], static_cast<unsigned>((k / STAGES - 1) & 1), a.ctl,
+                               a.timeout_ns)) {
           ok = false;
           break;
         }
+        issued = k + 1;
+        // test hook: this block withholds the first copy of its ring in pass j
+        if (k == 0 && static_cast<int>(blockIdx.x) == a.inject_block && j == a.inject_pass)
+          continue;
         const uint64_t off = (blockIdx.x + k * gridDim.x) * static_cast<uint64_t>(kTile);
         mbar_expect_tx(&R.full[s], kArrays * kTileBytes);
         for (int q = 0; q < kArrays; ++q)
           bulk_g2s(R.buf[s][q], src[q] + off, kTileBytes, &R.full[s]);
-        issued = k + 1;
       }
     }
   } else {
     for (uint64_t k = 0; k < my_tiles; ++k) {
       const int s = static_cast<int>(k % STAGES);
       const unsigned parity = static_cast<unsigned>((k / STAGES) & 1);
-      const bool mine = mbar_wait_bounded(&R.full[s], parity, a.ctl);
+      const bool mine = mbar_wait_bounded(&R.full[s], parity, a.ctl, a.timeout_ns);
       if (!__all_sync(0xffffffffu, mine)) {
         ok = false;
         break;
@@ -155,7 +159,7 @@ __global__ void __launch_bounds__(THREADS + 32, WsMinBlocks<THREADS>::value)
         const int s = static_cast<int>(q % STAGES);
         const unsigned long long t0 = global_ns();
         while (!mbar_try_wait(&R.full[s], static_cast<unsigned>((q / STAGES) & 1)) &&
-               global_ns() - t0 < kTmaWaitNs) {
+               global_ns() - t0 < a.timeout_ns) {
         }
       }
     }

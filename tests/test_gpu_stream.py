@@ -369,3 +369,54 @@ def test_read_state_objective_over_chunks(precision):
     assert want.dtype == x.dtype
     bad = np.nonzero(got["cur"] != want)[0]
     assert bad.size == 0, "cur differs at %d fish, first %d" % (bad.size, bad[0])
+
+
+@pytest.mark.parametrize("kernel", [2, 3])
+@pytest.mark.parametrize("pass_index", [0, 2, 4])
+def test_withheld_copy_times_out_without_hanging(kernel, pass_index):
+    """Failure detection without a GPU fault: one block withholds the first
+    bulk copy of its ring in one pass of a call (set from the host).  Its
+    bounded wait runs out after 50 ms, every other block gives up, the passes
+    behind it do nothing, the call reports FSB_ERR_TIMEOUT, and the context
+    stays usable."""
+    import time
+    s = fsb.School.create(stream_cfg(1 << 22, 8))
+    fsb.fsb_set_tuning(s.handle, stream_kernel=kernel)
+    s.step(2)
+    fsb.fsb_set_fault_injection(s.handle, 5, pass_index, 50_000_000)
+    t0 = time.perf_counter()
+    with pytest.raises(fsb.FsbError) as e:
+        s.step(4, stats=True)                   # passes 0 (swim) .. 4 (settle)
+    assert e.value.status == fsb.FSB_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 10.0
+    with pytest.raises(fsb.FsbError) as e:
+        s.read()                                # the latched status is reported
+    assert e.value.status == fsb.FSB_ERR_TIMEOUT
+    s.destroy()
+    t = torch.ones(1000, device="cuda")
+    assert float(t.sum().item()) == 1000.0
+    cfg = stream_cfg(50_001, 3)
+    ok = fsb.School.create(cfg)
+    fsb.fsb_set_tuning(ok.handle, stream_kernel=kernel)
+    stats = ok.step(3, stats=True)
+    got = ok.read()
+    ok.destroy()
+    ref = oracle.init(oracle_config(cfg))
+    ref_stats = oracle.run(oracle_config(cfg), ref, 0, 3)
+    assert_state_equal(got, ref, "after a failed handle")
+    assert_stats_match(stats, ref_stats, cfg.precision, "after a failed handle")
+
+
+def test_fault_injection_needs_a_copy_ring_kernel():
+    s = fsb.School.create(stream_cfg(10_000, 1))
+    fsb.fsb_set_tuning(s.handle, stream_kernel=1)
+    with pytest.raises(fsb.FsbError) as e:
+        fsb.fsb_set_fault_injection(s.handle, 0, 1, 0)
+    assert e.value.status == fsb.FSB_ERR_UNSUPPORTED
+    fsb.fsb_set_tuning(s.handle, stream_kernel=2)
+    with pytest.raises(fsb.FsbError) as e:
+        fsb.fsb_set_fault_injection(s.handle, 100000, 1, 0)
+    assert e.value.status == fsb.FSB_ERR_INVALID_ARG
+    fsb.fsb_set_fault_injection(s.handle, -1, 0, 0)   # clearing is always fine
+    s.step(2)
+    s.destroy()
