@@ -113,14 +113,28 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash():
+def _code_only(text):
+    """Source text without comments and blank runs: the profile records are
+    keyed to the code, so a comment edit does not void them."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
+def _sources_hash(names):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2507_20173_gb300", "csrc")
-    for name in ("fsb_stream.cu", "fsb_stream_tma.cu", "fsb_stream_ws.cu", "fsb_bulk_copy.cuh",
-                 "fsb_stream_common.cuh", "fsb_device.cuh", "fsb_reduce.cuh"):
-        with open(os.path.join(csrc, name), "rb") as f:
-            h.update(f.read())
+    for name in names:
+        with open(os.path.join(csrc, name)) as f:
+            h.update(_code_only(f.read()).encode())
     return h.hexdigest()[:16]
+
+
+def kernel_source_hash():
+    return _sources_hash(("fsb_stream.cu", "fsb_stream_tma.cu", "fsb_stream_ws.cu",
+                          "fsb_bulk_copy.cuh", "fsb_stream_common.cuh", "fsb_device.cuh",
+                          "fsb_reduce.cuh"))
 
 
 # Sources of the two on-chip kernels, whose roofline is instruction issue.
@@ -131,12 +145,7 @@ ALU_KERNEL_SOURCES = {
 
 
 def alu_source_hash(kernel):
-    h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2507_20173_gb300", "csrc")
-    for name in ALU_KERNEL_SOURCES[kernel]:
-        with open(os.path.join(csrc, name), "rb") as f:
-            h.update(f.read())
-    return h.hexdigest()[:16]
+    return _sources_hash(ALU_KERNEL_SOURCES[kernel])
 
 
 def alu_instr_per_fish_step(kernel, precision):

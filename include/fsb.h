@@ -89,9 +89,9 @@ typedef enum {
  *   path              fsb_path (ignored by fsb_run_batch)
  *   swim_mode         0 (default): each coordinate moves by (2u - 1) * s;
  *                     1: by (2u - 1) * ((w / w0) * s) with the fish's weight
- *                     before the step's eat -- the paper's weight that
- *                     "affects mobility" (Sec. 2.1.1, 2.1.2); a fish of
- *                     weight 0 stays put.  Not on the resident path.
+ *                     before the step's eat -- a reading of the paper's
+ *                     weight-dependent mobility (Sec. 2.1.1, 2.1.2); a fish
+ *                     of weight 0 stays put.  Every path runs it.
  *   feed_mode         0 (default): w += delta / max|delta|;
  *                     1: w += (prev - cur) / E with E = max(prev - cur), the
  *                     value the paper's eat() reduces (Sec. 2.3.2); nobody

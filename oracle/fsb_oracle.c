@@ -36,8 +36,9 @@
  *                 positions after this step's swim and the weights after
  *                 this step's eat (reading: weighted centre of the school)
  *
- * Variants (off by default; the paper says weight affects mobility,
- * Sec. 2.1.1 / 2.1.2, and its eat() reduces max(prev - cur), Sec. 2.3.2):
+ * Variants (off by default; the paper ties a fish's movement to its weight
+ * without a rule, Sec. 2.1.1 / 2.1.2, and its eat() reduces max(prev - cur),
+ * Sec. 2.3.2):
  *   swim_mode 1   the move's half-width is s * (w / w0) with the fish's
  *                 weight before this step's eat: heavier fish swim farther,
  *                 a fish of weight 0 stays put

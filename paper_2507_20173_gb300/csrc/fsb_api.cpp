@@ -274,8 +274,8 @@ int run_stream(fsb_school* h, uint32_t n) {
 // Pick (fish per thread, block, grid) so a school of n fish sits in
 // registers across at most one block per SM.  Returns false if it does not
 // fit on chip.
-bool resident_config(int sms, int acc, uint64_t n, fsb::ResidentLaunch* R, int want_fpt = 0,
-                     int want_block = 0) {
+bool resident_config(int sms, int acc, int swim_mode, uint64_t n, fsb::ResidentLaunch* R,
+                     int want_fpt = 0, int want_block = 0) {
   const int fpts[] = {4, 8, 12, 16};
   for (int fpt : fpts) {
     if (want_fpt && fpt != want_fpt) continue;
@@ -293,7 +293,7 @@ bool resident_config(int sms, int acc, uint64_t n, fsb::ResidentLaunch* R, int w
     const uint64_t threads = (slice + fpt - 1) / fpt;
     const int block = static_cast<int>(((threads + 31) / 32) * 32);
     if (block > maxb) continue;
-    if (fsb::resident_blocks_per_sm(fpt, acc, block) < 1) continue;
+    if (fsb::resident_blocks_per_sm(fpt, acc, block, swim_mode) < 1) continue;
     R->fpt = fpt;
     R->block = block;
     R->grid = static_cast<int>((n + slice - 1) / slice);
@@ -529,14 +529,9 @@ int fsb_create(const fsb_config* cfg, const fsb_state_dev* buffers, const fsb_st
     int r0 = configure_stream(h, 0, 0, 0, 0);
     if (r0 != FSB_OK) return r0;
 
-    // resident path: binary32 state that fits in registers across the SMs;
-    // its pipelined step swims ahead of the eat, so it runs the default swim
-    // only (the weight-scaled swim needs the step's eat first)
+    // resident path: binary32 state that fits in registers across the SMs
     fsb::ResidentLaunch& R = h->res;
-    if (cfg->path == FSB_PATH_RESIDENT && cfg->swim_mode != 0)
-      return fail(FSB_ERR_UNSUPPORTED, "resident path: the weight-scaled swim runs streaming");
-    const bool fits = !dbl && cfg->swim_mode == 0 &&
-                      resident_config(sms, h->launch.acc, cfg->n_fish, &R);
+    const bool fits = !dbl && resident_config(sms, h->launch.acc, cfg->swim_mode, cfg->n_fish, &R);
     if (cfg->path == FSB_PATH_RESIDENT && !fits)
       return fail(FSB_ERR_UNSUPPORTED,
                   "resident path: school of %llu fish does not fit on chip (binary32 only)",
@@ -555,6 +550,7 @@ int fsb_create(const fsb_config* cfg, const fsb_state_dev* buffers, const fsb_st
       R.w0 = cfg->w0;
       R.w_min = cfg->w_min;
       R.w_max = cfg->w_max;
+      R.swim_mode = cfg->swim_mode;
       R.feed_mode = cfg->feed_mode;
       R.acc = h->launch.acc;
       h->tuning.resident_fpt = R.fpt;
@@ -685,7 +681,8 @@ int fsb_set_tuning(fsb_handle h, const fsb_tuning* t) {
   }
   if (h->path == FSB_PATH_RESIDENT && (t->resident_fpt || t->resident_block)) {
     fsb::ResidentLaunch R = h->res;
-    if (!resident_config(h->sms, R.acc, h->cfg.n_fish, &R, t->resident_fpt, t->resident_block)) {
+    if (!resident_config(h->sms, R.acc, R.swim_mode, h->cfg.n_fish, &R, t->resident_fpt,
+                         t->resident_block)) {
       h->launch = saved;
       h->tuning = saved_t;
       return fail(FSB_ERR_INVALID_ARG, "resident tuning does not fit this school");

@@ -153,7 +153,7 @@ __device__ __forceinline__ Physics<Real> kernel_physics(const Physics<Real>& p) 
 }
 
 // Half-width of one fish's move: s, or (w / w0) * s when the swim is
-// weight-scaled (the paper's weight that affects mobility).
+// weight-scaled (a reading of the paper's weight-dependent movement).
 template <typename Real>
 __device__ __forceinline__ Real swim_width(const Physics<Real>& ph, Real w) {
   using A = Arith<Real>;

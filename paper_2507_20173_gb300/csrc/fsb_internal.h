@@ -92,7 +92,8 @@ struct ResidentLaunch {
   uint64_t seed;
   uint32_t school;
   double pond_half, step, w0, w_min, w_max;
-  int feed_mode;    // the resident kernel runs only the default swim
+  int swim_mode;    // 1: weight-scaled swim (swims each step after the eat)
+  int feed_mode;
   int acc;          // AccMode
   int fpt;          // fish per thread: 4, 8, 12 or 16
   int block;        // threads per block (<= resident_max_block(fpt))
@@ -110,7 +111,7 @@ struct ResidentLaunch {
 
 cudaError_t launch_resident(const ResidentLaunch& L, cudaStream_t s);
 int resident_max_block(int fpt);
-int resident_blocks_per_sm(int fpt, int acc, int block);
+int resident_blocks_per_sm(int fpt, int acc, int block, int swim_mode);
 size_t resident_smem_bytes(int fpt, int block);
 
 // Work queues of a batch: queue t (t = 0, 1, 2) holds the schools run on

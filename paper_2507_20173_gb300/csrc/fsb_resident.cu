@@ -71,7 +71,11 @@ __device__ __forceinline__ bool grid_wait(const ResidentArgs& a, unsigned k) {
 // step u + 1 (positions do not depend on weights).  Eating step u then needs
 // that step's delta and post-swim position, which wait in a double-buffered
 // shared-memory slab `pend[buffer][delta | x | y][fish slot][thread]`.
-template <int FPT, int MAXB, int ACC>
+// WSWIM: the weight-scaled swim (each fish's half-width is (w / w0) s with
+// its weight after the previous step's eat).  The swim of step u + 1 then
+// waits for the eat of step u, so it runs after it instead of beside the
+// barrier.
+template <int FPT, int MAXB, int ACC, bool WSWIM>
 __global__ void __launch_bounds__(MAXB, 1) resident_kernel(ResidentArgs a) {
   using Acc = SumAcc<ACC>;
   using Sum = typename Acc::Sum;
@@ -133,7 +137,8 @@ __global__ void __launch_bounds__(MAXB, 1) resident_kernel(ResidentArgs a) {
       if (k < nk) {
         pv[k] = f[k];
         if ((k & 1) == 0) r = pair_draw(a.key, a.school, fish(k) >> 1, t);
-        swim(x[k], y[k], r.v[2 * (k & 1)], r.v[2 * (k & 1) + 1], a.ph.step, a.ph);
+        swim(x[k], y[k], r.v[2 * (k & 1)], r.v[2 * (k & 1) + 1],
+             WSWIM ? swim_width(a.ph, w[k]) : a.ph.step, a.ph);
         f[k] = objective(x[k], y[k]);
         const float d = __fsub_rn(f[k], pv[k]);
         const uint32_t m = abs_bits(d);
@@ -185,7 +190,7 @@ __global__ void __launch_bounds__(MAXB, 1) resident_kernel(ResidentArgs a) {
     const bool has_next = u < a.n_steps;
     // ---- A: swim of step u + 1 while the grid settles M_u
     uint32_t mb = 0, ek = 0;
-    if (has_next) swim_all(u + 1, mb, ek);
+    if (!WSWIM && has_next) swim_all(u + 1, mb, ek);
 
     // ---- B: M_u
     if (tid == 0) {
@@ -227,6 +232,8 @@ __global__ void __launch_bounds__(MAXB, 1) resident_kernel(ResidentArgs a) {
         acc.add(w[k], P(u & 1u, 1, k), P(u & 1u, 2, k));
       }
     }
+    // ---- A (weight-scaled swim): swim of step u + 1 with the eaten weights
+    if (WSWIM && has_next) swim_all(u + 1, mb, ek);
 
     // ---- D: one block reduction for M_{u+1}, E_{u+1} and the sums of u
     mb = warp_max(mb);
@@ -338,23 +345,29 @@ struct MaxBlock<16> {
   static constexpr int value = 512;
 };
 
-template <int FPT>
-const void* pick_acc(int acc) {
+template <int FPT, int ACC>
+const void* kernel_ptr(bool wswim) {
   constexpr int MB = MaxBlock<FPT>::value;
+  if (wswim) return reinterpret_cast<const void*>(&resident_kernel<FPT, MB, ACC, true>);
+  return reinterpret_cast<const void*>(&resident_kernel<FPT, MB, ACC, false>);
+}
+
+template <int FPT>
+const void* pick_acc(int acc, bool wswim) {
   switch (acc) {
-    case kAccPlain32: return reinterpret_cast<const void*>(&resident_kernel<FPT, MB, kAccPlain32>);
-    case kAccKahan32: return reinterpret_cast<const void*>(&resident_kernel<FPT, MB, kAccKahan32>);
-    case kAccF64: return reinterpret_cast<const void*>(&resident_kernel<FPT, MB, kAccF64>);
+    case kAccPlain32: return kernel_ptr<FPT, kAccPlain32>(wswim);
+    case kAccKahan32: return kernel_ptr<FPT, kAccKahan32>(wswim);
+    case kAccF64: return kernel_ptr<FPT, kAccF64>(wswim);
     default: return nullptr;
   }
 }
 
-const void* pick(int fpt, int acc) {
+const void* pick(int fpt, int acc, bool wswim) {
   switch (fpt) {
-    case 4: return pick_acc<4>(acc);
-    case 8: return pick_acc<8>(acc);
-    case 12: return pick_acc<12>(acc);
-    case 16: return pick_acc<16>(acc);
+    case 4: return pick_acc<4>(acc, wswim);
+    case 8: return pick_acc<8>(acc, wswim);
+    case 12: return pick_acc<12>(acc, wswim);
+    case 16: return pick_acc<16>(acc, wswim);
     default: return nullptr;
   }
 }
@@ -375,8 +388,8 @@ size_t resident_smem_bytes(int fpt, int block) {
   return static_cast<size_t>(2) * 3 * fpt * block * sizeof(float);
 }
 
-int resident_blocks_per_sm(int fpt, int acc, int block) {
-  const void* fn = pick(fpt, acc);
+int resident_blocks_per_sm(int fpt, int acc, int block, int swim_mode) {
+  const void* fn = pick(fpt, acc, swim_mode != 0);
   if (!fn) return 0;
   const size_t smem = resident_smem_bytes(fpt, block);
   // the attribute is per kernel, shared by every handle: always the largest
@@ -391,7 +404,7 @@ int resident_blocks_per_sm(int fpt, int acc, int block) {
 }
 
 cudaError_t launch_resident(const ResidentLaunch& L, cudaStream_t s) {
-  const void* fn = pick(L.fpt, L.acc);
+  const void* fn = pick(L.fpt, L.acc, L.swim_mode != 0);
   if (!fn || L.grid < 1 || L.block < 32 || L.block > resident_max_block(L.fpt))
     return cudaErrorInvalidValue;
   ResidentArgs a;
@@ -409,7 +422,7 @@ cudaError_t launch_resident(const ResidentLaunch& L, cudaStream_t s) {
   a.ph.w0 = static_cast<float>(L.w0);
   a.ph.w_min = static_cast<float>(L.w_min);
   a.ph.w_max = static_cast<float>(L.w_max);
-  a.ph.swim_mode = 0;
+  a.ph.swim_mode = L.swim_mode;
   a.ph.feed_mode = L.feed_mode;
   a.base_step = L.base_step;
   a.n_steps = L.n_steps;

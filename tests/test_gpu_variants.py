@@ -1,6 +1,6 @@
 """GPU parity of the two model variants against the CPU oracle:
-swim_mode 1 (the move's half-width scales with the fish's weight, the
-paper's weight that affects mobility) and feed_mode 1 (feeding normalised by
+swim_mode 1 (the move's half-width scales with the fish's weight, a reading
+of the paper's weight-dependent movement) and feed_mode 1 (feeding normalised by
 the paper's eat() value max(prev - cur)), on every path that runs them."""
 import numpy as np
 import pytest
@@ -60,20 +60,23 @@ def test_binary64_state_variants(swim_mode, feed_mode):
     run_and_compare(cfg, 11)
 
 
+@pytest.mark.parametrize("swim_mode,feed_mode", MODES)
 @pytest.mark.parametrize("n", [5000, 300_001])
-def test_resident_paper_feeding(n):
-    cfg = fsb.fsb_config_init(n, 3, path=fsb.FSB_PATH_RESIDENT, feed_mode=1, init_weight_mode=1,
-                              step=2.0)
+def test_resident_variants(swim_mode, feed_mode, n):
+    """The resident kernel runs both variants; with the weight-scaled swim it
+    swims each step after the previous step's eat instead of beside the grid
+    barrier."""
+    cfg = fsb.fsb_config_init(n, 3, path=fsb.FSB_PATH_RESIDENT, swim_mode=swim_mode,
+                              feed_mode=feed_mode, init_weight_mode=1, step=2.0)
     assert run_and_compare(cfg, 13, calls=[6, 7]) == fsb.FSB_PATH_RESIDENT
 
 
-def test_weighted_swim_runs_streaming():
-    cfg = fsb.fsb_config_init(100_000, 3, path=fsb.FSB_PATH_RESIDENT, swim_mode=1)
-    with pytest.raises(fsb.FsbError) as e:
-        fsb.School.create(cfg)
-    assert e.value.status == fsb.FSB_ERR_UNSUPPORTED
-    cfg = fsb.fsb_config_init(100_000, 3, swim_mode=1)
-    assert run_and_compare(cfg, 5) == fsb.FSB_PATH_STREAM
+@pytest.mark.parametrize("fpt", [4, 8, 12, 16])
+def test_resident_weighted_swim_every_fish_per_thread(fpt):
+    cfg = fsb.fsb_config_init(200_000, 11, path=fsb.FSB_PATH_RESIDENT, swim_mode=1,
+                              init_weight_mode=1, step=3.0)
+    assert run_and_compare(cfg, 9, tuning={"resident_fpt": fpt},
+                           calls=[4, 5]) == fsb.FSB_PATH_RESIDENT
 
 
 @pytest.mark.parametrize("swim_mode,feed_mode", MODES)
