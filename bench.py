@@ -169,17 +169,20 @@ def issue_peak(sms, clocks):
     return sms * 4 * 32 * mhz * 1e6 / 1e9
 
 
-def ncu_traffic(n_fish, precision):
+def ncu_traffic(n_fish, precision, stream_kernel):
     """DRAM bytes per fused-pass launch from the committed ncu summary,
-    scaled to this launch's fish count; None if the kernel changed since."""
+    scaled to this launch's fish count; None if the summary is for another
+    stream kernel or precision, or the kernels changed since."""
     p = os.path.join(ROOT, "profiles", "stream_fused_traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
-        d = json.load(f)
-    if d.get("kernel_source_hash") != kernel_source_hash() or d.get("precision") != precision:
-        return None
-    return float(d["dram_bytes_per_fish"]) * n_fish
+        records = json.load(f)["records"]
+    for d in records:
+        if (d.get("kernel_source_hash") == kernel_source_hash() and d.get("precision") == precision
+                and d.get("stream_kernel") == stream_kernel):
+            return float(d["dram_bytes_per_fish"]) * n_fish
+    return None
 
 
 class ClockSampler:
@@ -594,7 +597,7 @@ def run_ours(args, world, rank, local, pg):
         roof["achieved"] = rate * ipfs / 1e9 if (rate and ipfs) else None
     else:
         achieved = bytes_per_fish_step * n / avg_fused_s / 1e9 if avg_fused_s else None
-        traffic = ncu_traffic(n, args.precision)
+        traffic = ncu_traffic(n, args.precision, tuning["stream_kernel"])
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
                 "peak_source": peak_kind + " hbm_gbs (STREAM copy)",

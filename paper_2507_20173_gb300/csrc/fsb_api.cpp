@@ -311,9 +311,10 @@ constexpr uint64_t kCurChunk = 1ull << 22;
 int configure_stream(fsb_school* h, int kernel, int block, int blocks_per_sm, int stages) {
   StreamLaunch L = h->launch;
   const bool tma_ok = !L.real_is_double && L.vec == 4;
-  // defaults measured on GB300 at N = 2^28: bulk-copy ring, 512 threads, 2
-  // stages (0.92 of the copy peak); vector loads, 256 threads, 4 blocks/SM
-  if (kernel == 0) kernel = tma_ok ? 2 : 1;
+  // default measured on GB300 at N = 2^28: vector loads, 256 threads, 4
+  // blocks per SM (0.96 of the copy peak, against 0.91 for the bulk-copy
+  // ring and 0.90 for its warp-specialised form, timed back to back)
+  if (kernel == 0) kernel = 1;
   if (stages == 0) stages = 2;
   if (stages < 2 || stages > 4) return fail(FSB_ERR_INVALID_ARG, "stream stages must be 2..4");
   if ((kernel == 2 || kernel == 3) && !tma_ok)
