@@ -33,7 +33,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libfsb_oracle.so")
-_SOURCES = ("philox.c", "fsb_oracle.c", "fsb_oracle.h")
+_SOURCES = ("philox.c", "collective.c", "fsb_oracle.c", "fsb_oracle.h")
 
 CFLAGS = ["-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math",
           "-fPIC", "-Wall", "-Wextra"]
@@ -44,7 +44,9 @@ FISH_F64 = np.dtype([("x", "<f8"), ("y", "<f8"), ("weight", "<f8"),
                      ("prevObjective", "<f8"), ("currentObjective", "<f8")])
 STATS = np.dtype([("max_abs_delta", "<f8"), ("eat_max_diff", "<f8"),
                   ("sum_w", "<f8"), ("sum_wx", "<f8"), ("sum_wy", "<f8"),
-                  ("sum_abs_wx", "<f8"), ("sum_abs_wy", "<f8")])
+                  ("sum_abs_wx", "<f8"), ("sum_abs_wy", "<f8"),
+                  ("inst_x", "<f8"), ("inst_y", "<f8"), ("vol_bx", "<f8"),
+                  ("vol_by", "<f8"), ("vol_dw", "<f8")])
 
 
 def build(force: bool = False) -> str:
@@ -55,7 +57,7 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB_PATH) >= newest_src):
         return _LIB_PATH
     objs = []
-    units = [("philox.c", [], "philox.o"),
+    units = [("philox.c", [], "philox.o"), ("collective.c", [], "collective.o"),
              ("fsb_oracle.c", ["-DFSBO_REAL=float", "-DFSBO_SFX=f32"], "oracle_f32.o"),
              ("fsb_oracle.c", ["-DFSBO_REAL=double", "-DFSBO_SFX=f64"], "oracle_f64.o")]
     for src, defs, obj in units:
@@ -75,7 +77,8 @@ class _CConfig(ctypes.Structure):
                 ("pond_half", ctypes.c_double), ("step", ctypes.c_double),
                 ("w0", ctypes.c_double), ("w_min", ctypes.c_double),
                 ("w_max", ctypes.c_double), ("swim_mode", ctypes.c_int32),
-                ("feed_mode", ctypes.c_int32)]
+                ("feed_mode", ctypes.c_int32), ("collective_mode", ctypes.c_int32),
+                ("step_vol", ctypes.c_double)]
 
 
 @dataclass
@@ -92,12 +95,14 @@ class Config:
     w_max: float = 2.0
     swim_mode: int = 0     # 1: half-width s * (w / w0) (weight-scaled swim)
     feed_mode: int = 0     # 1: normalise feeding by the paper's max(prev - cur)
+    collective_mode: int = 0   # 1: instinctive and volitive movements
+    step_vol: float = 0.1      # volitive step
 
     def c(self) -> _CConfig:
         return _CConfig(self.n_fish, self.seed, self.school_id,
                         self.init_weight_mode, self.pond_half, self.step,
                         self.w0, self.w_min, self.w_max, self.swim_mode,
-                        self.feed_mode)
+                        self.feed_mode, self.collective_mode, self.step_vol)
 
 
 _lib = None
@@ -112,6 +117,10 @@ def lib():
         L.fsbo_philox4x32_10.argtypes = [P, P, P]
         L.fsbo_swim_words.argtypes = [cfgp, ctypes.c_uint64, ctypes.c_uint32, P]
         L.fsbo_init_words.argtypes = [cfgp, ctypes.c_uint64, P]
+        L.fsbo_volitive_word.argtypes = [cfgp, ctypes.c_uint64, ctypes.c_uint32]
+        L.fsbo_volitive_word.restype = ctypes.c_uint32
+        L.fsbo_grid_exponent.argtypes = [ctypes.c_uint64, ctypes.c_double]
+        L.fsbo_grid_exponent.restype = ctypes.c_int
         for sfx in ("f32", "f64"):
             getattr(L, "fsbo_init_" + sfx).argtypes = [cfgp, P]
             getattr(L, "fsbo_init_" + sfx).restype = ctypes.c_int
@@ -159,6 +168,15 @@ def init_words(cfg: Config, i: int) -> np.ndarray:
     c = cfg.c()
     lib().fsbo_init_words(ctypes.byref(c), i, _ptr(out))
     return out
+
+
+def volitive_word(cfg: Config, i: int, t: int) -> int:
+    c = cfg.c()
+    return int(lib().fsbo_volitive_word(ctypes.byref(c), i, t))
+
+
+def grid_exponent(n: int, bound: float) -> int:
+    return int(lib().fsbo_grid_exponent(n, bound))
 
 
 def init(cfg: Config, precision: str = "f32") -> np.ndarray:

@@ -19,7 +19,8 @@
  *                        weight = the Config's initial weight (Sec. 2.1.3),
  *                        or optionally w0 * (0.5 + u) (reading: the paper
  *                        says the weight also comes from the generator).
- *   step t (Sec. 2.1.2, Sec. 2.2.1 "fish movement and feeding"), in order
+ *   step t (Sec. 2.1.2, and Sec. 2.2.1, which names moving and feeding as
+ *          the per-step work), in order
  *     swim        random move: x += (2u0 - 1) s, y += (2u1 - 1) s, then each
  *                 coordinate clamped to [-P, P] (reading: uniform step of
  *                 half-width s, independent of weight; clamp at the bank)
@@ -46,6 +47,18 @@
  *                 E_t = max_i (prev_i - cur_i): if E_t > 0,
  *                 w <- clamp(w + (prev - cur) / E_t, w_min, w_max); else no
  *                 fish eats
+ *   collective_mode 1   after the eat and the barycentre sums, the two
+ *                 collective movements of fish-school search (not in the
+ *                 paper; the method family it belongs to):
+ *                 instinctive  every fish moves by I = sum_{g>0} dx g /
+ *                              sum_{g>0} g, g = prev - cur the fish's
+ *                              improvement, dx its swim displacement
+ *                 volitive     with B the barycentre after the instinctive
+ *                              move and W the weight sum, each fish moves
+ *                              s_vol u |x - B|^-1 (x - B) toward B if W grew
+ *                              in the step, away from B otherwise
+ *                 The school sums are exact fixed-point sums (collective.c),
+ *                 and currentObjective becomes the final position's.
  *
  * Draws: u(r) = (r >> 8) * 2^-24 from Philox4x32-10 words (philox.c), so
  * 2u - 1 is exact in binary32.  Each arithmetic operation rounds once to
@@ -139,9 +152,35 @@ static real swim_width(const fsbo_config* cfg, real s, real w0, real w)
     return (w / w0) * s;
 }
 
+/* One term of an exact school sum: v * 2^k (exact: a power-of-two scaling)
+ * rounded to the nearest integer, ties to even. */
+static long long grid_term(real v, int k)
+{
+    if (sizeof(real) == sizeof(float))
+        return llrintf((float)v * ldexpf(1.0f, k));
+    return llrint((double)v * ldexp(1.0, k));
+}
+
+/* Grid exponents of the collective sums: swim products dx * g (kp),
+ * improvements g (kg), weight sums w, w x, w y (kw).  The bounds hold for
+ * every value the school can take (see fsbo_grid_exponent). */
+static void collective_grids(const fsbo_config* cfg, int* kp, int* kg, int* kw)
+{
+    const double a = fmax(fmax(fabs(cfg->w_min), fabs(cfg->w_max)), 1.5 * fabs(cfg->w0));
+    const double sm = cfg->swim_mode == 1 ? 2.0 * cfg->step * fmax(1.0, a / cfg->w0)
+                                          : 2.0 * cfg->step;
+    const double e = ldexp(1.0, -20) * fmax(cfg->pond_half, 1.0);
+    const double bd = sm + e;
+    *kp = fsbo_grid_exponent(cfg->n_fish, 2.0 * bd * bd);
+    *kg = fsbo_grid_exponent(cfg->n_fish, 2.0 * bd);
+    *kw = fsbo_grid_exponent(cfg->n_fish, 2.0 * a * fmax(cfg->pond_half, 1.0));
+}
+
 static int config_ok(const fsbo_config* cfg)
 {
     if (!cfg || cfg->n_fish == 0) return 0;
+    if (cfg->collective_mode != 0 && cfg->collective_mode != 1) return 0;
+    if (cfg->collective_mode == 1 && !(cfg->step_vol >= 0.0)) return 0;
     if (cfg->swim_mode != 0 && cfg->swim_mode != 1) return 0;
     if (cfg->feed_mode != 0 && cfg->feed_mode != 1) return 0;
     if (cfg->swim_mode == 1 && !(cfg->w0 > 0.0)) return 0;
@@ -186,11 +225,28 @@ int FN(fsbo_run)(const fsbo_config* cfg, uint64_t t0, uint32_t n_steps,
     const real wmin = (real)cfg->w_min;
     const real wmax = (real)cfg->w_max;
 
+    const int coll = cfg->collective_mode == 1;
+    int kp = 0, kg = 0, kw = 0;
+    if (coll) collective_grids(cfg, &kp, &kg, &kw);
+    const real s_vol = (real)cfg->step_vol;
+
     real* delta = (real*)malloc(sizeof(real) * N);
-    if (!delta) return -1;
+    real* dxs = coll ? (real*)malloc(sizeof(real) * N) : NULL;
+    real* dys = coll ? (real*)malloc(sizeof(real) * N) : NULL;
+    if (!delta || (coll && (!dxs || !dys))) {
+        free(delta);
+        free(dxs);
+        free(dys);
+        return -1;
+    }
 
     for (uint32_t k = 0; k < n_steps; ++k) {
         const uint32_t t = (uint32_t)(t0 + k + 1);
+
+        /* the school's weight on the grid before this step's eat */
+        long long w_before = 0;
+        if (coll)
+            for (uint64_t i = 0; i < N; ++i) w_before += grid_term(school[i].weight, kw);
 
         /* swim, objective, delta */
         for (uint64_t i = 0; i < N; ++i) {
@@ -201,8 +257,13 @@ int FN(fsbo_run)(const fsbo_config* cfg, uint64_t t0, uint32_t n_steps,
             } else {
                 fsbo_swim_words(cfg, i, t, r);
             }
+            const real x_before = school[i].x, y_before = school[i].y;
             delta[i] = swim_one(&school[i], r[0], r[1], P,
                                 swim_width(cfg, s, w0, school[i].weight));
+            if (coll) {
+                dxs[i] = school[i].x - x_before;
+                dys[i] = school[i].y - y_before;
+            }
         }
 
         /* max |delta| and the paper's eat() statistic, initialised to
@@ -253,9 +314,73 @@ int FN(fsbo_run)(const fsbo_config* cfg, uint64_t t0, uint32_t n_steps,
             stats[k].sum_wy = sy.s + sy.c;
             stats[k].sum_abs_wx = ax.s + ax.c;
             stats[k].sum_abs_wy = ay.s + ay.c;
+            stats[k].inst_x = stats[k].inst_y = 0.0;
+            stats[k].vol_bx = stats[k].vol_by = stats[k].vol_dw = 0.0;
+        }
+
+        if (coll) {
+            /* collective-instinctive movement: I = sum dx g / sum g over
+             * the fish that improved, from exact grid sums */
+            long long nx = 0, ny = 0, den = 0;
+            for (uint64_t i = 0; i < N; ++i) {
+                const real g = school[i].prevObjective - school[i].currentObjective;
+                if (g > 0) {
+                    nx += grid_term(dxs[i] * g, kp);
+                    ny += grid_term(dys[i] * g, kp);
+                    den += grid_term(g, kg);
+                }
+            }
+            real ix = 0, iy = 0;
+            if (den != 0) {
+                ix = (real)ldexp((double)nx / (double)den, kg - kp);
+                iy = (real)ldexp((double)ny / (double)den, kg - kp);
+            }
+            for (uint64_t i = 0; i < N; ++i) {
+                school[i].x = clamp_r(school[i].x + ix, -P, P);
+                school[i].y = clamp_r(school[i].y + iy, -P, P);
+            }
+
+            /* collective-volitive movement: barycentre of the moved school
+             * with its eaten weights; contract if the weight sum grew */
+            long long sw = 0, sx = 0, sy = 0;
+            for (uint64_t i = 0; i < N; ++i) {
+                const real w = school[i].weight;
+                sw += grid_term(w, kw);
+                sx += grid_term(w * school[i].x, kw);
+                sy += grid_term(w * school[i].y, kw);
+            }
+            real bx = 0, by = 0;
+            if (sw != 0) {
+                bx = (real)((double)sx / (double)sw);
+                by = (real)((double)sy / (double)sw);
+                const int contract = sw > w_before;
+                for (uint64_t i = 0; i < N; ++i) {
+                    FISH* f = &school[i];
+                    const real u = (real)(fsbo_volitive_word(cfg, i, t) >> 8) * (real)0x1p-24;
+                    const real dx = f->x - bx;
+                    const real dy = f->y - by;
+                    const real dist = sqrt_r(dx * dx + dy * dy);
+                    if (dist > 0) {
+                        const real m = (s_vol * u) / dist;
+                        f->x = clamp_r(contract ? f->x - m * dx : f->x + m * dx, -P, P);
+                        f->y = clamp_r(contract ? f->y - m * dy : f->y + m * dy, -P, P);
+                    }
+                }
+            }
+            for (uint64_t i = 0; i < N; ++i)
+                school[i].currentObjective = objective(school[i].x, school[i].y);
+            if (stats) {
+                stats[k].inst_x = (double)ix;
+                stats[k].inst_y = (double)iy;
+                stats[k].vol_bx = (double)bx;
+                stats[k].vol_by = (double)by;
+                stats[k].vol_dw = (double)(sw - w_before);
+            }
         }
     }
     free(delta);
+    free(dxs);
+    free(dys);
     return 0;
 }
 

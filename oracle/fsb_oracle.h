@@ -41,6 +41,9 @@ typedef struct {
     int32_t  swim_mode;       /* 0: move half-width s; 1: s * (w / w0) */
     int32_t  feed_mode;       /* 0: w += delta / max|delta|;
                                  1: w += (prev - cur) / max(prev - cur)  */
+    int32_t  collective_mode; /* 1: instinctive and volitive movements
+                                 after each step's eat (fish-school search) */
+    double   step_vol;        /* volitive step s_vol                     */
 } fsbo_config;
 
 /* Per-step statistics. */
@@ -52,7 +55,16 @@ typedef struct {
     double sum_wy;         /*   ~1e-15 of sum_abs_* for N <= 2^30             */
     double sum_abs_wx;     /* sum_i |w_i x_i|: normaliser of the bary error  */
     double sum_abs_wy;
+    /* collective_mode 1 only (0 otherwise): the instinctive vector, the
+     * barycentre the volitive move used, and W_t - W_{t-1} in grid units */
+    double inst_x, inst_y;
+    double vol_bx, vol_by;
+    double vol_dw;
 } fsbo_stats;
+
+/* Fixed-point grid exponent of an exact school sum (collective movements):
+ * the largest k in [-100, 100] with n * bound * 2^k <= 2^62. */
+int fsbo_grid_exponent(uint64_t n, double bound);
 
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): out = bijection of ctr
  * under key.  Shared by both precisions. */
@@ -65,6 +77,9 @@ void fsbo_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
 void fsbo_swim_words(const fsbo_config* cfg, uint64_t i, uint32_t t,
                      uint32_t out[2]);
 void fsbo_init_words(const fsbo_config* cfg, uint64_t i, uint32_t out[3]);
+/* The volitive draw of fish i at step t (collective_mode 1): word i % 2 of
+ * the domain-2 block of pair i / 2. */
+uint32_t fsbo_volitive_word(const fsbo_config* cfg, uint64_t i, uint32_t t);
 
 /* Fish state in the paper's layout (Sec. 2.1.1). */
 typedef struct { float  x, y, weight, prevObjective, currentObjective; } fsbo_fish_f32;

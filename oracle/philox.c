@@ -41,8 +41,9 @@ void fsbo_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
 
 /* Counter layout (reading of the unnamed RNG): word 0 = index low 32 bits,
  * word 1 = index high 32 bits XOR school id, word 2 = step, word 3 = domain
- * (0 = swim, 1 = initialisation).  Key = seed.  The index is the fish for
- * the initialisation draws and the fish pair i / 2 for the swim draws. */
+ * (0 = swim, 1 = initialisation, 2 = volitive move).  Key = seed.  The
+ * index is the fish for the initialisation draws and the fish pair i / 2
+ * for the swim and volitive draws. */
 static void fish_counter(const fsbo_config* cfg, uint64_t i, uint32_t step,
                          uint32_t domain, uint32_t ctr[4], uint32_t key[2])
 {
@@ -65,6 +66,16 @@ void fsbo_swim_words(const fsbo_config* cfg, uint64_t i, uint32_t t,
     fsbo_philox4x32_10(ctr, key, r);
     out[0] = r[2 * half];
     out[1] = r[2 * half + 1];
+}
+
+/* The volitive draw of fish i at step t (collective_mode 1): domain 2,
+ * indexed by the fish pair i / 2; fish 2p takes word 0, fish 2p + 1 word 1. */
+uint32_t fsbo_volitive_word(const fsbo_config* cfg, uint64_t i, uint32_t t)
+{
+    uint32_t ctr[4], key[2], r[4];
+    fish_counter(cfg, i >> 1, t, 2u, ctr, key);
+    fsbo_philox4x32_10(ctr, key, r);
+    return r[i & 1u];
 }
 
 void fsbo_init_words(const fsbo_config* cfg, uint64_t i, uint32_t out[3])

@@ -58,6 +58,24 @@ MUTANTS = [
     ("both fish of a pair take words 0 and 1", "philox.c",
      "out[0] = r[2 * half];\n    out[1] = r[2 * half + 1];",
      "out[0] = r[0];\n    out[1] = r[1];"),
+    # collective movements (fish-school search variant)
+    ("school contracts when its weight fell", "fsb_oracle.c",
+     "const int contract = sw > w_before;", "const int contract = sw < w_before;"),
+    ("instinctive vector over every fish", "fsb_oracle.c",
+     "                if (g > 0) {\n                    nx += grid_term",
+     "                if (g == g) {\n                    nx += grid_term"),
+    ("grid terms truncated", "fsb_oracle.c",
+     "return llrint((double)v * ldexp(1.0, k));",
+     "return (long long)((double)v * ldexp(1.0, k));"),
+    ("grid exponents swapped in the quotient", "fsb_oracle.c",
+     "ix = (real)ldexp((double)nx / (double)den, kg - kp);",
+     "ix = (real)ldexp((double)nx / (double)den, kp - kg);"),
+    ("objective not updated after the collective moves", "fsb_oracle.c",
+     "                school[i].currentObjective = objective(school[i].x, school[i].y);\n"
+     "            if (stats) {",
+     "                (void)0;\n            if (stats) {"),
+    ("both fish of a pair take volitive word 0", "philox.c",
+     "return r[i & 1u];", "return r[0];"),
 ]
 
 

@@ -100,7 +100,9 @@ def parse_fixture(path):
                                 step=float(kv["step"]), w0=float(kv["w0"]),
                                 w_min=float(kv["w_min"]), w_max=float(kv["w_max"]),
                                 swim_mode=int(kv.get("swim_mode", 0)),
-                                feed_mode=int(kv.get("feed_mode", 0)))
+                                feed_mode=int(kv.get("feed_mode", 0)),
+                                collective_mode=int(kv.get("collective_mode", 0)),
+                                step_vol=float(kv.get("step_vol", 0.1)))
         elif tok[0] == "init":
             init[int(tok[1])] = kv
         elif tok[0] == "step":
@@ -193,7 +195,7 @@ def test_philox_words_are_uniform():
 @pytest.mark.parametrize("precision", ["f32", "f64"])
 @pytest.mark.parametrize("name", ["handworked_n3.txt", "handworked_bank.txt",
                                   "handworked_mapping.txt", "handworked_weighted_swim.txt",
-                                  "handworked_paper_feeding.txt"])
+                                  "handworked_paper_feeding.txt", "handworked_collective.txt"])
 def test_handworked_fixture(name, precision):
     cfg, init, steps = parse_fixture(os.path.join(GOLDEN, name))
     dtype = oracle.FISH_F32 if precision == "f32" else oracle.FISH_F64
@@ -214,9 +216,11 @@ def test_handworked_fixture(name, precision):
         exp = st["stats"]
         names = {"M": "max_abs_delta", "E": "eat_max_diff", "S_w": "sum_w",
                  "S_x": "sum_wx", "S_y": "sum_wy", "A_x": "sum_abs_wx",
-                 "A_y": "sum_abs_wy"}
+                 "A_y": "sum_abs_wy", "I_x": "inst_x", "I_y": "inst_y",
+                 "B_x": "vol_bx", "B_y": "vol_by"}
         for key, field in names.items():
-            assert Fraction(float(stats[field])) == Fraction(exp[key]), (name, k + 1, key)
+            if key in exp:
+                assert Fraction(float(stats[field])) == Fraction(exp[key]), (name, k + 1, key)
 
 
 # --------------------------------------------------------- exact checks --
@@ -480,3 +484,167 @@ def test_bad_configuration_is_rejected():
         oracle.init(oracle.Config(n_fish=4, swim_mode=2))
     with pytest.raises(ValueError):
         oracle.init(oracle.Config(n_fish=4, feed_mode=3))
+
+
+# ------------------------------------------------- collective movements --
+# (fish-school search variant, collective_mode 1; not in the paper)
+
+def test_grid_exponent_is_the_largest_safe_power_of_two():
+    """The grid exponent of an exact school sum is the largest k (capped at
+    +-100) with n * bound * 2^k <= 2^62, checked in exact arithmetic on the
+    binary64 value of n * bound the oracle starts from."""
+    lim = Fraction(2) ** 62
+    cases = [(1, 1.0), (2, 512.0061), (1000, 0.0141), (1 << 28, 0.02), (1 << 32, 3.5),
+             (7, 1e-30), (3, 1e30), (1 << 40, 1e10), (5, 0.0)]
+    for n, b in cases:
+        k = oracle.grid_exponent(n, b)
+        t = Fraction(float(n) * b)
+        assert -100 <= k <= 100
+        if t == 0:
+            assert k == 100
+            continue
+        if k < 100:
+            assert t * Fraction(2) ** (k + 1) > lim, (n, b, k)
+        if k > -100:
+            assert t * Fraction(2) ** k <= lim, (n, b, k)
+
+
+def test_volitive_draw_counter_layout_matches_triton():
+    """Domain 2 holds the volitive draws, indexed by the fish pair: fish 2p
+    takes word 0 and fish 2p + 1 word 1 of the pair's block."""
+    cases = [(9, 0, 0, 1), (9, 0, 1, 1), (123, 5, 77, 40), (123, 5, 76, 40),
+             ((1 << 40) + 7, 11, (1 << 33) + 3, 9)]
+    rows = []
+    for seed, school, i, t in cases:
+        p = i >> 1
+        rows.append([p & 0xFFFFFFFF, ((p >> 32) ^ school) & 0xFFFFFFFF, t, 2, seed])
+    ref = triton_philox(rows)
+    for (seed, school, i, t), want in zip(cases, ref):
+        cfg = oracle.Config(n_fish=1, seed=seed, school_id=school)
+        assert oracle.volitive_word(cfg, i, t) == want[i & 1]
+
+
+def _grids(cfg):
+    """Grid exponents of the collective sums, from the bounds of the
+    configuration (products dx * g, improvements g, weights)."""
+    a = max(abs(cfg.w_min), abs(cfg.w_max), 1.5 * abs(cfg.w0))
+    sm = 2.0 * cfg.step * max(1.0, a / cfg.w0) if cfg.swim_mode == 1 else 2.0 * cfg.step
+    bd = sm + math.ldexp(1.0, -20) * max(cfg.pond_half, 1.0)
+    return (oracle.grid_exponent(cfg.n_fish, 2.0 * bd * bd),
+            oracle.grid_exponent(cfg.n_fish, 2.0 * bd),
+            oracle.grid_exponent(cfg.n_fish, 2.0 * a * max(cfg.pond_half, 1.0)))
+
+
+def _coll_cfg(n, **kw):
+    base = dict(n_fish=n, seed=21, collective_mode=1, step=2.0, init_weight_mode=1)
+    base.update(kw)
+    return oracle.Config(**base)
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_collective_sums_do_not_depend_on_fish_order(precision):
+    """The instinctive vector and the barycentre come from exact grid sums,
+    so reordering the school (with each fish keeping its draws) changes
+    nothing: same vector, same barycentre, same per-fish states."""
+    n, steps = 97, 4
+    cfg = _coll_cfg(n, step_vol=0.0)
+    rng = np.random.default_rng(5)
+    draws = rng.integers(0, 1 << 32, (steps, n, 2), dtype=np.uint64).astype(np.uint32)
+    a = oracle.init(cfg, precision)
+    perm = rng.permutation(n)
+    b = a[perm].copy()
+    sa = oracle.run(cfg, a, 0, steps, draws=draws)
+    sb = oracle.run(cfg, b, 0, steps, draws=draws[:, perm, :])
+    for f in ("inst_x", "inst_y", "vol_bx", "vol_by", "vol_dw", "max_abs_delta"):
+        assert np.array_equal(sa[f], sb[f]), f
+    assert np.array_equal(a[perm], b)
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_volitive_move_is_radial_by_s_vol_u(precision):
+    """Against the same step with a volitive step of 0, each fish moves along
+    the line through the barycentre B the step reports, by s_vol * u with
+    its own draw u, toward B when the school's weight sum grew and away from
+    it otherwise (fish clamped at the bank excluded)."""
+    n, s_vol = 400, 0.7
+    cfg0 = _coll_cfg(n, step_vol=0.0, pond_half=100.0)
+    cfg1 = _coll_cfg(n, step_vol=s_vol, pond_half=100.0)
+    a = oracle.init(cfg0, precision)
+    b = a.copy()
+    st = oracle.run(cfg0, a, 0, 1)[0]
+    st1 = oracle.run(cfg1, b, 0, 1)[0]
+    assert st["vol_bx"] == st1["vol_bx"] and st["vol_by"] == st1["vol_by"]
+    bx, by = float(st["vol_bx"]), float(st["vol_by"])
+    toward = st["vol_dw"] > 0
+    tol = 8 * float(np.spacing(np.float32(100.0) if precision == "f32" else np.float64(100.0)))
+    checked = 0
+    for i in range(n):
+        if max(abs(b["x"][i]), abs(b["y"][i])) >= 100.0:
+            continue
+        vx, vy = float(a["x"][i]) - bx, float(a["y"][i]) - by
+        dx, dy = float(b["x"][i]) - float(a["x"][i]), float(b["y"][i]) - float(a["y"][i])
+        dist = math.hypot(vx, vy)
+        u = (oracle.volitive_word(cfg1, i, 1) >> 8) * 2.0 ** -24
+        assert abs(math.hypot(dx, dy) - s_vol * u) <= tol, i
+        assert abs(vx * dy - vy * dx) <= tol * dist, i
+        assert (vx * dx + vy * dy < 0) == toward or math.hypot(dx, dy) <= tol, i
+        checked += 1
+    assert checked > n // 2
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_lone_fish_follows_its_own_improvement(precision):
+    """N = 1: when the fish improves, the instinctive vector is its own swim
+    displacement (up to the rounding of dx * g on the grid), and the fish is
+    its own barycentre (or weighs 0), so it makes no volitive move."""
+    real = np.float32 if precision == "f32" else np.float64
+    cfg = _coll_cfg(1, step_vol=0.9, step=3.0)
+    plain = oracle.Config(**{**cfg.__dict__, "collective_mode": 0})
+    seen = 0
+    for t in range(60):
+        a = oracle.init(cfg, precision)
+        oracle.run(cfg, a, 0, t)                  # advance to step t
+        ref = a.copy()
+        oracle.run(plain, ref, t, 1)              # the swim alone
+        st = oracle.run(cfg, a, t, 1)[0]
+        g = float(ref["prevObjective"][0]) - float(ref["currentObjective"][0])
+        if g <= 0:
+            assert st["inst_x"] == 0 and st["inst_y"] == 0
+            continue
+        seen += 1
+        before = oracle.init(cfg, precision)
+        oracle.run(cfg, before, 0, t)
+        dx = float(ref["x"][0]) - float(before["x"][0])
+        # grid quantisation: each grid term is within half a grid unit
+        kp, kg = _grids(cfg)[:2]
+        quant = (2.0 ** -(kp + 1) + abs(dx) * 2.0 ** -(kg + 1)) / g
+        assert abs(st["inst_x"] - dx) <= 1.01 * quant + 4 * float(np.spacing(real(abs(dx) + 1e-30)))
+        # no volitive move: the fish is its own barycentre, or weighs 0
+        # (then the weight sum is 0 and no barycentre is defined)
+        moved = np.clip(real(ref["x"][0]) + real(st["inst_x"]), -cfg.pond_half, cfg.pond_half)
+        assert a["x"][0] == moved
+        if a["weight"][0] != 0:
+            assert st["vol_bx"] == float(a["x"][0]) and st["vol_by"] == float(a["y"][0])
+        else:
+            assert st["vol_bx"] == 0 and st["vol_by"] == 0
+    assert seen > 5
+
+
+def test_no_improving_fish_means_no_instinctive_move():
+    """If every fish's objective worsens, the instinctive vector is 0 and,
+    with a volitive step of 0, the school ends where the swim left it."""
+    n = 16
+    cfg = _coll_cfg(n, step_vol=0.0, step=1.0, pond_half=100.0)
+    school = oracle.init(cfg)
+    # move every fish outward: dx with the sign of x, dy with the sign of y
+    draws = np.zeros((1, n, 2), np.uint32)
+    for i in range(n):
+        draws[0, i, 0] = 0xFFFFFF00 if school["x"][i] >= 0 else 0
+        draws[0, i, 1] = 0xFFFFFF00 if school["y"][i] >= 0 else 0
+    plain = oracle.Config(**{**cfg.__dict__, "collective_mode": 0})
+    ref = school.copy()
+    oracle.run(plain, ref, 0, 1, draws=draws)
+    st = oracle.run(cfg, school, 0, 1, draws=draws)[0]
+    assert np.all(ref["currentObjective"] > ref["prevObjective"])
+    assert st["inst_x"] == 0 and st["inst_y"] == 0
+    assert np.array_equal(school["x"], ref["x"]) and np.array_equal(school["y"], ref["y"])
