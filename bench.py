@@ -50,7 +50,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["stream", "small", "resident", "batch", "precision",
-                                           "eat"],
+                                           "eat", "collective"],
                     default="stream")
     ap.add_argument("--batch-schools", type=int, default=None,
                     help="use only the first N schools of the batched ensemble")
@@ -76,7 +76,7 @@ def parse_args():
 
 def workload_of(name):
     return {"stream": workloads.STREAM, "small": workloads.SMALL,
-            "resident": workloads.RESIDENT}[name]
+            "resident": workloads.RESIDENT, "collective": workloads.COLLECTIVE}[name]
 
 
 def dist_setup(args):
@@ -141,6 +141,7 @@ def kernel_source_hash():
 ALU_KERNEL_SOURCES = {
     "resident": ("fsb_resident.cu", "fsb_device.cuh", "fsb_reduce.cuh"),
     "batch": ("fsb_batch.cu", "fsb_device.cuh", "fsb_reduce.cuh"),
+    "collective": ("fsb_collective.cu", "fsb_device.cuh", "fsb_reduce.cuh"),
 }
 
 
@@ -247,10 +248,10 @@ class ClockSampler:
                 "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
 
 
-def cpu_oracle_rate(n_fish, seed, steps):
+def cpu_oracle_rate(n_fish, seed, steps, collective=False):
     """Time the CPU oracle (single thread) on n_fish x steps fish-steps."""
     import oracle
-    cfg = oracle.Config(n_fish=n_fish, seed=seed)
+    cfg = oracle.Config(n_fish=n_fish, seed=seed, collective_mode=1 if collective else 0)
     school = oracle.init(cfg)
     t0 = time.perf_counter()
     oracle.run(cfg, school, 0, steps)
@@ -503,7 +504,8 @@ def run_reference(args, world, rank):
     import oracle
     n = min(wl.n_fish, args.reference_fish)
     steps = args.steps if args.steps is not None else wl.steps
-    cfg = oracle.Config(n_fish=n, seed=wl.seed)
+    cfg = oracle.Config(n_fish=n, seed=wl.seed,
+                        collective_mode=1 if args.workload == "collective" else 0)
     school = oracle.init(cfg)
     oracle.run(cfg, school, 0, args.warmup)
     t0 = time.perf_counter()
@@ -542,7 +544,9 @@ def run_ours(args, world, rank, local, pg):
     dbl = prec == fsb.FSB_FP64_STATE
     elem = 8 if dbl else 4
     n = args.n_fish or wl.n_fish
-    cfg = fsb.fsb_config_init(n, wl.seed + rank, precision=prec, school_id=wl.school_id)
+    coll = args.workload == "collective"
+    cfg = fsb.fsb_config_init(n, wl.seed + rank, precision=prec, school_id=wl.school_id,
+                              collective_mode=1 if coll else 0)
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -579,9 +583,28 @@ def run_ours(args, world, rank, local, pg):
 
     # ---- roofline of the dominant kernel
     peak, peak_kind = measured_peaks()
-    bytes_per_fish_step = 8 * elem
+    # per fish-step: 16 B in, 16 B out; with the collective movements the
+    # step's two passes move 28 B in and 20 B out (eat: x y w prev in, x y w
+    # out; move: x y in, x y prev out)
+    bytes_per_fish_step = (12 if coll else 8) * elem
     avg_fused_s = (fused_ms / fused_n) / 1e3 if fused_n else None
-    if path == fsb.FSB_PATH_RESIDENT:
+    if coll:
+        # two passes per step, bound by instruction issue (grid terms, two
+        # draws and three square roots per fish); HBM fraction kept beside
+        ipfs = alu_instr_per_fish_step("collective", args.precision)
+        rate = n / avg_fused_s if avg_fused_s else None
+        hbm = bytes_per_fish_step * n / avg_fused_s / 1e9 if avg_fused_s else None
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        roof = {"bound": "alu", "unit": "Glane-instr/s",
+                "kernel": "coll_kernel<eat> + coll_kernel<move> (one step)",
+                "launches": fused_n, "avg_launch_ms": avg_fused_s * 1e3 if avg_fused_s else None,
+                "fish_steps_per_launch": n, "lane_instr_per_fish_step": ipfs, "traffic": None,
+                "achieved": rate * ipfs / 1e9 if (rate and ipfs) else None,
+                "peak_source": "issue peak %d SMs x 128 lanes x measured median SM clock" % sms,
+                "_sms": sms, "hbm_achieved_gbs": hbm,
+                "hbm_frac_of_measured": hbm / peak if hbm else None,
+                "algorithmic_bytes_per_launch": bytes_per_fish_step * n}
+    elif path == fsb.FSB_PATH_RESIDENT:
         # one launch advances all `steps` steps with the state on chip: bound
         # by instruction issue, 152 SMs x 4 schedulers x 32 lanes per clock
         ipfs = alu_instr_per_fish_step("resident", args.precision)
@@ -655,7 +678,7 @@ def run_ours(args, world, rank, local, pg):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cn, cs = min(n, 1 << 20), 20 if n >= (1 << 20) else wl.steps
-        rate, dt = cpu_oracle_rate(cn, wl.seed, cs)
+        rate, dt = cpu_oracle_rate(cn, wl.seed, cs, collective=coll)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "%d fish x %d steps of the %s school (same init rule), %.1f s"
                          % (cn, cs, wl.name, dt)}

@@ -95,7 +95,21 @@ typedef enum {
  *   feed_mode         0 (default): w += delta / max|delta|;
  *                     1: w += (prev - cur) / E with E = max(prev - cur), the
  *                     value the paper's eat() reduces (Sec. 2.3.2); nobody
- *                     eats when E <= 0                                     */
+ *                     eats when E <= 0
+ *   collective_mode   0 (default); 1: after each step's eat, the two
+ *                     collective movements of fish-school search (not in
+ *                     the paper): every fish moves by the instinctive vector
+ *                     (the improvement-weighted mean swim displacement of
+ *                     the fish that improved), then by step_vol * u along
+ *                     the line through the school's barycentre, toward it if
+ *                     the school's weight grew in the step, away otherwise.
+ *                     Those school sums are exact fixed-point sums, so the
+ *                     result does not depend on the reduction order.
+ *                     Streaming path only (fsb_create with FSB_PATH_RESIDENT,
+ *                     fsb_run_batch / fsb_batch_create, fsb_step_static,
+ *                     fsb_autotune and fsb_set_fault_injection return
+ *                     FSB_ERR_UNSUPPORTED); two passes per step
+ *   step_vol          volitive step (default 0.1)                          */
 typedef struct {
     uint64_t n_fish;
     uint64_t seed;
@@ -110,6 +124,8 @@ typedef struct {
     int32_t  path;
     int32_t  swim_mode;
     int32_t  feed_mode;
+    int32_t  collective_mode;
+    double   step_vol;
 } fsb_config;
 
 /* Per-fish state arrays on the device, structure of arrays, n_fish elements

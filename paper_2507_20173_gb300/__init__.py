@@ -64,7 +64,8 @@ class FsbConfig(ctypes.Structure):
                 ("w0", ctypes.c_double), ("w_min", ctypes.c_double),
                 ("w_max", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("path", ctypes.c_int32), ("swim_mode", ctypes.c_int32),
-                ("feed_mode", ctypes.c_int32)]
+                ("feed_mode", ctypes.c_int32), ("collective_mode", ctypes.c_int32),
+                ("step_vol", ctypes.c_double)]
 
 
 class FsbStateDev(ctypes.Structure):

@@ -5,6 +5,7 @@
 // the device status word.  All arithmetic of the method runs in the CUDA
 // kernels (fsb_stream.cu, fsb_resident.cu, fsb_batch.cu); this file only
 // orchestrates.
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -65,7 +66,46 @@ int validate_config(const fsb_config* c) {
     return fail(FSB_ERR_INVALID_ARG, "feed_mode must be 0 or 1");
   if (c->swim_mode == 1 && !(c->w0 > 0.0))
     return fail(FSB_ERR_INVALID_ARG, "the weight-scaled swim needs w0 > 0");
+  if (c->collective_mode != 0 && c->collective_mode != 1)
+    return fail(FSB_ERR_INVALID_ARG, "collective_mode must be 0 or 1");
+  if (c->collective_mode == 1 && !(c->step_vol >= 0.0))
+    return fail(FSB_ERR_INVALID_ARG, "step_vol must be >= 0");
   return FSB_OK;
+}
+
+// Largest k in [-100, 100] with max(n, 2^19) * bound * 2^k <= 2^62: the
+// grid of an exact school sum of n terms bounded by `bound` (collective
+// movements); the sum stays below 2^62 and each term below 2^43.
+int grid_exponent(uint64_t n, double bound) {
+  const double lim = 4611686018427387904.0;  // 2^62
+  double t = static_cast<double>(n < 524288u ? 524288u : n) * bound;
+  int k = 0;
+  if (t > lim) {
+    while (t > lim && k > -100) {
+      t *= 0.5;
+      --k;
+    }
+    return k;
+  }
+  while (2.0 * t <= lim && k < 100) {
+    t *= 2.0;
+    ++k;
+  }
+  return k;
+}
+
+// Grid exponents of the collective sums from bounds that hold for every
+// value the school can take: swim products dx * g, improvements g, and the
+// weight sums w, w x, w y.
+void collective_grids(const fsb_config* c, int* kp, int* kg, int* kw) {
+  const double a =
+      std::fmax(std::fmax(std::fabs(c->w_min), std::fabs(c->w_max)), 1.5 * std::fabs(c->w0));
+  const double sm = c->swim_mode == 1 ? 2.0 * c->step * std::fmax(1.0, a / c->w0) : 2.0 * c->step;
+  const double e = std::ldexp(1.0, -20) * std::fmax(c->pond_half, 1.0);
+  const double bd = sm + e;
+  *kp = grid_exponent(c->n_fish, 2.0 * bd * bd);
+  *kg = grid_exponent(c->n_fish, 2.0 * bd);
+  *kw = grid_exponent(c->n_fish, 2.0 * a * std::fmax(c->pond_half, 1.0));
 }
 
 int acc_mode(int precision) {
@@ -121,6 +161,9 @@ struct fsb_school {
   uint64_t fused_launches = 0;
   void* cur_stage = nullptr;       // two chunks of currentObjective for fsb_read_state
   uint64_t cur_chunk = 0;          // fish per chunk
+  bool collective = false;         // collective_mode 1: two passes per step
+  fsb::CollLaunch coll{};
+  uint32_t coll_cap = 0;           // steps the collective record ring holds
 };
 
 namespace {
@@ -132,6 +175,23 @@ int check_status_word(fsb_school* h) {
   FSB_CUDA(cudaStreamSynchronize(h->stream));
   if (status != 0)
     return fail(status, "device status word latched %d (%s)", status, fsb_strerror(status));
+  return FSB_OK;
+}
+
+// The collective records of a call of n steps (one per step).
+int ensure_coll(fsb_school* h, uint32_t n) {
+  if (!h->collective || h->coll_cap >= n) return FSB_OK;
+  uint32_t cap = h->coll_cap ? h->coll_cap : 1024;
+  while (cap < n) cap = cap > 0x7FFFFFFFu ? n : cap * 2;
+  FSB_CUDA(cudaStreamSynchronize(h->stream));
+  fsb::CollRec* recs = nullptr;
+  FSB_CUDA(cudaMalloc(&recs, sizeof(fsb::CollRec) * cap));
+  FSB_CUDA(cudaMemset(recs, 0, sizeof(fsb::CollRec) * cap));
+  if (h->coll.coll) cudaFree(h->coll.coll);
+  h->coll.coll = recs;
+  h->coll_cap = cap;
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+  h->graphs.clear();
   return FSB_OK;
 }
 
@@ -164,8 +224,35 @@ int launch_pass(fsb_school* h, int kind, cudaStream_t s) {
   return FSB_OK;
 }
 
+cudaEvent_t take_event(fsb_school* h);
+
+// The collective call (collective_mode 1): swim0, then eat t and move t for
+// every step t; the last move closes the call.
+int enqueue_collective(fsb_school* h, uint32_t n, cudaStream_t s, bool timed) {
+  fsb::CollLaunch& C = h->coll;
+  C.ring = h->ring;
+  FSB_CUDA(fsb::launch_coll_pass(C, fsb::kCSwim0, n, s));
+  for (uint32_t t = 1; t <= n; ++t) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (timed) {
+      a = take_event(h);
+      b = take_event(h);
+      if (!a || !b) return fail(FSB_ERR_CUDA, "cudaEventCreate failed");
+      FSB_CUDA(cudaEventRecord(a, s));
+    }
+    FSB_CUDA(fsb::launch_coll_pass(C, fsb::kCEat, n, s));
+    FSB_CUDA(fsb::launch_coll_pass(C, t == n ? fsb::kCMoveLast : fsb::kCMove, n, s));
+    if (timed) {
+      FSB_CUDA(cudaEventRecord(b, s));
+      h->ev_pending.emplace_back(a, b);
+    }
+  }
+  return FSB_OK;
+}
+
 // Enqueue the pass sequence of one call on stream s (capturable).
 int enqueue_call(fsb_school* h, uint32_t n, cudaStream_t s) {
+  if (h->collective) return enqueue_collective(h, n, s, false);
   int rc = launch_pass(h, fsb::kSwimOnly, s);
   for (uint32_t k = 1; rc == FSB_OK && k < n; ++k) rc = launch_pass(h, fsb::kFused, s);
   if (rc == FSB_OK) rc = launch_pass(h, fsb::kSettle, s);
@@ -248,6 +335,14 @@ int run_timed(fsb_school* h, uint32_t n) {
 }
 
 int run_stream(fsb_school* h, uint32_t n) {
+  if (h->collective) {
+    if (h->timing || n > kGraphMaxSteps) return enqueue_collective(h, n, h->stream, h->timing);
+    cudaGraphExec_t exec = nullptr;
+    int rc = get_graph(h, n, &exec);
+    if (rc != FSB_OK) return rc;
+    FSB_CUDA(cudaGraphLaunch(exec, h->stream));
+    return FSB_OK;
+  }
   if (h->timing) return run_timed(h, n);
   cudaGraphExec_t exec = nullptr;
   if (n <= kGraphMaxSteps) {
@@ -419,6 +514,8 @@ void release(fsb_school* h) {
   cudaFree(h->partials);
   cudaFree(h->ring);
   cudaFree(h->cur_stage);
+  cudaFree(h->coll.partials);
+  cudaFree(h->coll.coll);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
 }
@@ -441,6 +538,8 @@ int fsb_config_init(fsb_config* cfg, uint64_t n_fish, uint64_t seed) {
   cfg->w_max = 2.0;
   cfg->precision = FSB_FP32_KAHAN;
   cfg->path = FSB_PATH_AUTO;
+  cfg->collective_mode = 0;
+  cfg->step_vol = 0.1;
   return FSB_OK;
 }
 
@@ -530,9 +629,39 @@ int fsb_create(const fsb_config* cfg, const fsb_state_dev* buffers, const fsb_st
     int r0 = configure_stream(h, 0, 0, 0, 0);
     if (r0 != FSB_OK) return r0;
 
+    // collective movements: streaming only (two passes per step)
+    if (cfg->collective_mode == 1) {
+      if (cfg->path == FSB_PATH_RESIDENT)
+        return fail(FSB_ERR_UNSUPPORTED, "resident path: the collective movements run streaming");
+      h->collective = true;
+      fsb::CollLaunch& C = h->coll;
+      C.x = h->x;
+      C.y = h->y;
+      C.w = h->w;
+      C.pv = h->pv;
+      C.n = cfg->n_fish;
+      C.seed = cfg->seed;
+      C.school = cfg->school_id;
+      C.real_is_double = dbl ? 1 : 0;
+      C.acc = L.acc;
+      C.pond_half = cfg->pond_half;
+      C.step = cfg->step;
+      C.w0 = cfg->w0;
+      C.w_min = cfg->w_min;
+      C.w_max = cfg->w_max;
+      C.step_vol = cfg->step_vol;
+      C.swim_mode = cfg->swim_mode;
+      C.feed_mode = cfg->feed_mode;
+      collective_grids(cfg, &C.kp, &C.kg, &C.kw);
+      C.ctl = h->ctl;
+      C.grid = fsb::coll_grid(C, sms);
+      FSB_CUDA(cudaMalloc(&C.partials, sizeof(fsb::CollPartial) * C.grid));
+    }
+
     // resident path: binary32 state that fits in registers across the SMs
     fsb::ResidentLaunch& R = h->res;
-    const bool fits = !dbl && resident_config(sms, h->launch.acc, cfg->swim_mode, cfg->n_fish, &R);
+    const bool fits = !dbl && !h->collective &&
+                      resident_config(sms, h->launch.acc, cfg->swim_mode, cfg->n_fish, &R);
     if (cfg->path == FSB_PATH_RESIDENT && !fits)
       return fail(FSB_ERR_UNSUPPORTED,
                   "resident path: school of %llu fish does not fit on chip (binary32 only)",
@@ -589,6 +718,7 @@ int fsb_step(fsb_handle h, uint32_t n_steps, fsb_step_stats* host_stats) {
   if (h->step + n_steps > 0xFFFFFFFFull)
     return fail(FSB_ERR_INVALID_ARG, "step counter would pass 2^32 - 1");
   int rc = ensure_ring(h, n_steps);
+  if (rc == FSB_OK) rc = ensure_coll(h, n_steps);
   if (rc != FSB_OK) return rc;
   rc = h->path == FSB_PATH_RESIDENT ? run_resident(h, n_steps) : run_stream(h, n_steps);
   if (rc != FSB_OK) return rc;
@@ -703,6 +833,8 @@ int fsb_get_tuning(fsb_handle h, fsb_tuning* t) {
 
 int fsb_set_fault_injection(fsb_handle h, int block, uint32_t step, uint64_t timeout_ns) {
   if (!h) return fail(FSB_ERR_INVALID_ARG, "handle is NULL");
+  if (h->collective)
+    return fail(FSB_ERR_UNSUPPORTED, "the collective passes have no waits to make run out");
   if (h->path == FSB_PATH_RESIDENT) {
     if (block >= h->res.grid) return fail(FSB_ERR_INVALID_ARG, "block out of range");
     h->res.inject_cta = block < 0 ? -1 : block;

@@ -66,6 +66,8 @@ extern "C" int fsb_autotune(const fsb_config* cfg, uint32_t n_steps, int* best_p
                             uint32_t* candidates_tried) {
   if (!cfg || !best_path || !best_tuning) return fsb::record_error(FSB_ERR_INVALID_ARG, "NULL");
   if (n_steps == 0) return fsb::record_error(FSB_ERR_INVALID_ARG, "n_steps must be >= 1");
+  if (cfg->collective_mode != 0)
+    return fsb::record_error(FSB_ERR_UNSUPPORTED, "the collective passes have one launch shape");
   const bool dbl = cfg->precision == FSB_FP64_STATE;
   std::vector<Candidate> cands;
   const int blocks[] = {256, 512};

@@ -252,6 +252,8 @@ int fsb_batch_create(const fsb_config* tmpl, uint32_t n_schools, const uint64_t*
   if (n_schools == 0) return bfail(FSB_ERR_INVALID_ARG, "n_schools must be >= 1");
   if (tmpl->precision == FSB_FP64_STATE)
     return bfail(FSB_ERR_UNSUPPORTED, "the batched path holds binary32 state only");
+  if (tmpl->collective_mode != 0)
+    return bfail(FSB_ERR_UNSUPPORTED, "the batched path runs no collective movements");
   if (tmpl->precision < FSB_FP32 || tmpl->precision > FSB_FP64_STATE)
     return bfail(FSB_ERR_INVALID_ARG, "unknown precision");
   if (!(tmpl->pond_half > 0.0) || !(tmpl->step >= 0.0) || !(tmpl->w_min <= tmpl->w_max) ||

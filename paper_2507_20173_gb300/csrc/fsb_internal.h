@@ -78,6 +78,52 @@ cudaError_t stream_ws_prepare(const StreamLaunch& L);
 int stream_ws_blocks_per_sm(const StreamLaunch& L);
 cudaError_t launch_stream_pass_ws(const StreamLaunch& L, int pass_kind, cudaStream_t s);
 cudaError_t launch_init(const StreamLaunch& L, int weight_mode, cudaStream_t s);
+
+// ---- collective movements (collective_mode 1, fsb_collective.cu)
+// A call of n steps runs pass 0 (kCSwim0), then for t = 1 .. n the passes
+// 2t - 1 (kCEat) and 2t (kCMove, kCMoveLast for t = n).
+enum CollPassKind : int { kCSwim0 = 0, kCEat = 1, kCMove = 2, kCMoveLast = 3 };
+
+// One block's contribution to a collective pass's reductions.
+struct alignas(16) CollPartial {
+  unsigned long long max_bits, e_key;
+  double sum_w, sum_wx, sum_wy;
+  long long q[4];  // exact grid sums
+};
+
+// The collective quantities of one step of a call (index t - 1 for step t).
+struct alignas(16) CollRec {
+  long long w_before;  // the school's weight on the grid before the step's eat
+  long long sw;        // ... after it
+  double ix, iy;       // instinctive vector
+  double bx, by;       // barycentre of the volitive move
+  int has_b;           // sw != 0: a barycentre exists
+  int contract;        // sw > w_before: the school moves toward it
+};
+
+struct CollLaunch {
+  void* x;
+  void* y;
+  void* w;
+  void* pv;
+  uint64_t n;
+  uint64_t seed;
+  uint32_t school;
+  int real_is_double;
+  int acc;
+  int grid;
+  double pond_half, step, w0, w_min, w_max, step_vol;
+  int swim_mode, feed_mode;
+  int kp, kg, kw;      // grid exponents of the exact sums
+  Ctl* ctl;
+  CollPartial* partials;
+  fsb_step_stats* ring;
+  CollRec* coll;
+};
+
+int coll_grid(const CollLaunch& L, int sms);
+cudaError_t launch_coll_pass(const CollLaunch& L, int pass_kind, uint32_t n_steps,
+                             cudaStream_t s);
 // currentObjective of fish [first, first + count) into cur[0, count).
 cudaError_t launch_objective(const StreamLaunch& L, uint64_t first, uint64_t count, void* cur,
                              cudaStream_t s);

@@ -102,6 +102,8 @@ extern "C" int fsb_step_static(const fsb_config* cfg, const fsb_state_dev* state
       (cfg->swim_mode == 1 && !(cfg->w0 > 0.0)))
     return fail(FSB_ERR_INVALID_ARG, "fsb_step_static: invalid configuration");
   if (n_steps == 0) return fail(FSB_ERR_INVALID_ARG, "fsb_step_static: n_steps must be >= 1");
+  if (cfg->collective_mode != 0)
+    return fail(FSB_ERR_UNSUPPORTED, "fsb_step_static: the collective movements need fsb_step");
   if (n_steps > kStaticMaxSteps)
     return fail(FSB_ERR_INVALID_ARG,
                 "fsb_step_static: n_steps exceeds the static scratch limit of 4096 steps "

@@ -29,6 +29,9 @@ class SchoolWorkload:
 SMALL = SchoolWorkload("small N=10,000 T=100", 10_000, 0, 100)
 RESIDENT = SchoolWorkload("resident N=2^20 T=1000", 1 << 20, 1, 1000)
 STREAM = SchoolWorkload("stream N=2^28 T=100", 1 << 28, 2, 100)
+# the stream school with the collective movements of fish-school search
+# (collective_mode 1, volitive step 0.1)
+COLLECTIVE = SchoolWorkload("collective N=2^28 T=100", 1 << 28, 2, 100)
 
 
 @dataclass(frozen=True)

@@ -18,7 +18,8 @@ def oracle_config(cfg) -> oracle.Config:
     return oracle.Config(n_fish=cfg.n_fish, seed=cfg.seed, school_id=cfg.school_id,
                          init_weight_mode=cfg.init_weight_mode, pond_half=cfg.pond_half,
                          step=cfg.step, w0=cfg.w0, w_min=cfg.w_min, w_max=cfg.w_max,
-                         swim_mode=cfg.swim_mode, feed_mode=cfg.feed_mode)
+                         swim_mode=cfg.swim_mode, feed_mode=cfg.feed_mode,
+                         collective_mode=cfg.collective_mode, step_vol=cfg.step_vol)
 
 
 def oracle_precision(cfg) -> str:
