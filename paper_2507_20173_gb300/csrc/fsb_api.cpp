@@ -876,31 +876,36 @@ int fsb_eat_max(const void* prev_objective, const void* current_objective, uint6
   int dev = 0, sms = 0;
   FSB_CUDA(cudaGetDevice(&dev));
   FSB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  unsigned* key = nullptr;
-  double* value = nullptr;
-  FSB_CUDA(cudaMallocAsync(&key, sizeof(unsigned), s));
-  FSB_CUDA(cudaMallocAsync(&value, sizeof(double), s));
+  // one scratch allocation: the winning order key, then the decoded value
+  struct Scratch {
+    double value;
+    unsigned key;
+  };
+  Scratch* scratch = nullptr;
+  FSB_CUDA(cudaMallocAsync(&scratch, sizeof(Scratch), s));
   cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e = cudaSuccess;
   if (device_ms) {
-    FSB_CUDA(cudaEventCreate(&a));
-    FSB_CUDA(cudaEventCreate(&b));
-    FSB_CUDA(cudaEventRecord(a, s));
+    e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    if (e == cudaSuccess) e = cudaEventRecord(a, s);
   }
   const uint64_t want = (n / 4 + 255) / 256;
   const uint64_t full = static_cast<uint64_t>(sms) * 8;
   const int grid = static_cast<int>(want < 1 ? 1 : (want < full ? want : full));
-  cudaError_t e = fsb::launch_eat_max(static_cast<const float*>(prev_objective),
-                                      static_cast<const float*>(current_objective), n, construct,
-                                      key, value, grid, s);
+  if (e == cudaSuccess)
+    e = fsb::launch_eat_max(static_cast<const float*>(prev_objective),
+                            static_cast<const float*>(current_objective), n, construct,
+                            &scratch->key, &scratch->value, grid, s);
   if (device_ms && e == cudaSuccess) e = cudaEventRecord(b, s);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(result, value, sizeof(double), cudaMemcpyDeviceToHost, s);
+    e = cudaMemcpyAsync(result, &scratch->value, sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (device_ms && e == cudaSuccess) e = cudaEventElapsedTime(device_ms, a, b);
+  // released on every path
   if (a) cudaEventDestroy(a);
   if (b) cudaEventDestroy(b);
-  cudaFreeAsync(key, s);
-  cudaFreeAsync(value, s);
+  cudaFreeAsync(scratch, s);
   FSB_CUDA(e);
   return FSB_OK;
 }
