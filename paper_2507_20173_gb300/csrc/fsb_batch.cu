@@ -4,16 +4,20 @@
 // Thread-block clusters of C blocks pop schools from work queues sorted by
 // size, largest first (longest-processing-time order), through atomic
 // counters over a ragged offset table, and run all n_steps of a school on
-// chip: each thread keeps FPT fish (x, y, weight, currentObjective,
-// prevObjective) in registers.  A school goes to the queue of the smallest
-// cluster that holds it (8, 4, 2 or 1 blocks):
+// chip: each block keeps up to 8192 fish (x, y, weight, currentObjective and
+// the feeding input) in shared memory and runs one compact pass over them
+// per step -- the eat of step p fused with the swim of step p + 1, as in the
+// streaming kernel -- so the step's code stays small and a school of a few
+// hundred fish costs little more than its own pairs.  A school goes to the
+// queue of the smallest cluster that holds it (8, 4, 2 or 1 blocks):
 //   - a cluster first takes schools from the queue of its own size, then
-//     from the queues of smaller multi-block clusters; the per-step maxima
-//     and barycentre partials of its C blocks meet in rank 0's shared memory
-//     through distributed shared memory, with one cluster barrier per step
-//     (partials double-buffered by step parity);
+//     from the queues of smaller multi-block clusters; the warps of its C
+//     blocks combine the per-step maxima by atomics in rank 0's shared
+//     memory (distributed shared memory), with one cluster barrier per step,
+//     and the barycentre partials follow one and two barriers behind, folded
+//     in a fixed order;
 //   - when those run out, every block pops single-block schools on its own
-//     and reduces with __syncthreads only.
+//     and synchronises with __syncthreads only.
 // The per-step order within a school is the paper's (Sec. 2.1.2 swim,
 // Sec. 2.1.1 objective, delta, the Sec. 2.3.2 max, feeding, barycentre).
 // School k uses key seeds[k] and school id k, so it reproduces the
@@ -58,239 +62,283 @@ struct BatchArgs {
   fsb_step_stats* stats;                           // n_schools * n_steps, school-major
 };
 
-// Per-block partial of one step exchanged across the cluster (the sums in
-// the accumulation mode's partial type, so the exchange stays in binary32
-// in the binary32 modes).
+// Barycentre partials of one step: a warp's, a block's.
 template <typename Part>
-struct ClusterPartial {
-  uint32_t max_bits, e_key;
-  Part sum_w, sum_wx, sum_wy;
+struct Part3 {
+  Part w, x, y;
 };
 
 constexpr int kBatchThreads = 512;
-constexpr int kBatchFpt = 16;
+constexpr int kBatchWarps = kBatchThreads / 32;
+constexpr int kBlockFish = 8192;              // fish one block holds
+constexpr int kBlockPairs = kBlockFish / 2;
 constexpr int kMaxCluster = 8;
+// The block's fish in shared memory: five arrays of kBlockPairs float2
+// (fish 2p and 2p + 1 of the block's slice share element p).
+constexpr size_t kStateSmem = 5 * sizeof(float2) * kBlockPairs;
 
+// Shared-memory exchange of one block.  The step maxima go into rank 0's
+// slots by atomics (three slots rotate by step: a slot is read after the
+// barrier that ends its step's swim, and zeroed three steps ahead of its
+// next use).  Barycentre partials are double-buffered by step parity: the
+// warps' partials of step p are folded into the block's after the barrier
+// that ends step p's eat, and, on a cluster, the blocks' partials in rank 0
+// one barrier later.
 template <int ACC>
-struct BlockReduce {
+struct BatchShared {
   using Part = typename SumAcc<ACC>::Part;
-  uint32_t s_max[32], s_ekey[32];
-  Part s_w[32], s_x[32], s_y[32];
+  uint32_t slot_max[3], slot_ekey[3];
+  Part3<Part> warp_part[2][kBatchWarps];
+  Part3<Part> block_part[2][kMaxCluster];
 };
 
-// Block reduction of (max, key, three sums); the result is valid in thread 0.
-template <int ACC>
-__device__ __forceinline__ void block_reduce(BlockReduce<ACC>& R, uint32_t& m, uint32_t& e,
-                                             typename SumAcc<ACC>::Part& sw,
-                                             typename SumAcc<ACC>::Part& sx,
-                                             typename SumAcc<ACC>::Part& sy) {
-  using Part = typename SumAcc<ACC>::Part;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  constexpr int nw = kBatchThreads / 32;
-  m = warp_max(m);
-  e = warp_max(e);
-  sw = warp_tree(sw);
-  sx = warp_tree(sx);
-  sy = warp_tree(sy);
-  __syncthreads();  // previous use of R is finished
-  if (lane == 0) {
-    R.s_max[warp] = m;
-    R.s_ekey[warp] = e;
-    R.s_w[warp] = sw;
-    R.s_x[warp] = sx;
-    R.s_y[warp] = sy;
+// Fold of the warps' partials (warp 0; the result is valid in lanes 0-15).
+// Lanes 16-31 would only add zeros, which merge exactly, so the tree starts
+// at offset 8.
+template <typename Part>
+__device__ __forceinline__ Part3<Part> fold_warps(const Part3<Part>* wp) {
+  static_assert(kBatchWarps == 16, "fold tree sized for 16 warps");
+  const int lane = threadIdx.x & 31;
+  Part3<Part> r = wp[lane & 15];
+#pragma unroll
+  for (int off = 8; off > 0; off >>= 1) {
+    r.w = merge(r.w, shfl_xor(r.w, off));
+    r.x = merge(r.x, shfl_xor(r.x, off));
+    r.y = merge(r.y, shfl_xor(r.y, off));
   }
-  __syncthreads();
-  if (warp == 0) {
-    m = lane < nw ? R.s_max[lane] : 0u;
-    e = lane < nw ? R.s_ekey[lane] : 0u;
-    sw = lane < nw ? R.s_w[lane] : part_zero<Part>();
-    sx = lane < nw ? R.s_x[lane] : part_zero<Part>();
-    sy = lane < nw ? R.s_y[lane] : part_zero<Part>();
-    m = warp_max(m);
-    e = warp_max(e);
-    sw = warp_merge(sw);
-    sx = warp_merge(sx);
-    sy = warp_merge(sy);
-  }
+  return r;
 }
+
+__device__ __forceinline__ void put_sums(fsb_step_stats* st, double w, double x, double y) {
+  st->sum_w = w;
+  st->sum_wx = x;
+  st->sum_wy = y;
+}
+
+// The block's fish in shared memory.  D holds the step's feeding input
+// (delta, or prev - cur when feeding follows the paper's eat() value) --
+// except after the school's last swim, when it holds that swim's starting
+// objective (the state's prevObjective) and the final eat forms the input
+// from F and D.
+struct BlockState {
+  float2* X;
+  float2* Y;
+  float2* W;
+  float2* F;  // currentObjective
+  float2* D;
+};
 
 // Runs one school on `nb` blocks (this block is rank `rank`): load or
 // initialise, all steps, write back.  For nb > 1 the caller's cluster must
-// contain exactly nb blocks that all call this with the same school.
+// contain exactly nb blocks that all call this with the same school, and
+// rank 0's slots must be zero (they are again on return).
+//
+// Pass p = 0 .. T over the block's fish pairs: the eat of step p with
+// normaliser N_p and its barycentre terms (p >= 1), then the swim of step
+// p + 1 with its objective and maxima (p < T).  One barrier follows each
+// pass (a cluster barrier for nb > 1):
+//   before it: each warp's maxima of step p + 1 into rank 0's slots
+//              (atomics) and its barycentre partial of step p;
+//   after it:  rank 0 zeroes the slots of step p + 3; warp 0 folds the
+//              block's partial of step p (nb = 1: the step's sums; else into
+//              rank 0's block_part), rank 0 folds the blocks' partials of
+//              step p - 1, and every thread reads M_{p+1} and E_{p+1}.
 template <int ACC, bool VAR>
 __device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int rank, int nb,
-                                           BlockReduce<ACC>& R,
-                                           ClusterPartial<typename SumAcc<ACC>::Part> (*xchg)[kMaxCluster],
-                                           uint32_t* s_M,
-                                           uint32_t* s_E, float (*spv)[kBatchThreads]) {
+                                           BatchShared<ACC>& S, const BlockState& B) {
   using Acc = SumAcc<ACC>;
   using Part = typename Acc::Part;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint64_t s_lo = a.offsets[k];
   // in-school fish indices fit 32 bits (schools hold at most C * 8192 fish)
   const uint32_t n = static_cast<uint32_t>(a.offsets[k + 1] - s_lo);
-  // an even slice keeps each fish pair (one swim block) in one thread
+  // an even slice keeps each fish pair (one swim block) in one block
   const uint32_t slice = ((n + nb - 1) / nb + 1) & ~1u;
   const uint32_t lo = static_cast<uint32_t>(rank) * slice;
   const uint32_t hi = lo + slice < n ? lo + slice : n;
-  // slot q of this thread is fish lo + 2 (tid + (q / 2) kBatchThreads) + q % 2
-  // (in-school index); slots q < nq are in the school
-  auto fish = [&](int q) -> uint32_t {
-    return lo + 2u * (static_cast<uint32_t>(tid) + static_cast<uint32_t>(q >> 1) * kBatchThreads) +
-           static_cast<uint32_t>(q & 1);
-  };
-  int nq = 0;
-#pragma unroll
-  for (int q = 0; q < kBatchFpt; ++q)
-    if (fish(q) < hi) nq = q + 1;
+  const uint32_t nf = hi > lo ? hi - lo : 0u;     // this block's fish
+  const uint32_t np = (nf + 1) / 2;               // ... and pairs; the last may be half
+  const uint32_t pair0 = lo / 2;                  // in-school pair index of element 0
   const Key key{static_cast<uint32_t>(a.seeds[k]), static_cast<uint32_t>(a.seeds[k] >> 32)};
   const uint32_t school = k;
   const Physics<float> ph = kernel_physics<VAR>(a.ph);
   cg::cluster_group cluster = cg::this_cluster();
+  // rank 0's exchange (this block's own for nb = 1)
+  BatchShared<ACC>* S0 = nb > 1 ? cluster.map_shared_rank(&S, 0) : &S;
+  fsb_step_stats* const st = a.stats + static_cast<uint64_t>(k) * a.n_steps;
+  const uint32_t T = a.n_steps;
 
-  // prevObjective of each fish waits in shared memory (spv[q][tid]); the
-  // other four fields stay in registers
-  float x[kBatchFpt], y[kBatchFpt], w[kBatchFpt], f[kBatchFpt];
+  // load (or initialise) the slice; the second fish of a half pair is zero
+  for (uint32_t e = tid; e < np; e += kBatchThreads) {
+    float xv[2] = {0.f, 0.f}, yv[2] = {0.f, 0.f}, wv[2] = {0.f, 0.f}, fv[2] = {0.f, 0.f};
 #pragma unroll
-  for (int q = 0; q < kBatchFpt; ++q) {
-    const uint32_t i = fish(q);  // index in school
-    if (q < nq) {
-      if (a.init) {
-        init_fish(key, school, i, a.weight_mode, ph, x[q], y[q], w[q]);
-      } else {
-        x[q] = a.x[s_lo + i];
-        y[q] = a.y[s_lo + i];
-        w[q] = a.w[s_lo + i];
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t i = lo + 2 * e + h;  // index in school
+      if (2 * e + h < nf) {
+        if (a.init) {
+          init_fish(key, school, i, a.weight_mode, ph, xv[h], yv[h], wv[h]);
+        } else {
+          xv[h] = a.x[s_lo + i];
+          yv[h] = a.y[s_lo + i];
+          wv[h] = a.w[s_lo + i];
+        }
+        fv[h] = objective(xv[h], yv[h]);
       }
-      f[q] = objective(x[q], y[q]);
-    } else {
-      x[q] = y[q] = w[q] = f[q] = 0.f;
     }
+    B.X[e] = make_float2(xv[0], xv[1]);
+    B.Y[e] = make_float2(yv[0], yv[1]);
+    B.W[e] = make_float2(wv[0], wv[1]);
+    B.F[e] = make_float2(fv[0], fv[1]);
   }
 
-  // Each step: swim -> local maxima (+ the previous step's sums) -> one
-  // exchange -> eat.  The exchange of step u carries the sums of step u - 1;
-  // one extra exchange after the last step carries the last sums.
-  Part sw = part_zero<Part>(), sx = part_zero<Part>(), sy = part_zero<Part>();
-  for (uint32_t u = 1; u <= a.n_steps + 1; ++u) {
-    const bool swim_step = u <= a.n_steps;
+  const uint32_t last = T + (nb > 1 ? 1u : 0u);  // a cluster's last fold needs one more barrier
+  const uint64_t t0 = *a.base_step_ptr;
+  float N = 0.f;  // feeding normaliser of the pass's eat
+  for (uint32_t p = 0; p <= last; ++p) {
+    const bool do_eat = p >= 1 && p <= T;
+    const bool do_swim = p < T;
+    const bool last_swim = p + 1 == T;  // D keeps the starting objective
+    const bool last_eat = p == T;       // the input comes from F and D
+    const uint32_t t = static_cast<uint32_t>(t0 + p + 1);
     uint32_t mb = 0, ek = 0;
-    if (swim_step) {
-      const uint32_t t = static_cast<uint32_t>(*a.base_step_ptr + u);
-      Words4 r{};
-#pragma unroll
-      for (int q = 0; q < kBatchFpt; ++q) {
-        if (q < nq) {
-          const float old = f[q];
-          spv[q][tid] = old;
-          if ((q & 1) == 0) r = pair_draw(key, school, fish(q) >> 1, t);
-          swim(x[q], y[q], r.v[2 * (q & 1)], r.v[2 * (q & 1) + 1], swim_width(ph, w[q]), ph);
-          f[q] = objective(x[q], y[q]);
-          const uint32_t mm = abs_bits(__fsub_rn(f[q], old));
-          const uint32_t ee = order_key(__fsub_rn(old, f[q]));
-          mb = mm > mb ? mm : mb;
-          ek = ee > ek ? ee : ek;
+    Acc acc;
+    if (do_eat || do_swim) {
+      for (uint32_t e = tid; e < np; e += kBatchThreads) {
+        const bool two = 2 * e + 1 < nf;
+        float2 xv = B.X[e], yv = B.Y[e], fv = B.F[e];
+        float2 wv = (do_eat || ph.swim_mode) ? B.W[e] : make_float2(0.f, 0.f);
+        if (do_eat) {
+          const float2 dv = B.D[e];
+          float g0 = dv.x, g1 = dv.y;
+          if (last_eat) {
+            g0 = ph.feed_mode ? __fsub_rn(dv.x, fv.x) : __fsub_rn(fv.x, dv.x);
+            g1 = ph.feed_mode ? __fsub_rn(dv.y, fv.y) : __fsub_rn(fv.y, dv.y);
+          }
+          if (N > 0.f) {
+            wv.x = eat(wv.x, g0, N, ph);
+            wv.y = eat(wv.y, g1, N, ph);
+          }
+          acc.add(wv.x, xv.x, yv.x);
+          if (two) acc.add(wv.y, xv.y, yv.y);
+          B.W[e] = wv;
+        }
+        if (do_swim) {
+          const Words4 r = pair_draw(key, school, pair0 + e, t);
+          const float o0 = fv.x, o1 = fv.y;
+          swim(xv.x, yv.x, r.v[0], r.v[1], swim_width(ph, wv.x), ph);
+          swim(xv.y, yv.y, r.v[2], r.v[3], swim_width(ph, wv.y), ph);
+          fv.x = objective(xv.x, yv.x);
+          fv.y = objective(xv.y, yv.y);
+          const float i0 = __fsub_rn(o0, fv.x), i1 = __fsub_rn(o1, fv.y);  // prev - cur
+          const float d0 = __fsub_rn(fv.x, o0), d1 = __fsub_rn(fv.y, o1);  // delta
+          uint32_t m = abs_bits(d0), q = order_key(i0);
+          if (two) {
+            const uint32_t m1 = abs_bits(d1), q1 = order_key(i1);
+            m = m1 > m ? m1 : m;
+            q = q1 > q ? q1 : q;
+          }
+          mb = m > mb ? m : mb;
+          ek = q > ek ? q : ek;
+          B.X[e] = xv;
+          B.Y[e] = yv;
+          B.F[e] = fv;
+          B.D[e] = last_swim ? make_float2(o0, o1)
+                             : (ph.feed_mode ? make_float2(i0, i1) : make_float2(d0, d1));
         }
       }
     }
-    block_reduce<ACC>(R, mb, ek, sw, sx, sy);
-    if (nb == 1) {
-      if (tid == 0) {
-        *s_M = mb;
-        *s_E = ek;
-        if (u > 1) {
-          fsb_step_stats* st = a.stats + static_cast<uint64_t>(k) * a.n_steps + (u - 2);
-          st->sum_w = to_double(sw);
-          st->sum_wx = to_double(sx);
-          st->sum_wy = to_double(sy);
+    if (do_swim) {
+      mb = warp_max(mb);
+      ek = warp_max(ek);
+      if (lane == 0) {
+        atomicMax(&S0->slot_max[(p + 1) % 3], mb);
+        atomicMax(&S0->slot_ekey[(p + 1) % 3], ek);
+      }
+    }
+    if (do_eat) {
+      Part3<Part> wp;
+      wp.w = warp_tree(acc.pw());
+      wp.x = warp_tree(acc.px());
+      wp.y = warp_tree(acc.py());
+      if (lane == 0) S.warp_part[p & 1][warp] = wp;
+    }
+    if (nb > 1)
+      cluster.sync();
+    else
+      __syncthreads();
+    if (rank == 0 && tid == 0) {
+      S.slot_max[p % 3] = 0u;
+      S.slot_ekey[p % 3] = 0u;
+    }
+    if (warp == 0) {
+      if (do_eat) {
+        const Part3<Part> bp = fold_warps(S.warp_part[p & 1]);
+        if (lane == 0) {
+          if (nb == 1)
+            put_sums(st + (p - 1), to_double(bp.w), to_double(bp.x), to_double(bp.y));
+          else
+            S0->block_part[p & 1][rank] = bp;
         }
       }
-      __syncthreads();
-    } else {
-      // every block writes its partial into rank 0's slot for this parity
-      if (tid == 0) {
-        ClusterPartial<Part>* dst = cluster.map_shared_rank(&xchg[u & 1][rank], 0);
-        ClusterPartial<Part> p;
-        p.max_bits = mb;
-        p.e_key = ek;
-        p.sum_w = sw;
-        p.sum_wx = sx;
-        p.sum_wy = sy;
-        *dst = p;
-      }
-      cluster.sync();
-      // fold the nb partials in rank order (identical in every block)
-      if (tid == 0) {
-        const ClusterPartial<Part>* src = cluster.map_shared_rank(&xchg[u & 1][0], 0);
-        uint32_t m = 0, e = 0;
+      // the blocks' partials of step p - 1, in rank order
+      if (nb > 1 && rank == 0 && lane == 0 && p >= 2) {
+        const Part3<Part>* src = S.block_part[(p - 1) & 1];
         Part fw = part_zero<Part>(), fx = part_zero<Part>(), fy = part_zero<Part>();
         for (int r = 0; r < nb; ++r) {
-          const ClusterPartial<Part> p = src[r];
-          m = p.max_bits > m ? p.max_bits : m;
-          e = p.e_key > e ? p.e_key : e;
-          fw = merge(fw, p.sum_w);
-          fx = merge(fx, p.sum_wx);
-          fy = merge(fy, p.sum_wy);
+          fw = merge(fw, src[r].w);
+          fx = merge(fx, src[r].x);
+          fy = merge(fy, src[r].y);
         }
-        *s_M = m;
-        *s_E = e;
-        if (rank == 0 && u > 1) {
-          fsb_step_stats* st = a.stats + static_cast<uint64_t>(k) * a.n_steps + (u - 2);
-          st->sum_w = to_double(fw);
-          st->sum_wx = to_double(fx);
-          st->sum_wy = to_double(fy);
-        }
-      }
-      __syncthreads();
-    }
-    if (!swim_step) break;
-    const float M = __uint_as_float(*s_M);
-    // feeding normaliser: M_u, or the paper's eat() value E_u
-    const float N = ph.feed_mode ? key_to_value(*s_E, 0.f) : M;
-    if (rank == 0 && tid == 0) {
-      fsb_step_stats* st = a.stats + static_cast<uint64_t>(k) * a.n_steps + (u - 1);
-      st->max_abs_delta = static_cast<double>(M);
-      st->eat_max_diff = static_cast<double>(key_to_value(*s_E, 0.f));
-    }
-    // eat of step u and its barycentre partials
-    Acc acc;
-#pragma unroll
-    for (int q = 0; q < kBatchFpt; ++q) {
-      if (q < nq) {
-        if (N > 0.f)
-          w[q] = eat(w[q],
-                     ph.feed_mode ? __fsub_rn(spv[q][tid], f[q]) : __fsub_rn(f[q], spv[q][tid]),
-                     N, ph);
-        acc.add(w[q], x[q], y[q]);
+        put_sums(st + (p - 2), to_double(fw), to_double(fx), to_double(fy));
       }
     }
-    sw = acc.pw();
-    sx = acc.px();
-    sy = acc.py();
+    if (do_swim) {
+      const float M = __uint_as_float(S0->slot_max[(p + 1) % 3]);
+      const uint32_t E_key = S0->slot_ekey[(p + 1) % 3];
+      const float E = key_to_value(E_key, 0.f);
+      // feeding normaliser: M, or the paper's eat() value E
+      N = ph.feed_mode ? E : M;
+      if (rank == 0 && tid == 0) {
+        st[p].max_abs_delta = static_cast<double>(M);
+        st[p].eat_max_diff = static_cast<double>(E);
+      }
+    }
   }
-  if (nb > 1) cluster.sync();  // rank 0's slots are free again for the next school
+  // rank 0 has read every block's partials, and its slots are zero, before
+  // any block leaves for the next school
+  if (nb > 1) cluster.sync();
 
-#pragma unroll
-  for (int q = 0; q < kBatchFpt; ++q) {
-    const uint32_t i = fish(q);
-    if (q < nq) {
-      a.x[s_lo + i] = x[q];
-      a.y[s_lo + i] = y[q];
-      a.w[s_lo + i] = w[q];
-      a.pv[s_lo + i] = a.n_steps ? spv[q][tid] : f[q];
+  for (uint32_t e = tid; e < np; e += kBatchThreads) {
+    const float2 xv = B.X[e], yv = B.Y[e], wv = B.W[e];
+    const float2 pv = T ? B.D[e] : B.F[e];
+    const uint64_t g = s_lo + lo + 2 * e;
+    a.x[g] = xv.x;
+    a.y[g] = yv.x;
+    a.w[g] = wv.x;
+    a.pv[g] = pv.x;
+    if (2 * e + 1 < nf) {
+      a.x[g + 1] = xv.y;
+      a.y[g + 1] = yv.y;
+      a.w[g + 1] = wv.y;
+      a.pv[g + 1] = pv.y;
     }
   }
+  __syncthreads();  // the slice's shared state is free for the next school
 }
 
 template <int CLUSTER, int ACC, bool VAR>
 __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs a) {
-  __shared__ BlockReduce<ACC> R;
-  __shared__ ClusterPartial<typename SumAcc<ACC>::Part> xchg[2][kMaxCluster];
-  __shared__ float spv[kBatchFpt][kBatchThreads];
-  __shared__ uint32_t s_M, s_E, s_pick;
+  __shared__ BatchShared<ACC> S;
+  __shared__ uint32_t s_pick;
+  extern __shared__ float2 state_smem[];
+  const BlockState B{state_smem, state_smem + kBlockPairs, state_smem + 2 * kBlockPairs,
+                     state_smem + 3 * kBlockPairs, state_smem + 4 * kBlockPairs};
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = static_cast<int>(cluster.block_rank());
+  if (threadIdx.x < 3) {
+    S.slot_max[threadIdx.x] = 0u;  // visible to the cluster after the first pick's barriers
+    S.slot_ekey[threadIdx.x] = 0u;
+  }
 
   // Phase 1 (whole cluster per school) through the multi-block queues from
   // this launch's own on, then phase 2 (each block on its own) through the
@@ -319,7 +367,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs a) {
       continue;
     }
     run_school<ACC, VAR>(a, a.order[a.queue_lo[t] + idx], whole_cluster ? rank : 0,
-                         whole_cluster ? CLUSTER : 1, R, xchg, &s_M, &s_E, spv);
+                         whole_cluster ? CLUSTER : 1, S, B);
   }
 }
 
@@ -355,7 +403,7 @@ cudaLaunchConfig_t make_config(int cluster, int grid, cudaStream_t s, cudaLaunch
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(kBatchThreads);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = kStateSmem;
   cfg.stream = s;
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = cluster;
@@ -375,13 +423,22 @@ cudaError_t launch_bump_step(unsigned long long* base_step, uint32_t n, cudaStre
   return cudaGetLastError();
 }
 
-uint64_t batch_block_capacity() { return static_cast<uint64_t>(kBatchThreads) * kBatchFpt; }
+uint64_t batch_block_capacity() { return kBlockFish; }
 int batch_threads() { return kBatchThreads; }
 
 // Clusters of `cluster` blocks that can be resident at once (0: cannot run).
+// Also lets the cluster size's kernels (default and variant model) use the
+// shared memory that holds a block's fish, so it runs before any launch.
 int batch_max_clusters(int cluster, int acc) {
   const void* fn = pick(cluster, acc);
   if (!fn) return 0;
+  for (const void* f : {fn, pick(cluster, acc, true)}) {
+    if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kStateSmem)) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+  }
   cudaLaunchAttribute attr[1];
   cudaLaunchConfig_t cfg = make_config(cluster, cluster, nullptr, attr);
   int n = 0;
