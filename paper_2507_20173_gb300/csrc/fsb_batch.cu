@@ -30,6 +30,7 @@
 // launch of single blocks takes the SMs the clusters leave over); all of
 // them share the queues, so the launches that finish first help the rest.
 #include <cstdint>
+#include <cstring>
 
 #include <cooperative_groups.h>
 
@@ -92,16 +93,17 @@ struct BatchShared {
   Part3<Part> block_part[2][kMaxCluster];
 };
 
-// Fold of the warps' partials (warp 0; the result is valid in lanes 0-15).
-// Lanes 16-31 would only add zeros, which merge exactly, so the tree starts
-// at offset 8.
+// Fold of the warps' partials by one warp, a fixed xor tree over the
+// kBatchWarps partials (lanes beyond them repeat them); the result is valid
+// in every lane.
 template <typename Part>
 __device__ __forceinline__ Part3<Part> fold_warps(const Part3<Part>* wp) {
-  static_assert(kBatchWarps == 16, "fold tree sized for 16 warps");
+  static_assert(kBatchWarps <= 32 && (kBatchWarps & (kBatchWarps - 1)) == 0,
+                "fold tree over a power-of-two warp count");
   const int lane = threadIdx.x & 31;
-  Part3<Part> r = wp[lane & 15];
+  Part3<Part> r = wp[lane & (kBatchWarps - 1)];
 #pragma unroll
-  for (int off = 8; off > 0; off >>= 1) {
+  for (int off = kBatchWarps / 2; off > 0; off >>= 1) {
     r.w = merge(r.w, shfl_xor(r.w, off));
     r.x = merge(r.x, shfl_xor(r.x, off));
     r.y = merge(r.y, shfl_xor(r.y, off));
@@ -109,10 +111,25 @@ __device__ __forceinline__ Part3<Part> fold_warps(const Part3<Part>* wp) {
   return r;
 }
 
-__device__ __forceinline__ void put_sums(fsb_step_stats* st, double w, double x, double y) {
-  st->sum_w = w;
-  st->sum_wx = x;
-  st->sum_wy = y;
+// A step's barycentre sums go out as the accumulation mode's raw partial
+// in the bits of each binary64 field (binary32: the low word; compensated
+// pair: hi in the low word, lo in the high word), and the host converts them
+// after the copy-out (batch_finish_stats), which keeps binary64 arithmetic,
+// slow on this GPU, off the per-step critical path.
+__device__ __forceinline__ double raw_sum(float v) {
+  return __longlong_as_double(static_cast<long long>(__float_as_uint(v)));
+}
+__device__ __forceinline__ double raw_sum(double v) { return v; }
+__device__ __forceinline__ double raw_sum(F2 v) {
+  return __longlong_as_double(static_cast<long long>(
+      (static_cast<unsigned long long>(__float_as_uint(v.lo)) << 32) | __float_as_uint(v.hi)));
+}
+
+template <typename Part>
+__device__ __forceinline__ void put_sums(fsb_step_stats* st, Part w, Part x, Part y) {
+  st->sum_w = raw_sum(w);
+  st->sum_wx = raw_sum(x);
+  st->sum_wy = raw_sum(y);
 }
 
 // The block's fish in shared memory.  D holds the step's feeding input
@@ -275,7 +292,7 @@ __device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int r
         const Part3<Part> bp = fold_warps(S.warp_part[p & 1]);
         if (lane == 0) {
           if (nb == 1)
-            put_sums(st + (p - 1), to_double(bp.w), to_double(bp.x), to_double(bp.y));
+            put_sums(st + (p - 1), bp.w, bp.x, bp.y);
           else
             S0->block_part[p & 1][rank] = bp;
         }
@@ -289,7 +306,7 @@ __device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int r
           fx = merge(fx, src[r].x);
           fy = merge(fy, src[r].y);
         }
-        put_sums(st + (p - 2), to_double(fw), to_double(fx), to_double(fy));
+        put_sums(st + (p - 2), fw, fx, fy);
       }
     }
     if (do_swim) {
@@ -424,6 +441,25 @@ cudaError_t launch_bump_step(unsigned long long* base_step, uint32_t n, cudaStre
 }
 
 uint64_t batch_block_capacity() { return kBlockFish; }
+
+void batch_finish_stats(fsb_step_stats* st, size_t count, int acc) {
+  if (acc == kAccF64) return;
+  auto conv = [acc](double& v) {
+    uint64_t bits;
+    std::memcpy(&bits, &v, sizeof(bits));
+    const uint32_t hb = static_cast<uint32_t>(bits), lb = static_cast<uint32_t>(bits >> 32);
+    float hi, lo;
+    std::memcpy(&hi, &hb, sizeof(hi));
+    std::memcpy(&lo, &lb, sizeof(lo));
+    v = acc == kAccKahan32 ? static_cast<double>(hi) + static_cast<double>(lo)
+                           : static_cast<double>(hi);
+  };
+  for (size_t i = 0; i < count; ++i) {
+    conv(st[i].sum_w);
+    conv(st[i].sum_wx);
+    conv(st[i].sum_wy);
+  }
+}
 int batch_threads() { return kBatchThreads; }
 
 // Clusters of `cluster` blocks that can be resident at once (0: cannot run).

@@ -372,10 +372,11 @@ int fsb_batch_step(fsb_batch_handle b, uint32_t n_steps, fsb_step_stats* host_st
   b->step += n_steps;
   b->last_n = n_steps;
   if (host_stats && n_steps) {
-    BCUDA(cudaMemcpyAsync(host_stats, b->d_stats,
-                          sizeof(fsb_step_stats) * static_cast<size_t>(b->n_schools) * n_steps,
+    const size_t count = static_cast<size_t>(b->n_schools) * n_steps;
+    BCUDA(cudaMemcpyAsync(host_stats, b->d_stats, sizeof(fsb_step_stats) * count,
                           cudaMemcpyDeviceToHost, b->stream));
     BCUDA(cudaStreamSynchronize(b->stream));
+    fsb::batch_finish_stats(host_stats, count, b->L.acc);
   }
   return FSB_OK;
 }

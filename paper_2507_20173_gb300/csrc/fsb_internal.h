@@ -209,6 +209,9 @@ cudaError_t launch_batch(const BatchLaunch& L, cudaStream_t s, const cudaStream_
                          cudaEvent_t fork, const cudaEvent_t* join);
 int batch_max_clusters(int cluster, int acc);
 uint64_t batch_block_capacity();
+// Host side: completes the barycentre sums of `count` records copied out of
+// the batch kernel's statistics (raw partials of accumulation mode acc).
+void batch_finish_stats(fsb_step_stats* st, size_t count, int acc);
 int batch_threads();
 cudaError_t launch_bump_step(unsigned long long* base_step, uint32_t n, cudaStream_t s);
 
