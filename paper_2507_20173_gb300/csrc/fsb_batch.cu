@@ -145,6 +145,75 @@ struct BlockState {
   float2* D;
 };
 
+// Per-pass context of one block.
+struct PassCtx {
+  Key key;
+  uint32_t school;
+  uint32_t pair0;   // in-school pair index of element 0
+  uint32_t t;       // step counter of the pass's swim
+  float N;          // feeding normaliser of the pass's eat (no feeding if <= 0)
+};
+
+// One fish pair of a pass: the eat of step p and its barycentre terms (EAT),
+// then the swim of step p + 1 with its objective and maxima (SWIM).
+// LAST_SWIM: D keeps the swim's starting objectives; LAST_EAT: the feeding
+// input comes from F and D.  `two`: the pair's second fish is in the school.
+template <bool EAT, bool SWIM, bool LAST_SWIM, bool LAST_EAT, typename Acc>
+__device__ __forceinline__ void pair_pass(const BlockState& B, uint32_t e, bool two,
+                                          const PassCtx& c, const Physics<float>& ph, Acc& acc,
+                                          uint32_t& mb, uint32_t& ek) {
+  float2 xv = B.X[e], yv = B.Y[e], fv = B.F[e];
+  float2 wv = (EAT || ph.swim_mode) ? B.W[e] : make_float2(0.f, 0.f);
+  if (EAT) {
+    const float2 dv = B.D[e];
+    float g0 = dv.x, g1 = dv.y;
+    if (LAST_EAT) {
+      g0 = ph.feed_mode ? __fsub_rn(dv.x, fv.x) : __fsub_rn(fv.x, dv.x);
+      g1 = ph.feed_mode ? __fsub_rn(dv.y, fv.y) : __fsub_rn(fv.y, dv.y);
+    }
+    if (c.N > 0.f) {
+      wv.x = eat(wv.x, g0, c.N, ph);
+      wv.y = eat(wv.y, g1, c.N, ph);
+    }
+    acc.add2(wv.x, xv.x, yv.x, two ? wv.y : 0.f, xv.y, yv.y);
+    B.W[e] = wv;
+  }
+  if (SWIM) {
+    const Words4 r = pair_draw(c.key, c.school, c.pair0 + e, c.t);
+    const float o0 = fv.x, o1 = fv.y;
+    swim(xv.x, yv.x, r.v[0], r.v[1], swim_width(ph, wv.x), ph);
+    swim(xv.y, yv.y, r.v[2], r.v[3], swim_width(ph, wv.y), ph);
+    fv.x = objective(xv.x, yv.x);
+    fv.y = objective(xv.y, yv.y);
+    const float i0 = __fsub_rn(o0, fv.x), i1 = __fsub_rn(o1, fv.y);  // prev - cur
+    const float d0 = __fsub_rn(fv.x, o0), d1 = __fsub_rn(fv.y, o1);  // delta
+    const uint32_t m0 = abs_bits(d0), q0 = order_key(i0);
+    const uint32_t m1 = two ? abs_bits(d1) : 0u, q1 = two ? order_key(i1) : 0u;
+    mb = max(mb, max(m0, m1));
+    ek = max(ek, max(q0, q1));
+    B.X[e] = xv;
+    B.Y[e] = yv;
+    B.F[e] = fv;
+    B.D[e] = LAST_SWIM ? make_float2(o0, o1)
+                       : (ph.feed_mode ? make_float2(i0, i1) : make_float2(d0, d1));
+  }
+}
+
+// All of this thread's pairs in one pass: elements tid, tid + kBatchThreads,
+// ... below np, two per iteration so that two independent draws overlap.
+template <bool EAT, bool SWIM, bool LAST_SWIM, bool LAST_EAT, typename Acc>
+__device__ __forceinline__ void block_pass(const BlockState& B, uint32_t np, uint32_t nf,
+                                           const PassCtx& c, const Physics<float>& ph, Acc& acc,
+                                           uint32_t& mb, uint32_t& ek) {
+  uint32_t e = threadIdx.x;
+  for (; e + kBatchThreads < np; e += 2 * kBatchThreads) {
+    pair_pass<EAT, SWIM, LAST_SWIM, LAST_EAT>(B, e, true, c, ph, acc, mb, ek);
+    const uint32_t e2 = e + kBatchThreads;
+    pair_pass<EAT, SWIM, LAST_SWIM, LAST_EAT>(B, e2, 2 * e2 + 1 < nf, c, ph, acc, mb, ek);
+  }
+  if (e < np) pair_pass<EAT, SWIM, LAST_SWIM, LAST_EAT>(B, e, 2 * e + 1 < nf, c, ph, acc, mb, ek);
+}
+
 // Runs one school on `nb` blocks (this block is rank `rank`): load or
 // initialise, all steps, write back.  For nb > 1 the caller's cluster must
 // contain exactly nb blocks that all call this with the same school, and
@@ -214,56 +283,19 @@ __device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int r
   for (uint32_t p = 0; p <= last; ++p) {
     const bool do_eat = p >= 1 && p <= T;
     const bool do_swim = p < T;
-    const bool last_swim = p + 1 == T;  // D keeps the starting objective
-    const bool last_eat = p == T;       // the input comes from F and D
-    const uint32_t t = static_cast<uint32_t>(t0 + p + 1);
+    PassCtx c{key, school, pair0, static_cast<uint32_t>(t0 + p + 1), N};
     uint32_t mb = 0, ek = 0;
     Acc acc;
-    if (do_eat || do_swim) {
-      for (uint32_t e = tid; e < np; e += kBatchThreads) {
-        const bool two = 2 * e + 1 < nf;
-        float2 xv = B.X[e], yv = B.Y[e], fv = B.F[e];
-        float2 wv = (do_eat || ph.swim_mode) ? B.W[e] : make_float2(0.f, 0.f);
-        if (do_eat) {
-          const float2 dv = B.D[e];
-          float g0 = dv.x, g1 = dv.y;
-          if (last_eat) {
-            g0 = ph.feed_mode ? __fsub_rn(dv.x, fv.x) : __fsub_rn(fv.x, dv.x);
-            g1 = ph.feed_mode ? __fsub_rn(dv.y, fv.y) : __fsub_rn(fv.y, dv.y);
-          }
-          if (N > 0.f) {
-            wv.x = eat(wv.x, g0, N, ph);
-            wv.y = eat(wv.y, g1, N, ph);
-          }
-          acc.add(wv.x, xv.x, yv.x);
-          if (two) acc.add(wv.y, xv.y, yv.y);
-          B.W[e] = wv;
-        }
-        if (do_swim) {
-          const Words4 r = pair_draw(key, school, pair0 + e, t);
-          const float o0 = fv.x, o1 = fv.y;
-          swim(xv.x, yv.x, r.v[0], r.v[1], swim_width(ph, wv.x), ph);
-          swim(xv.y, yv.y, r.v[2], r.v[3], swim_width(ph, wv.y), ph);
-          fv.x = objective(xv.x, yv.x);
-          fv.y = objective(xv.y, yv.y);
-          const float i0 = __fsub_rn(o0, fv.x), i1 = __fsub_rn(o1, fv.y);  // prev - cur
-          const float d0 = __fsub_rn(fv.x, o0), d1 = __fsub_rn(fv.y, o1);  // delta
-          uint32_t m = abs_bits(d0), q = order_key(i0);
-          if (two) {
-            const uint32_t m1 = abs_bits(d1), q1 = order_key(i1);
-            m = m1 > m ? m1 : m;
-            q = q1 > q ? q1 : q;
-          }
-          mb = m > mb ? m : mb;
-          ek = q > ek ? q : ek;
-          B.X[e] = xv;
-          B.Y[e] = yv;
-          B.F[e] = fv;
-          B.D[e] = last_swim ? make_float2(o0, o1)
-                             : (ph.feed_mode ? make_float2(i0, i1) : make_float2(d0, d1));
-        }
-      }
-    }
+    if (p == 0 && T > 1)
+      block_pass<false, true, false, false>(B, np, nf, c, ph, acc, mb, ek);
+    else if (p == 0 && T == 1)
+      block_pass<false, true, true, false>(B, np, nf, c, ph, acc, mb, ek);
+    else if (p + 1 < T)
+      block_pass<true, true, false, false>(B, np, nf, c, ph, acc, mb, ek);
+    else if (p + 1 == T)
+      block_pass<true, true, true, false>(B, np, nf, c, ph, acc, mb, ek);
+    else if (p == T)
+      block_pass<true, false, false, true>(B, np, nf, c, ph, acc, mb, ek);
     if (do_swim) {
       mb = warp_max(mb);
       ek = warp_max(ek);

@@ -99,6 +99,11 @@ struct SumAcc<kAccPlain32> {
 #pragma unroll
     for (int q = 0; q < 4; ++q) add(wi[q], xi[q], yi[q]);
   }
+  __device__ __forceinline__ void add2(float w0, float x0, float y0, float w1, float x1,
+                                       float y1) {
+    add(w0, x0, y0);
+    add(w1, x1, y1);
+  }
   __device__ __forceinline__ float rw() const { return w; }
   __device__ __forceinline__ float rx() const { return x; }
   __device__ __forceinline__ float ry() const { return y; }
@@ -137,6 +142,14 @@ struct SumAcc<kAccKahan32> {
     kadd(sx, cx, px);
     kadd(sy, cy, py);
   }
+  // Two fish (one swim pair): binary32 pair sums (one rounding each, exact
+  // when one weight is zero), then one compensated add per quantity.
+  __device__ __forceinline__ void add2(float w0, float x0, float y0, float w1, float x1,
+                                       float y1) {
+    kadd(sw, cw, __fadd_rn(w0, w1));
+    kadd(sx, cx, __fadd_rn(__fmul_rn(w0, x0), __fmul_rn(w1, x1)));
+    kadd(sy, cy, __fadd_rn(__fmul_rn(w0, y0), __fmul_rn(w1, y1)));
+  }
   __device__ __forceinline__ double rw() const { return double(sw) - double(cw); }
   __device__ __forceinline__ double rx() const { return double(sx) - double(cx); }
   __device__ __forceinline__ double ry() const { return double(sy) - double(cy); }
@@ -164,6 +177,11 @@ struct SumAcc<kAccF64> {
                                        const Real (&yi)[4]) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) add(wi[q], xi[q], yi[q]);
+  }
+  __device__ __forceinline__ void add2(float w0, float x0, float y0, float w1, float x1,
+                                       float y1) {
+    add(w0, x0, y0);
+    add(w1, x1, y1);
   }
   __device__ __forceinline__ double rw() const { return w; }
   __device__ __forceinline__ double rx() const { return x; }
