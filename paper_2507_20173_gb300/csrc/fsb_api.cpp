@@ -383,6 +383,11 @@ bool resident_config(int sms, int acc, int swim_mode, uint64_t n, fsb::ResidentL
     uint64_t grid = (n + per_block - 1) / per_block;
     if (grid > static_cast<uint64_t>(sms)) continue;
     if (grid < 1) grid = 1;
+    // spread over more SMs while every block keeps at least 2048 fish (a
+    // block's step is latency-bound below that)
+    const uint64_t spread = (n + 2047) / 2048;
+    const uint64_t most = spread < static_cast<uint64_t>(sms) ? spread : sms;
+    if (grid < most) grid = most;
     // even, so no fish pair (one swim block) straddles two blocks
     const uint64_t slice = ((n + grid - 1) / grid + 1) & ~1ull;
     const uint64_t threads = (slice + fpt - 1) / fpt;

@@ -36,6 +36,7 @@
 
 #include "fsb_device.cuh"
 #include "fsb_internal.h"
+#include "fsb_onchip.cuh"
 #include "fsb_reduce.cuh"
 
 namespace fsb {
@@ -111,107 +112,14 @@ __device__ __forceinline__ Part3<Part> fold_warps(const Part3<Part>* wp) {
   return r;
 }
 
-// A step's barycentre sums go out as the accumulation mode's raw partial
-// in the bits of each binary64 field (binary32: the low word; compensated
-// pair: hi in the low word, lo in the high word), and the host converts them
-// after the copy-out (batch_finish_stats), which keeps binary64 arithmetic,
-// slow on this GPU, off the per-step critical path.
-__device__ __forceinline__ double raw_sum(float v) {
-  return __longlong_as_double(static_cast<long long>(__float_as_uint(v)));
-}
-__device__ __forceinline__ double raw_sum(double v) { return v; }
-__device__ __forceinline__ double raw_sum(F2 v) {
-  return __longlong_as_double(static_cast<long long>(
-      (static_cast<unsigned long long>(__float_as_uint(v.lo)) << 32) | __float_as_uint(v.hi)));
-}
-
+// A step's barycentre sums go out as raw partials (raw_sum) and the host
+// converts them after the copy-out (batch_finish_stats), which keeps
+// binary64 arithmetic, slow on this GPU, off the per-step critical path.
 template <typename Part>
 __device__ __forceinline__ void put_sums(fsb_step_stats* st, Part w, Part x, Part y) {
   st->sum_w = raw_sum(w);
   st->sum_wx = raw_sum(x);
   st->sum_wy = raw_sum(y);
-}
-
-// The block's fish in shared memory.  D holds the step's feeding input
-// (delta, or prev - cur when feeding follows the paper's eat() value) --
-// except after the school's last swim, when it holds that swim's starting
-// objective (the state's prevObjective) and the final eat forms the input
-// from F and D.
-struct BlockState {
-  float2* X;
-  float2* Y;
-  float2* W;
-  float2* F;  // currentObjective
-  float2* D;
-};
-
-// Per-pass context of one block.
-struct PassCtx {
-  Key key;
-  uint32_t school;
-  uint32_t pair0;   // in-school pair index of element 0
-  uint32_t t;       // step counter of the pass's swim
-  float N;          // feeding normaliser of the pass's eat (no feeding if <= 0)
-};
-
-// One fish pair of a pass: the eat of step p and its barycentre terms (EAT),
-// then the swim of step p + 1 with its objective and maxima (SWIM).
-// LAST_SWIM: D keeps the swim's starting objectives; LAST_EAT: the feeding
-// input comes from F and D.  `two`: the pair's second fish is in the school.
-template <bool EAT, bool SWIM, bool LAST_SWIM, bool LAST_EAT, typename Acc>
-__device__ __forceinline__ void pair_pass(const BlockState& B, uint32_t e, bool two,
-                                          const PassCtx& c, const Physics<float>& ph, Acc& acc,
-                                          uint32_t& mb, uint32_t& ek) {
-  float2 xv = B.X[e], yv = B.Y[e], fv = B.F[e];
-  float2 wv = (EAT || ph.swim_mode) ? B.W[e] : make_float2(0.f, 0.f);
-  if (EAT) {
-    const float2 dv = B.D[e];
-    float g0 = dv.x, g1 = dv.y;
-    if (LAST_EAT) {
-      g0 = ph.feed_mode ? __fsub_rn(dv.x, fv.x) : __fsub_rn(fv.x, dv.x);
-      g1 = ph.feed_mode ? __fsub_rn(dv.y, fv.y) : __fsub_rn(fv.y, dv.y);
-    }
-    if (c.N > 0.f) {
-      wv.x = eat(wv.x, g0, c.N, ph);
-      wv.y = eat(wv.y, g1, c.N, ph);
-    }
-    acc.add2(wv.x, xv.x, yv.x, two ? wv.y : 0.f, xv.y, yv.y);
-    B.W[e] = wv;
-  }
-  if (SWIM) {
-    const Words4 r = pair_draw(c.key, c.school, c.pair0 + e, c.t);
-    const float o0 = fv.x, o1 = fv.y;
-    swim(xv.x, yv.x, r.v[0], r.v[1], swim_width(ph, wv.x), ph);
-    swim(xv.y, yv.y, r.v[2], r.v[3], swim_width(ph, wv.y), ph);
-    fv.x = objective(xv.x, yv.x);
-    fv.y = objective(xv.y, yv.y);
-    const float i0 = __fsub_rn(o0, fv.x), i1 = __fsub_rn(o1, fv.y);  // prev - cur
-    const float d0 = __fsub_rn(fv.x, o0), d1 = __fsub_rn(fv.y, o1);  // delta
-    const uint32_t m0 = abs_bits(d0), q0 = order_key(i0);
-    const uint32_t m1 = two ? abs_bits(d1) : 0u, q1 = two ? order_key(i1) : 0u;
-    mb = max(mb, max(m0, m1));
-    ek = max(ek, max(q0, q1));
-    B.X[e] = xv;
-    B.Y[e] = yv;
-    B.F[e] = fv;
-    B.D[e] = LAST_SWIM ? make_float2(o0, o1)
-                       : (ph.feed_mode ? make_float2(i0, i1) : make_float2(d0, d1));
-  }
-}
-
-// All of this thread's pairs in one pass: elements tid, tid + kBatchThreads,
-// ... below np, two per iteration so that two independent draws overlap.
-template <bool EAT, bool SWIM, bool LAST_SWIM, bool LAST_EAT, typename Acc>
-__device__ __forceinline__ void block_pass(const BlockState& B, uint32_t np, uint32_t nf,
-                                           const PassCtx& c, const Physics<float>& ph, Acc& acc,
-                                           uint32_t& mb, uint32_t& ek) {
-  uint32_t e = threadIdx.x;
-  for (; e + kBatchThreads < np; e += 2 * kBatchThreads) {
-    pair_pass<EAT, SWIM, LAST_SWIM, LAST_EAT>(B, e, true, c, ph, acc, mb, ek);
-    const uint32_t e2 = e + kBatchThreads;
-    pair_pass<EAT, SWIM, LAST_SWIM, LAST_EAT>(B, e2, 2 * e2 + 1 < nf, c, ph, acc, mb, ek);
-  }
-  if (e < np) pair_pass<EAT, SWIM, LAST_SWIM, LAST_EAT>(B, e, 2 * e + 1 < nf, c, ph, acc, mb, ek);
 }
 
 // Runs one school on `nb` blocks (this block is rank `rank`): load or
@@ -231,7 +139,7 @@ __device__ __forceinline__ void block_pass(const BlockState& B, uint32_t np, uin
 //              step p - 1, and every thread reads M_{p+1} and E_{p+1}.
 template <int ACC, bool VAR>
 __device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int rank, int nb,
-                                           BatchShared<ACC>& S, const BlockState& B) {
+                                           BatchShared<ACC>& S, const PairState& B) {
   using Acc = SumAcc<ACC>;
   using Part = typename Acc::Part;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -271,8 +179,8 @@ __device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int r
         fv[h] = objective(xv[h], yv[h]);
       }
     }
-    B.X[e] = make_float2(xv[0], xv[1]);
-    B.Y[e] = make_float2(yv[0], yv[1]);
+    B.Xd[e] = make_float2(xv[0], xv[1]);
+    B.Yd[e] = make_float2(yv[0], yv[1]);
     B.W[e] = make_float2(wv[0], wv[1]);
     B.F[e] = make_float2(fv[0], fv[1]);
   }
@@ -358,8 +266,8 @@ __device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int r
   if (nb > 1) cluster.sync();
 
   for (uint32_t e = tid; e < np; e += kBatchThreads) {
-    const float2 xv = B.X[e], yv = B.Y[e], wv = B.W[e];
-    const float2 pv = T ? B.D[e] : B.F[e];
+    const float2 xv = B.Xs[e], yv = B.Ys[e], wv = B.W[e];
+    const float2 pv = T ? B.Ds[e] : B.F[e];
     const uint64_t g = s_lo + lo + 2 * e;
     a.x[g] = xv.x;
     a.y[g] = yv.x;
@@ -380,8 +288,10 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs a) {
   __shared__ BatchShared<ACC> S;
   __shared__ uint32_t s_pick;
   extern __shared__ float2 state_smem[];
-  const BlockState B{state_smem, state_smem + kBlockPairs, state_smem + 2 * kBlockPairs,
-                     state_smem + 3 * kBlockPairs, state_smem + 4 * kBlockPairs};
+  float2* const X = state_smem;
+  float2* const Y = state_smem + kBlockPairs;
+  float2* const D = state_smem + 4 * kBlockPairs;
+  const PairState B{X, Y, D, X, Y, D, state_smem + 3 * kBlockPairs, state_smem + 2 * kBlockPairs};
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = static_cast<int>(cluster.block_rank());
   if (threadIdx.x < 3) {

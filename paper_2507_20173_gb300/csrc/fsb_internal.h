@@ -141,8 +141,9 @@ struct ResidentLaunch {
   int swim_mode;    // 1: weight-scaled swim (swims each step after the eat)
   int feed_mode;
   int acc;          // AccMode
-  int fpt;          // fish per thread: 4, 8, 12 or 16
-  int block;        // threads per block (<= resident_max_block(fpt))
+  int fpt;          // fish per thread a block can hold: 4, 8, 12 or 16
+  int block;        // threads per block (<= resident_max_block(fpt));
+                    // slice <= fpt * block
   int grid;         // blocks, all co-resident (cooperative launch)
   uint64_t base_step;
   uint32_t n_steps;
@@ -158,7 +159,7 @@ struct ResidentLaunch {
 cudaError_t launch_resident(const ResidentLaunch& L, cudaStream_t s);
 int resident_max_block(int fpt);
 int resident_blocks_per_sm(int fpt, int acc, int block, int swim_mode);
-size_t resident_smem_bytes(int fpt, int block);
+size_t resident_smem_bytes(uint64_t slice);
 
 // Work queues of a batch: queue t (t = 0, 1, 2) holds the schools run on
 // whole clusters of 8 >> t blocks, queue 3 the schools one block runs; each

@@ -1,0 +1,108 @@
+// fsb_onchip.cuh -- the per-pair pass of the on-chip kernels (batched
+// schools, resident single school): a block's fish live in shared memory as
+// float2 pairs (fish 2e and 2e + 1 of the block's slice share element e, the
+// two fish one swim draw moves), and one compact loop per pass walks this
+// thread's pairs.  The code of a pass stays small, so the instruction cache
+// holds it and a school of a few hundred fish costs little more than its own
+// pairs.
+#pragma once
+
+#include <cstdint>
+
+#include "fsb_device.cuh"
+#include "fsb_reduce.cuh"
+
+namespace fsb {
+
+// A block's fish.  Positions and the feeding input are read from the source
+// arrays and written to the destination arrays (the same arrays for an
+// in-place pass; a double-buffered pass keeps step u's positions and input
+// for the eat of step u while the swim of step u + 1 writes the others).
+// D holds a step's feeding input (delta, or prev - cur when feeding follows
+// the paper's eat() value) -- except after the school's last swim, when it
+// holds that swim's starting objective (the state's prevObjective) and the
+// final eat forms the input from F and D.
+struct PairState {
+  const float2* Xs;
+  const float2* Ys;
+  const float2* Ds;
+  float2* Xd;
+  float2* Yd;
+  float2* Dd;
+  float2* F;  // currentObjective
+  float2* W;
+};
+
+// Per-pass context of one block.
+struct PassCtx {
+  Key key;
+  uint32_t school;
+  uint32_t pair0;  // in-school pair index of element 0
+  uint32_t t;      // step counter of the pass's swim
+  float N;         // feeding normaliser of the pass's eat (no feeding if <= 0)
+};
+
+// One fish pair of a pass: the eat of step p and its barycentre terms (EAT),
+// then the swim of step p + 1 with its objective and maxima (SWIM).
+// LAST_SWIM: D keeps the swim's starting objectives; LAST_EAT: the feeding
+// input comes from F and D.  `two`: the pair's second fish is in the school
+// (a half pair's second fish is computed but neither summed nor maximised).
+template <bool EAT, bool SWIM, bool LAST_SWIM, bool LAST_EAT, typename Acc>
+__device__ __forceinline__ void pair_pass(const PairState& B, uint32_t e, bool two,
+                                          const PassCtx& c, const Physics<float>& ph, Acc& acc,
+                                          uint32_t& mb, uint32_t& ek) {
+  float2 xv = B.Xs[e], yv = B.Ys[e], fv = B.F[e];
+  float2 wv = (EAT || ph.swim_mode) ? B.W[e] : make_float2(0.f, 0.f);
+  if (EAT) {
+    const float2 dv = B.Ds[e];
+    float g0 = dv.x, g1 = dv.y;
+    if (LAST_EAT) {
+      g0 = ph.feed_mode ? __fsub_rn(dv.x, fv.x) : __fsub_rn(fv.x, dv.x);
+      g1 = ph.feed_mode ? __fsub_rn(dv.y, fv.y) : __fsub_rn(fv.y, dv.y);
+    }
+    if (c.N > 0.f) {
+      wv.x = eat(wv.x, g0, c.N, ph);
+      wv.y = eat(wv.y, g1, c.N, ph);
+    }
+    acc.add2(wv.x, xv.x, yv.x, two ? wv.y : 0.f, xv.y, yv.y);
+    B.W[e] = wv;
+  }
+  if (SWIM) {
+    const Words4 r = pair_draw(c.key, c.school, c.pair0 + e, c.t);
+    const float o0 = fv.x, o1 = fv.y;
+    swim(xv.x, yv.x, r.v[0], r.v[1], swim_width(ph, wv.x), ph);
+    swim(xv.y, yv.y, r.v[2], r.v[3], swim_width(ph, wv.y), ph);
+    fv.x = objective(xv.x, yv.x);
+    fv.y = objective(xv.y, yv.y);
+    const float i0 = __fsub_rn(o0, fv.x), i1 = __fsub_rn(o1, fv.y);  // prev - cur
+    const float d0 = __fsub_rn(fv.x, o0), d1 = __fsub_rn(fv.y, o1);  // delta
+    const uint32_t m0 = abs_bits(d0), q0 = order_key(i0);
+    const uint32_t m1 = two ? abs_bits(d1) : 0u, q1 = two ? order_key(i1) : 0u;
+    mb = max(mb, max(m0, m1));
+    ek = max(ek, max(q0, q1));
+    B.Xd[e] = xv;
+    B.Yd[e] = yv;
+    B.F[e] = fv;
+    B.Dd[e] = LAST_SWIM ? make_float2(o0, o1)
+                        : (ph.feed_mode ? make_float2(i0, i1) : make_float2(d0, d1));
+  }
+}
+
+// All of this thread's pairs in one pass: elements threadIdx.x,
+// threadIdx.x + blockDim.x, ... below np (nf fish), two per iteration so
+// that two independent draws overlap.
+template <bool EAT, bool SWIM, bool LAST_SWIM, bool LAST_EAT, typename Acc>
+__device__ __forceinline__ void block_pass(const PairState& B, uint32_t np, uint32_t nf,
+                                           const PassCtx& c, const Physics<float>& ph, Acc& acc,
+                                           uint32_t& mb, uint32_t& ek) {
+  const uint32_t step = blockDim.x;
+  uint32_t e = threadIdx.x;
+  for (; e + step < np; e += 2 * step) {
+    pair_pass<EAT, SWIM, LAST_SWIM, LAST_EAT>(B, e, true, c, ph, acc, mb, ek);
+    const uint32_t e2 = e + step;
+    pair_pass<EAT, SWIM, LAST_SWIM, LAST_EAT>(B, e2, 2 * e2 + 1 < nf, c, ph, acc, mb, ek);
+  }
+  if (e < np) pair_pass<EAT, SWIM, LAST_SWIM, LAST_EAT>(B, e, 2 * e + 1 < nf, c, ph, acc, mb, ek);
+}
+
+}  // namespace fsb

@@ -71,6 +71,24 @@ __device__ __forceinline__ double to_double(double v) { return v; }
 __device__ __forceinline__ double to_double(F2 v) {
   return static_cast<double>(v.hi) + static_cast<double>(v.lo);
 }
+// A partial in the bits of one binary64 word, unconverted: binary32 in the
+// low word; a compensated pair with hi in the low word and lo in the high
+// word; binary64 as is.  raw_to_sum completes one (binary64 arithmetic) where
+// its cost is off the per-step path.
+__device__ __forceinline__ double raw_sum(float v) {
+  return __longlong_as_double(static_cast<long long>(__float_as_uint(v)));
+}
+__device__ __forceinline__ double raw_sum(double v) { return v; }
+__device__ __forceinline__ double raw_sum(F2 v) {
+  return __longlong_as_double(static_cast<long long>(
+      (static_cast<unsigned long long>(__float_as_uint(v.lo)) << 32) | __float_as_uint(v.hi)));
+}
+__device__ __forceinline__ void raw_parts(double r, float& hi, float& lo) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(r));
+  hi = __uint_as_float(static_cast<uint32_t>(b));
+  lo = __uint_as_float(static_cast<uint32_t>(b >> 32));
+}
+
 template <typename T>
 __device__ __forceinline__ T part_zero();
 template <>
@@ -190,6 +208,25 @@ struct SumAcc<kAccF64> {
   __device__ __forceinline__ Part px() const { return x; }
   __device__ __forceinline__ Part py() const { return y; }
 };
+
+// The value of a raw partial of accumulation mode ACC, in that mode's Sum
+// type (the compensated pair as hi + lo in binary64).
+template <int ACC>
+__device__ __forceinline__ typename SumAcc<ACC>::Sum raw_to_sum(double r);
+template <>
+__device__ __forceinline__ float raw_to_sum<kAccPlain32>(double r) {
+  float hi, lo;
+  raw_parts(r, hi, lo);
+  return hi;
+}
+template <>
+__device__ __forceinline__ double raw_to_sum<kAccKahan32>(double r) {
+  float hi, lo;
+  raw_parts(r, hi, lo);
+  return to_double(F2{hi, lo});
+}
+template <>
+__device__ __forceinline__ double raw_to_sum<kAccF64>(double r) { return r; }
 
 __device__ __forceinline__ float sum2(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ double sum2(double a, double b) { return __dadd_rn(a, b); }

@@ -1,23 +1,25 @@
 // fsb_resident.cu -- the on-chip ("resident") single-school kernel.
 //
 // One cooperative launch advances a school by all n_steps of an fsb_step call.
-// Each thread keeps FPT fish (x, y, weight, currentObjective and
-// prevObjective) in registers for the whole call; HBM is read once at the
-// start and written once at the end.  Each step follows the paper's order
-// (Sec. 2.1.2 swim, Sec. 2.1.1 objective, delta, the Sec. 2.3.2 max
-// reduction, feeding, barycentre), with the phases of consecutive steps
-// overlapped:
+// Each block keeps its slice of the school in shared memory for the whole
+// call (HBM is read once at the start and written once at the end) and walks
+// it with the compact per-pair passes of fsb_onchip.cuh.  Each step follows
+// the paper's order (Sec. 2.1.2 swim, Sec. 2.1.1 objective, delta, the
+// Sec. 2.3.2 max reduction, feeding, barycentre), with the phases of
+// consecutive steps overlapped:
 //   A. swim + objective + delta of step u+1 for every fish (positions do not
-//      depend on weights), while the grid is still agreeing on M_u;
+//      depend on weights) into the other half of double-buffered position
+//      and feeding-input arrays, while the grid is still agreeing on M_u; the
+//      warps' maxima of step u+1 meet in shared memory by atomics;
 //   B. thread 0 waits for barrier u (one arrival per block on a monotonic
 //      counter; the wait is bounded by a %globaltimer deadline and gives up
-//      with FSB_ERR_TIMEOUT, so a missing block can never hang the GPU) and
+//      with FSB_ERR_TIMEOUT, so a missing block can never hang the GPU),
 //      reads M_u and the eat() value max(prev - cur) from a rotating slot
-//      that every block fed with one atomicMax (exact, order-free);
-//   C. eat of step u from the parked (delta, x, y) of step u, barycentre
-//      partials of step u;
-//   D. one block reduction for the maxima of step u+1 and the sums of step u;
-//      thread 0 writes the sums, feeds the slot of step u+1 and arrives.
+//      that every block fed with one atomicMax (exact, order-free), then at
+//      once hands the block's maxima of step u+1 to the grid and arrives at
+//      barrier u+1; warp 0 folds the block's barycentre partial of step u-1;
+//   C. eat of step u from the kept (delta, x, y) of step u and the warps'
+//      barycentre partials of step u.
 // After the last step the state is written back, a final barrier is taken
 // and the per-step partials are folded in a fixed order into the statistics
 // ring.  If any wait gives up, every block leaves without writing state, so
@@ -26,10 +28,18 @@
 
 #include "fsb_device.cuh"
 #include "fsb_internal.h"
+#include "fsb_onchip.cuh"
 #include "fsb_reduce.cuh"
 
 namespace fsb {
 namespace {
+
+constexpr int kResThreads = 512;  // largest block
+// shared memory per fish: x and y (two buffers), feeding input (two
+// buffers), currentObjective and weight, binary32 each
+constexpr size_t kResSmemPerFish = 8 * sizeof(float);
+// largest slice a block holds (its arrays fill the opt-in shared memory)
+constexpr uint64_t kResMaxSlice = 7168;
 
 struct ResidentArgs {
   float* __restrict__ x;
@@ -66,133 +76,148 @@ __device__ __forceinline__ bool grid_wait(const ResidentArgs& a, unsigned k) {
                           &a.ctl->timeout_site, k, a.timeout_ns);
 }
 
-// The resident loop is software-pipelined so the barrier's latency hides
-// behind arithmetic: while the grid agrees on M_u, every block already swims
-// step u + 1 (positions do not depend on weights).  Eating step u then needs
-// that step's delta and post-swim position, which wait in a double-buffered
-// shared-memory slab `pend[buffer][delta | x | y][fish slot][thread]`.
+template <typename Part>
+struct ResPart3 {
+  Part w, x, y;
+};
+
 // WSWIM: the weight-scaled swim (each fish's half-width is (w / w0) s with
 // its weight after the previous step's eat).  The swim of step u + 1 then
-// waits for the eat of step u, so it runs after it instead of beside the
-// barrier.
-template <int FPT, int MAXB, int ACC, bool WSWIM>
-__global__ void __launch_bounds__(MAXB, 1) resident_kernel(ResidentArgs a) {
+// waits for the eat of step u, so it runs fused with it, after the barrier.
+template <int ACC, bool WSWIM>
+__global__ void __launch_bounds__(kResThreads, 1) resident_kernel(ResidentArgs a) {
   using Acc = SumAcc<ACC>;
   using Sum = typename Acc::Sum;
   using Part = typename Acc::Part;
-  extern __shared__ float pend[];
-  __shared__ uint32_t s_max[32], s_ekey[32];
-  __shared__ Part s_w[32], s_x[32], s_y[32];
+  extern __shared__ float2 res_smem[];
+  __shared__ uint32_t s_bmax[2], s_bkey[2];  // the block's maxima of a step, by parity
+  __shared__ ResPart3<Part> s_wpart[2][32];  // the warps' barycentre partials, by parity
   __shared__ uint32_t s_M, s_E;
   __shared__ int s_abort;
 
-  const int B = blockDim.x;
-  const int nw = (B + 31) >> 5;
   const int tid = threadIdx.x;
+  const int nw = (blockDim.x + 31) >> 5;
   const int lane = tid & 31, warp = tid >> 5;
   const bool multi = gridDim.x > 1;
-  // a resident school holds at most ~2.5 million fish, so indices fit 32
-  // bits.  The thread owns fish pairs (one swim block moves a pair): slot k
-  // is fish lo + 2 (tid + (k / 2) B) + k % 2, and slots k < nk are in the
-  // school (the slice, hence lo, is even)
+  // a resident school holds at most ~1.1 million fish, so indices fit 32
+  // bits; the slice (hence lo) is even, so no swim pair straddles two blocks
   const uint32_t lo = static_cast<uint32_t>(blockIdx.x * a.slice);
   const uint32_t hi = static_cast<uint32_t>(lo + a.slice < a.n ? lo + a.slice : a.n);
-  auto fish = [&](int k) -> uint32_t {
-    return lo + 2u * (static_cast<uint32_t>(tid) + static_cast<uint32_t>(k >> 1) * B) +
-           static_cast<uint32_t>(k & 1);
+  const uint32_t nf = hi > lo ? hi - lo : 0u;
+  const uint32_t np = (nf + 1) / 2;
+  const uint32_t cap = static_cast<uint32_t>(a.slice / 2);  // pairs per array
+  float2* const X0 = res_smem;
+  float2* const X1 = res_smem + cap;
+  float2* const Y0 = res_smem + 2 * cap;
+  float2* const Y1 = res_smem + 3 * cap;
+  float2* const D0 = res_smem + 4 * cap;
+  float2* const D1 = res_smem + 5 * cap;
+  float2* const F = res_smem + 6 * cap;
+  float2* const W = res_smem + 7 * cap;
+  // buffer k holds the positions after (and the feeding input of) the steps
+  // of parity k
+  auto state = [&](uint32_t from, uint32_t to) -> PairState {
+    return PairState{from & 1u ? X1 : X0, from & 1u ? Y1 : Y0, from & 1u ? D1 : D0,
+                     to & 1u ? X1 : X0,   to & 1u ? Y1 : Y0,   to & 1u ? D1 : D0,
+                     F,                   W};
   };
-  int nk = 0;
-#pragma unroll
-  for (int k = 0; k < FPT; ++k)
-    if (fish(k) < hi) nk = k + 1;
-  auto P = [&](uint32_t buf, int q, int k) -> float& {
-    return pend[((buf * 3 + q) * FPT + k) * B + tid];
-  };
+  const Physics<float> ph = a.ph;
+  const uint32_t T = a.n_steps;
 
-  float x[FPT], y[FPT], w[FPT], f[FPT], pv[FPT];
+  for (uint32_t e = tid; e < np; e += blockDim.x) {
+    float xv[2] = {0.f, 0.f}, yv[2] = {0.f, 0.f}, wv[2] = {0.f, 0.f}, fv[2] = {0.f, 0.f};
 #pragma unroll
-  for (int k = 0; k < FPT; ++k) {
-    const uint32_t i = fish(k);
-    if (k < nk) {
-      x[k] = a.x[i];
-      y[k] = a.y[i];
-      w[k] = a.w[i];
-      f[k] = objective(x[k], y[k]);
-    } else {
-      x[k] = y[k] = w[k] = f[k] = 0.f;
-    }
-    pv[k] = f[k];
-  }
-  if (tid == 0) s_abort = 0;
-
-  // swim of step u for every fish of this thread; parks (delta, x, y) in
-  // pend[u & 1] and returns the thread's maxima
-  auto swim_all = [&](uint32_t u, uint32_t& mb, uint32_t& ek) {
-    const uint32_t t = static_cast<uint32_t>(a.base_step + u);
-    mb = 0;
-    ek = 0;
-    Words4 r{};
-#pragma unroll
-    for (int k = 0; k < FPT; ++k) {
-      if (k < nk) {
-        pv[k] = f[k];
-        if ((k & 1) == 0) r = pair_draw(a.key, a.school, fish(k) >> 1, t);
-        swim(x[k], y[k], r.v[2 * (k & 1)], r.v[2 * (k & 1) + 1],
-             WSWIM ? swim_width(a.ph, w[k]) : a.ph.step, a.ph);
-        f[k] = objective(x[k], y[k]);
-        const float d = __fsub_rn(f[k], pv[k]);
-        const uint32_t m = abs_bits(d);
-        const uint32_t e = order_key(__fsub_rn(pv[k], f[k]));
-        mb = m > mb ? m : mb;
-        ek = e > ek ? e : ek;
-        P(u & 1u, 0, k) = d;
-        P(u & 1u, 1, k) = x[k];
-        P(u & 1u, 2, k) = y[k];
+    for (int h = 0; h < 2; ++h) {
+      if (2 * e + h < nf) {
+        const uint32_t i = lo + 2 * e + h;
+        xv[h] = a.x[i];
+        yv[h] = a.y[i];
+        wv[h] = a.w[i];
+        fv[h] = objective(xv[h], yv[h]);
       }
     }
-  };
+    X0[e] = make_float2(xv[0], xv[1]);
+    Y0[e] = make_float2(yv[0], yv[1]);
+    W[e] = make_float2(wv[0], wv[1]);
+    F[e] = make_float2(fv[0], fv[1]);
+  }
+  if (tid == 0) {
+    s_abort = 0;
+    s_bmax[0] = s_bmax[1] = 0u;
+    s_bkey[0] = s_bkey[1] = 0u;
+  }
+  __syncthreads();
 
-  // thread 0: hand the block's maxima of step u to the grid (one atomicMax
-  // per slot, then the arrival at barrier u), or keep them for a lone block
-  auto publish = [&](uint32_t u, uint32_t m, uint32_t e) {
-    if (multi) {
-      atomicMax(&a.rctl->max_slot[u % 3], m);
-      atomicMax(&a.rctl->ekey_slot[u % 3], e);
-      const bool skip = static_cast<int>(blockIdx.x) == a.inject_cta && u - 1 == a.inject_step;
-      if (!skip) grid_arrive(a);
+  PassCtx c{a.key, a.school, lo / 2, 0u, 0.f};
+  // swim of step u from buffer (u - 1) & 1 into buffer u & 1 (fused with the
+  // eat of step u - 1 when EAT); the warps' maxima into s_bmax[u & 1]
+  auto swim_pass = [&](uint32_t u, bool eat_too, Acc& acc) {
+    uint32_t mb = 0, ek = 0;
+    c.t = static_cast<uint32_t>(a.base_step + u);
+    const PairState B = state(u - 1, u);
+    if (!eat_too) {
+      if (u == T)
+        block_pass<false, true, true, false>(B, np, nf, c, ph, acc, mb, ek);
+      else
+        block_pass<false, true, false, false>(B, np, nf, c, ph, acc, mb, ek);
     } else {
-      s_M = m;
-      s_E = e;
+      if (u == T)
+        block_pass<true, true, true, false>(B, np, nf, c, ph, acc, mb, ek);
+      else
+        block_pass<true, true, false, false>(B, np, nf, c, ph, acc, mb, ek);
+    }
+    mb = warp_max(mb);
+    ek = warp_max(ek);
+    if (lane == 0) {
+      atomicMax(&s_bmax[u & 1u], mb);
+      atomicMax(&s_bkey[u & 1u], ek);
+    }
+  };
+  // thread 0: hand the block's maxima of step u to the grid (one atomicMax
+  // per slot, then the arrival at barrier u); a lone block keeps them
+  auto publish = [&](uint32_t u) {
+    if (!multi) return;
+    atomicMax(&a.rctl->max_slot[u % 3], s_bmax[u & 1u]);
+    atomicMax(&a.rctl->ekey_slot[u % 3], s_bkey[u & 1u]);
+    s_bmax[u & 1u] = 0u;
+    s_bkey[u & 1u] = 0u;
+    const bool skip = static_cast<int>(blockIdx.x) == a.inject_cta && u - 1 == a.inject_step;
+    if (!skip) grid_arrive(a);
+  };
+  // warp 0: the block's barycentre partial of step u, raw, into a.sums
+  auto fold_sums = [&](uint32_t u) {
+    const ResPart3<Part>* wp = s_wpart[u & 1u];
+    Part w = lane < nw ? wp[lane].w : part_zero<Part>();
+    Part x = lane < nw ? wp[lane].x : part_zero<Part>();
+    Part y = lane < nw ? wp[lane].y : part_zero<Part>();
+    w = warp_merge(w);
+    x = warp_merge(x);
+    y = warp_merge(y);
+    if (lane == 0) {
+      double* p = a.sums + (static_cast<uint64_t>(u - 1) * gridDim.x + blockIdx.x) * 3;
+      p[0] = raw_sum(w);
+      p[1] = raw_sum(x);
+      p[2] = raw_sum(y);
     }
   };
 
   // ---- prologue: swim of step 1
   {
-    uint32_t mb, ek;
-    swim_all(1, mb, ek);
-    mb = warp_max(mb);
-    ek = warp_max(ek);
-    if (lane == 0) {
-      s_max[warp] = mb;
-      s_ekey[warp] = ek;
-    }
+    Acc unused;
+    swim_pass(1, false, unused);
     __syncthreads();
-    if (warp == 0) {
-      uint32_t m = lane < nw ? s_max[lane] : 0u;
-      uint32_t e = lane < nw ? s_ekey[lane] : 0u;
-      m = warp_max(m);
-      e = warp_max(e);
-      if (lane == 0) publish(1, m, e);
-    }
+    if (tid == 0) publish(1);
   }
 
-  for (uint32_t u = 1; u <= a.n_steps; ++u) {
-    const bool has_next = u < a.n_steps;
+  for (uint32_t u = 1; u <= T; ++u) {
+    const bool has_next = u < T;
     // ---- A: swim of step u + 1 while the grid settles M_u
-    uint32_t mb = 0, ek = 0;
-    if (!WSWIM && has_next) swim_all(u + 1, mb, ek);
-
-    // ---- B: M_u
+    if (!WSWIM && has_next) {
+      Acc unused;
+      swim_pass(u + 1, false, unused);
+    }
+    __syncthreads();
+    // ---- B: M_u; hand over the maxima of step u + 1
     if (tid == 0) {
       if (multi) {
         if (grid_wait(a, u)) {
@@ -204,99 +229,86 @@ __global__ void __launch_bounds__(MAXB, 1) resident_kernel(ResidentArgs a) {
             a.rctl->max_slot[(u + 2) % 3] = 0u;
             a.rctl->ekey_slot[(u + 2) % 3] = 0u;
           }
+          if (!WSWIM && has_next) publish(u + 1);
         } else {
           s_abort = 1;
         }
+      } else {
+        s_M = s_bmax[u & 1u];
+        s_E = s_bkey[u & 1u];
+        s_bmax[u & 1u] = 0u;
+        s_bkey[u & 1u] = 0u;
       }
       if (blockIdx.x == 0 && !s_abort) {
         a.ring[u - 1].max_abs_delta = static_cast<double>(__uint_as_float(s_M));
         a.ring[u - 1].eat_max_diff = static_cast<double>(key_to_value(s_E, 0.f));
       }
     }
+    if (warp == 0 && u > 1) fold_sums(u - 1);
     __syncthreads();
     if (s_abort) return;
-    // feeding normaliser: M_u, or the paper's eat() value E_u (then the
-    // numerator is prev - cur = -delta, exactly, and a zero delta gives the
-    // same weight either sign)
-    const float M = a.ph.feed_mode ? key_to_value(s_E, 0.f) : __uint_as_float(s_M);
+    // feeding normaliser: M_u, or the paper's eat() value E_u
+    c.N = ph.feed_mode ? key_to_value(s_E, 0.f) : __uint_as_float(s_M);
 
-    // ---- C: eat of step u and its barycentre partials
+    // ---- C: eat of step u (fused with the swim of step u + 1 for WSWIM)
     Acc acc;
-#pragma unroll
-    for (int k = 0; k < FPT; ++k) {
-      if (k < nk) {
-        if (M > 0.f) {
-          const float d = P(u & 1u, 0, k);
-          w[k] = eat(w[k], a.ph.feed_mode ? -d : d, M, a.ph);
-        }
-        acc.add(w[k], P(u & 1u, 1, k), P(u & 1u, 2, k));
-      }
+    if (WSWIM && has_next) {
+      swim_pass(u + 1, true, acc);
+    } else {
+      uint32_t mb = 0, ek = 0;
+      const PairState B = state(u, u);
+      if (u == T)
+        block_pass<true, false, false, true>(B, np, nf, c, ph, acc, mb, ek);
+      else
+        block_pass<true, false, false, false>(B, np, nf, c, ph, acc, mb, ek);
     }
-    // ---- A (weight-scaled swim): swim of step u + 1 with the eaten weights
-    if (WSWIM && has_next) swim_all(u + 1, mb, ek);
-
-    // ---- D: one block reduction for M_{u+1}, E_{u+1} and the sums of u
-    mb = warp_max(mb);
-    ek = warp_max(ek);
-    Part sw = warp_tree(acc.pw()), sx = warp_tree(acc.px()), sy = warp_tree(acc.py());
-    if (lane == 0) {
-      s_max[warp] = mb;
-      s_ekey[warp] = ek;
-      s_w[warp] = sw;
-      s_x[warp] = sx;
-      s_y[warp] = sy;
-    }
-    __syncthreads();
-    if (warp == 0) {
-      uint32_t m = lane < nw ? s_max[lane] : 0u;
-      uint32_t e = lane < nw ? s_ekey[lane] : 0u;
-      sw = lane < nw ? s_w[lane] : part_zero<Part>();
-      sx = lane < nw ? s_x[lane] : part_zero<Part>();
-      sy = lane < nw ? s_y[lane] : part_zero<Part>();
-      m = warp_max(m);
-      e = warp_max(e);
-      sw = warp_merge(sw);
-      sx = warp_merge(sx);
-      sy = warp_merge(sy);
-      if (lane == 0) {
-        double* p = a.sums + (static_cast<uint64_t>(u - 1) * gridDim.x + blockIdx.x) * 3;
-        p[0] = to_double(sw);
-        p[1] = to_double(sx);
-        p[2] = to_double(sy);
-        if (has_next)
-          publish(u + 1, m, e);
-        else if (multi)
-          grid_arrive(a);  // final barrier: every block's partials are out
-      }
-    }
-    // the next iteration's first __syncthreads orders reuse of the arrays
-  }
-
-  // ---- write the state back
-#pragma unroll
-  for (int k = 0; k < FPT; ++k) {
-    const uint32_t i = fish(k);
-    if (k < nk) {
-      a.x[i] = x[k];
-      a.y[i] = y[k];
-      a.w[i] = w[k];
-      a.pv[i] = pv[k];
+    ResPart3<Part> wp;
+    wp.w = warp_tree(acc.pw());
+    wp.x = warp_tree(acc.px());
+    wp.y = warp_tree(acc.py());
+    if (lane == 0) s_wpart[u & 1u][warp] = wp;
+    if (WSWIM && has_next) {
+      __syncthreads();
+      if (tid == 0) publish(u + 1);
     }
   }
 
-  // ---- final barrier, then fold the barycentre partials step by step
+  // ---- the last step's partial, then write the state back
   __syncthreads();
-  if (tid == 0 && multi && !grid_wait(a, a.n_steps + 1)) s_abort = 1;
+  if (warp == 0 && T > 0) fold_sums(T);
+  for (uint32_t e = tid; e < np; e += blockDim.x) {
+    const float2 xv = (T & 1u ? X1 : X0)[e], yv = (T & 1u ? Y1 : Y0)[e], wv = W[e];
+    const float2 pv = T ? (T & 1u ? D1 : D0)[e] : F[e];
+    const uint32_t i = lo + 2 * e;
+    a.x[i] = xv.x;
+    a.y[i] = yv.x;
+    a.w[i] = wv.x;
+    a.pv[i] = pv.x;
+    if (2 * e + 1 < nf) {
+      a.x[i + 1] = xv.y;
+      a.y[i + 1] = yv.y;
+      a.w[i + 1] = wv.y;
+      a.pv[i + 1] = pv.y;
+    }
+  }
+
+  // ---- final barrier (every block's partials are out), then fold the
+  // barycentre partials step by step
+  __syncthreads();
+  if (tid == 0 && multi) {
+    grid_arrive(a);
+    if (!grid_wait(a, T + 1)) s_abort = 1;
+  }
   __syncthreads();
   if (s_abort) return;
   __shared__ Sum f_w[32], f_x[32], f_y[32];
-  for (uint32_t s = blockIdx.x; s < a.n_steps; s += gridDim.x) {
+  for (uint32_t s = blockIdx.x; s < T; s += gridDim.x) {
     Sum fw = Sum(0), fx = Sum(0), fy = Sum(0);
-    for (uint32_t b = tid; b < gridDim.x; b += B) {
+    for (uint32_t b = tid; b < gridDim.x; b += blockDim.x) {
       const double* p = a.sums + (static_cast<uint64_t>(s) * gridDim.x + b) * 3;
-      fw = sum2(fw, Sum(__ldcg(p + 0)));
-      fx = sum2(fx, Sum(__ldcg(p + 1)));
-      fy = sum2(fy, Sum(__ldcg(p + 2)));
+      fw = sum2(fw, raw_to_sum<ACC>(__ldcg(p + 0)));
+      fx = sum2(fx, raw_to_sum<ACC>(__ldcg(p + 1)));
+      fy = sum2(fy, raw_to_sum<ACC>(__ldcg(p + 2)));
     }
     fw = warp_sum(fw);
     fx = warp_sum(fx);
@@ -324,88 +336,58 @@ __global__ void __launch_bounds__(MAXB, 1) resident_kernel(ResidentArgs a) {
   }
 }
 
-// Largest block each fish-per-thread variant is compiled for (registers:
-// five per fish plus the Philox and reduction temporaries).
-template <int FPT>
-struct MaxBlock;
-template <>
-struct MaxBlock<4> {
-  static constexpr int value = 1024;
-};
-template <>
-struct MaxBlock<8> {
-  static constexpr int value = 896;
-};
-template <>
-struct MaxBlock<12> {
-  static constexpr int value = 640;
-};
-template <>
-struct MaxBlock<16> {
-  static constexpr int value = 512;
-};
-
-template <int FPT, int ACC>
+template <int ACC>
 const void* kernel_ptr(bool wswim) {
-  constexpr int MB = MaxBlock<FPT>::value;
-  if (wswim) return reinterpret_cast<const void*>(&resident_kernel<FPT, MB, ACC, true>);
-  return reinterpret_cast<const void*>(&resident_kernel<FPT, MB, ACC, false>);
+  if (wswim) return reinterpret_cast<const void*>(&resident_kernel<ACC, true>);
+  return reinterpret_cast<const void*>(&resident_kernel<ACC, false>);
 }
 
-template <int FPT>
-const void* pick_acc(int acc, bool wswim) {
+const void* pick(int acc, bool wswim) {
   switch (acc) {
-    case kAccPlain32: return kernel_ptr<FPT, kAccPlain32>(wswim);
-    case kAccKahan32: return kernel_ptr<FPT, kAccKahan32>(wswim);
-    case kAccF64: return kernel_ptr<FPT, kAccF64>(wswim);
-    default: return nullptr;
-  }
-}
-
-const void* pick(int fpt, int acc, bool wswim) {
-  switch (fpt) {
-    case 4: return pick_acc<4>(acc, wswim);
-    case 8: return pick_acc<8>(acc, wswim);
-    case 12: return pick_acc<12>(acc, wswim);
-    case 16: return pick_acc<16>(acc, wswim);
+    case kAccPlain32: return kernel_ptr<kAccPlain32>(wswim);
+    case kAccKahan32: return kernel_ptr<kAccKahan32>(wswim);
+    case kAccF64: return kernel_ptr<kAccF64>(wswim);
     default: return nullptr;
   }
 }
 
 }  // namespace
 
+// Largest block for `fpt` fish per thread: at most kResThreads threads, and
+// fpt times the block within the largest slice.
 int resident_max_block(int fpt) {
-  switch (fpt) {
-    case 4: return MaxBlock<4>::value;
-    case 8: return MaxBlock<8>::value;
-    case 12: return MaxBlock<12>::value;
-    case 16: return MaxBlock<16>::value;
-    default: return 0;
-  }
+  if (fpt != 4 && fpt != 8 && fpt != 12 && fpt != 16) return 0;
+  const int by_smem = static_cast<int>(kResMaxSlice / fpt) / 32 * 32;
+  return by_smem < kResThreads ? by_smem : kResThreads;
 }
 
-size_t resident_smem_bytes(int fpt, int block) {
-  return static_cast<size_t>(2) * 3 * fpt * block * sizeof(float);
-}
+size_t resident_smem_bytes(uint64_t slice) { return kResSmemPerFish * slice; }
 
 int resident_blocks_per_sm(int fpt, int acc, int block, int swim_mode) {
-  const void* fn = pick(fpt, acc, swim_mode != 0);
-  if (!fn) return 0;
-  const size_t smem = resident_smem_bytes(fpt, block);
+  const void* fn = pick(acc, swim_mode != 0);
+  if (!fn || block < 32 || block > resident_max_block(fpt)) return 0;
   // the attribute is per kernel, shared by every handle: always the largest
-  // slab this variant can ask for, so no handle lowers it under another
-  const size_t most = resident_smem_bytes(fpt, resident_max_block(fpt));
+  // slice, so no handle lowers it under another
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(most)) != cudaSuccess)
+                           static_cast<int>(resident_smem_bytes(kResMaxSlice))) != cudaSuccess) {
+    cudaGetLastError();
     return 0;
+  }
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block, smem) != cudaSuccess) return 0;
+  const size_t smem = resident_smem_bytes(static_cast<uint64_t>(fpt) * block);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
   return nb;
 }
 
 cudaError_t launch_resident(const ResidentLaunch& L, cudaStream_t s) {
-  const void* fn = pick(L.fpt, L.acc, L.swim_mode != 0);
-  if (!fn || L.grid < 1 || L.block < 32 || L.block > resident_max_block(L.fpt))
+  const void* fn = pick(L.acc, L.swim_mode != 0);
+  if (!fn || L.grid < 1 || L.block < 32 || L.block > resident_max_block(L.fpt) ||
+      L.slice < 2 || L.slice % 2 || L.slice > kResMaxSlice ||
+      L.slice > static_cast<uint64_t>(L.fpt) * L.block ||
+      static_cast<uint64_t>(L.grid) * L.slice < L.n)
     return cudaErrorInvalidValue;
   ResidentArgs a;
   a.x = static_cast<float*>(L.x);
@@ -439,7 +421,7 @@ cudaError_t launch_resident(const ResidentLaunch& L, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(L.grid);
   cfg.blockDim = dim3(L.block);
-  cfg.dynamicSmemBytes = resident_smem_bytes(L.fpt, L.block);
+  cfg.dynamicSmemBytes = resident_smem_bytes(L.slice);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
