@@ -195,15 +195,15 @@ __device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int r
     uint32_t mb = 0, ek = 0;
     Acc acc;
     if (p == 0 && T > 1)
-      block_pass<false, true, false, false>(B, np, nf, c, ph, acc, mb, ek);
+      block_pass<false, true, false, false>(B, np, nf, c, ph, acc, mb, ek, kBatchThreads);
     else if (p == 0 && T == 1)
-      block_pass<false, true, true, false>(B, np, nf, c, ph, acc, mb, ek);
+      block_pass<false, true, true, false>(B, np, nf, c, ph, acc, mb, ek, kBatchThreads);
     else if (p + 1 < T)
-      block_pass<true, true, false, false>(B, np, nf, c, ph, acc, mb, ek);
+      block_pass<true, true, false, false>(B, np, nf, c, ph, acc, mb, ek, kBatchThreads);
     else if (p + 1 == T)
-      block_pass<true, true, true, false>(B, np, nf, c, ph, acc, mb, ek);
+      block_pass<true, true, true, false>(B, np, nf, c, ph, acc, mb, ek, kBatchThreads);
     else if (p == T)
-      block_pass<true, false, false, true>(B, np, nf, c, ph, acc, mb, ek);
+      block_pass<true, false, false, true>(B, np, nf, c, ph, acc, mb, ek, kBatchThreads);
     if (do_swim) {
       mb = warp_max(mb);
       ek = warp_max(ek);

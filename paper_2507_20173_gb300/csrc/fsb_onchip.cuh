@@ -89,13 +89,13 @@ __device__ __forceinline__ void pair_pass(const PairState& B, uint32_t e, bool t
 }
 
 // All of this thread's pairs in one pass: elements threadIdx.x,
-// threadIdx.x + blockDim.x, ... below np (nf fish), two per iteration so
+// threadIdx.x + step, ... below np (nf fish), where step is the number of
+// threads that share the pass (threads 0 .. step - 1), two per iteration so
 // that two independent draws overlap.
 template <bool EAT, bool SWIM, bool LAST_SWIM, bool LAST_EAT, typename Acc>
 __device__ __forceinline__ void block_pass(const PairState& B, uint32_t np, uint32_t nf,
                                            const PassCtx& c, const Physics<float>& ph, Acc& acc,
-                                           uint32_t& mb, uint32_t& ek) {
-  const uint32_t step = blockDim.x;
+                                           uint32_t& mb, uint32_t& ek, uint32_t step) {
   uint32_t e = threadIdx.x;
   for (; e + step < np; e += 2 * step) {
     pair_pass<EAT, SWIM, LAST_SWIM, LAST_EAT>(B, e, true, c, ph, acc, mb, ek);

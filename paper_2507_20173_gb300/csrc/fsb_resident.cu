@@ -34,7 +34,7 @@
 namespace fsb {
 namespace {
 
-constexpr int kResThreads = 512;  // largest block
+constexpr int kResThreads = 512;  // most fish threads per block (one more warp synchronises)
 // shared memory per fish: x and y (two buffers), feeding input (two
 // buffers), currentObjective and weight, binary32 each
 constexpr size_t kResSmemPerFish = 8 * sizeof(float);
@@ -81,23 +81,46 @@ struct ResPart3 {
   Part w, x, y;
 };
 
+// Named hardware barriers between the fish warps and the synchronisation
+// warp (id 0 is __syncthreads).  Each handover alternates between two ids by
+// step parity, so an arrival for step u + 2 can never join a phase of step u.
+__device__ __forceinline__ void named_arrive(int id, int threads) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+__device__ __forceinline__ void named_sync(int id, int threads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+constexpr int kBarM = 1;    // ids 1, 2: "M_u is in s_M[u & 1]" (sync warp -> fish warps)
+constexpr int kBarMax = 3;  // ids 3, 4: "the block's maxima of step u are in s_bmax[u & 1]
+                            //            and every warp's partials of step u - 2 are out"
+
+// The block is blockDim.x - 32 fish threads (warps 0 .. nw - 1) and one
+// synchronisation warp (the last).  The fish warps only swim, eat and meet
+// the synchronisation warp at the two named handovers per step; the
+// synchronisation warp does all the grid-wide work: it waits for barrier u,
+// reads M_u, hands the block's maxima of step u + 1 to the grid, arrives at
+// barrier u + 1 and folds the block's barycentre partials, while the fish
+// warps swim.
 // WSWIM: the weight-scaled swim (each fish's half-width is (w / w0) s with
 // its weight after the previous step's eat).  The swim of step u + 1 then
-// waits for the eat of step u, so it runs fused with it, after the barrier.
+// waits for the eat of step u, so it runs fused with it, after M_u.
 template <int ACC, bool WSWIM>
-__global__ void __launch_bounds__(kResThreads, 1) resident_kernel(ResidentArgs a) {
+__global__ void __launch_bounds__(kResThreads + 32, 1) resident_kernel(ResidentArgs a) {
   using Acc = SumAcc<ACC>;
   using Sum = typename Acc::Sum;
   using Part = typename Acc::Part;
   extern __shared__ float2 res_smem[];
   __shared__ uint32_t s_bmax[2], s_bkey[2];  // the block's maxima of a step, by parity
   __shared__ ResPart3<Part> s_wpart[2][32];  // the warps' barycentre partials, by parity
-  __shared__ uint32_t s_M, s_E;
+  __shared__ uint32_t s_M[2], s_E[2];        // M_u and E_u, by parity
   __shared__ int s_abort;
 
   const int tid = threadIdx.x;
-  const int nw = (blockDim.x + 31) >> 5;
+  const int nthreads = blockDim.x;             // fish threads + the sync warp
+  const int fish_threads = nthreads - 32;
+  const int nw = fish_threads >> 5;            // fish warps
   const int lane = tid & 31, warp = tid >> 5;
+  const bool sync_warp = warp == nw;
   const bool multi = gridDim.x > 1;
   // a resident school holds at most ~1.1 million fish, so indices fit 32
   // bits; the slice (hence lo) is even, so no swim pair straddles two blocks
@@ -123,8 +146,9 @@ __global__ void __launch_bounds__(kResThreads, 1) resident_kernel(ResidentArgs a
   };
   const Physics<float> ph = a.ph;
   const uint32_t T = a.n_steps;
+  if (T == 0) return;  // calls advance by at least one step
 
-  for (uint32_t e = tid; e < np; e += blockDim.x) {
+  for (uint32_t e = tid; e < np; e += nthreads) {
     float xv[2] = {0.f, 0.f}, yv[2] = {0.f, 0.f}, wv[2] = {0.f, 0.f}, fv[2] = {0.f, 0.f};
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -148,135 +172,168 @@ __global__ void __launch_bounds__(kResThreads, 1) resident_kernel(ResidentArgs a
   }
   __syncthreads();
 
-  PassCtx c{a.key, a.school, lo / 2, 0u, 0.f};
-  // swim of step u from buffer (u - 1) & 1 into buffer u & 1 (fused with the
-  // eat of step u - 1 when EAT); the warps' maxima into s_bmax[u & 1]
-  auto swim_pass = [&](uint32_t u, bool eat_too, Acc& acc) {
-    uint32_t mb = 0, ek = 0;
-    c.t = static_cast<uint32_t>(a.base_step + u);
-    const PairState B = state(u - 1, u);
-    if (!eat_too) {
-      if (u == T)
-        block_pass<false, true, true, false>(B, np, nf, c, ph, acc, mb, ek);
-      else
-        block_pass<false, true, false, false>(B, np, nf, c, ph, acc, mb, ek);
-    } else {
-      if (u == T)
-        block_pass<true, true, true, false>(B, np, nf, c, ph, acc, mb, ek);
-      else
-        block_pass<true, true, false, false>(B, np, nf, c, ph, acc, mb, ek);
-    }
-    mb = warp_max(mb);
-    ek = warp_max(ek);
-    if (lane == 0) {
-      atomicMax(&s_bmax[u & 1u], mb);
-      atomicMax(&s_bkey[u & 1u], ek);
-    }
-  };
-  // thread 0: hand the block's maxima of step u to the grid (one atomicMax
-  // per slot, then the arrival at barrier u); a lone block keeps them
-  auto publish = [&](uint32_t u) {
-    if (!multi) return;
-    atomicMax(&a.rctl->max_slot[u % 3], s_bmax[u & 1u]);
-    atomicMax(&a.rctl->ekey_slot[u % 3], s_bkey[u & 1u]);
-    s_bmax[u & 1u] = 0u;
-    s_bkey[u & 1u] = 0u;
-    const bool skip = static_cast<int>(blockIdx.x) == a.inject_cta && u - 1 == a.inject_step;
-    if (!skip) grid_arrive(a);
-  };
-  // warp 0: the block's barycentre partial of step u, raw, into a.sums
-  auto fold_sums = [&](uint32_t u) {
-    const ResPart3<Part>* wp = s_wpart[u & 1u];
-    Part w = lane < nw ? wp[lane].w : part_zero<Part>();
-    Part x = lane < nw ? wp[lane].x : part_zero<Part>();
-    Part y = lane < nw ? wp[lane].y : part_zero<Part>();
-    w = warp_merge(w);
-    x = warp_merge(x);
-    y = warp_merge(y);
-    if (lane == 0) {
-      double* p = a.sums + (static_cast<uint64_t>(u - 1) * gridDim.x + blockIdx.x) * 3;
-      p[0] = raw_sum(w);
-      p[1] = raw_sum(x);
-      p[2] = raw_sum(y);
-    }
-  };
-
-  // ---- prologue: swim of step 1
-  {
-    Acc unused;
-    swim_pass(1, false, unused);
-    __syncthreads();
-    if (tid == 0) publish(1);
-  }
-
-  for (uint32_t u = 1; u <= T; ++u) {
-    const bool has_next = u < T;
-    // ---- A: swim of step u + 1 while the grid settles M_u
-    if (!WSWIM && has_next) {
-      Acc unused;
-      swim_pass(u + 1, false, unused);
-    }
-    __syncthreads();
-    // ---- B: M_u; hand over the maxima of step u + 1
-    if (tid == 0) {
-      if (multi) {
-        if (grid_wait(a, u)) {
-          s_M = atomicAdd(&a.rctl->max_slot[u % 3], 0u);
-          s_E = atomicAdd(&a.rctl->ekey_slot[u % 3], 0u);
+  if (sync_warp) {
+    // ---- the synchronisation warp
+    // fold of the block's barycentre partial of step u, raw, into a.sums
+    auto fold_sums = [&](uint32_t u) {
+      const ResPart3<Part>* wp = s_wpart[u & 1u];
+      Part w = lane < nw ? wp[lane].w : part_zero<Part>();
+      Part x = lane < nw ? wp[lane].x : part_zero<Part>();
+      Part y = lane < nw ? wp[lane].y : part_zero<Part>();
+      w = warp_merge(w);
+      x = warp_merge(x);
+      y = warp_merge(y);
+      if (lane == 0) {
+        double* p = a.sums + (static_cast<uint64_t>(u - 1) * gridDim.x + blockIdx.x) * 3;
+        p[0] = raw_sum(w);
+        p[1] = raw_sum(x);
+        p[2] = raw_sum(y);
+      }
+    };
+    // the block's maxima of step u to the grid (one atomicMax per slot,
+    // then the arrival at barrier u); a lone block passes them on directly
+    auto publish = [&](uint32_t u) {
+      if (lane == 0 && multi) {
+        atomicMax(&a.rctl->max_slot[u % 3], s_bmax[u & 1u]);
+        atomicMax(&a.rctl->ekey_slot[u % 3], s_bkey[u & 1u]);
+        s_bmax[u & 1u] = 0u;
+        s_bkey[u & 1u] = 0u;
+        const bool skip = static_cast<int>(blockIdx.x) == a.inject_cta && u - 1 == a.inject_step;
+        if (!skip) grid_arrive(a);
+      }
+    };
+    named_sync(kBarMax + 1, nthreads);  // maxima of step 1
+    publish(1);
+    for (uint32_t u = 1; u <= T; ++u) {
+      if (lane == 0) {
+        bool ok = true;
+        uint32_t m, e;
+        if (multi) {
+          ok = grid_wait(a, u);
+          m = ld_relaxed_gpu(&a.rctl->max_slot[u % 3]);
+          e = ld_relaxed_gpu(&a.rctl->ekey_slot[u % 3]);
           // slot (u + 2) % 3 was last read before barrier u and is next
           // written after barrier u + 1
-          if (blockIdx.x == 0) {
+          if (ok && blockIdx.x == 0) {
             a.rctl->max_slot[(u + 2) % 3] = 0u;
             a.rctl->ekey_slot[(u + 2) % 3] = 0u;
           }
-          if (!WSWIM && has_next) publish(u + 1);
         } else {
-          s_abort = 1;
+          m = s_bmax[u & 1u];
+          e = s_bkey[u & 1u];
+          s_bmax[u & 1u] = 0u;
+          s_bkey[u & 1u] = 0u;
         }
-      } else {
-        s_M = s_bmax[u & 1u];
-        s_E = s_bkey[u & 1u];
-        s_bmax[u & 1u] = 0u;
-        s_bkey[u & 1u] = 0u;
+        if (!ok) s_abort = 1;
+        s_M[u & 1u] = m;
+        s_E[u & 1u] = e;
+        if (ok && blockIdx.x == 0) {
+          a.ring[u - 1].max_abs_delta = static_cast<double>(__uint_as_float(m));
+          a.ring[u - 1].eat_max_diff = static_cast<double>(key_to_value(e, 0.f));
+        }
       }
-      if (blockIdx.x == 0 && !s_abort) {
-        a.ring[u - 1].max_abs_delta = static_cast<double>(__uint_as_float(s_M));
-        a.ring[u - 1].eat_max_diff = static_cast<double>(key_to_value(s_E, 0.f));
+      __syncwarp();
+      named_arrive(kBarM + (u & 1u), nthreads);
+      if (s_abort) return;
+      if (u < T) {
+        // the fish warps' maxima of step u + 1 (and, with them, their
+        // partials of step u - 1)
+        named_sync(kBarMax + ((u + 1) & 1u), nthreads);
+        publish(u + 1);
+        if (u > 1) fold_sums(u - 1);
       }
     }
-    if (warp == 0 && u > 1) fold_sums(u - 1);
-    __syncthreads();
-    if (s_abort) return;
-    // feeding normaliser: M_u, or the paper's eat() value E_u
-    c.N = ph.feed_mode ? key_to_value(s_E, 0.f) : __uint_as_float(s_M);
-
-    // ---- C: eat of step u (fused with the swim of step u + 1 for WSWIM)
-    Acc acc;
-    if (WSWIM && has_next) {
-      swim_pass(u + 1, true, acc);
-    } else {
+  } else {
+    // ---- the fish warps
+    PassCtx c{a.key, a.school, lo / 2, 0u, 0.f};
+    // swim of step u from buffer (u - 1) & 1 into buffer u & 1 (fused with
+    // the eat of step u - 1 when eat_too); the warps' maxima into
+    // s_bmax[u & 1], then the handover to the synchronisation warp
+    auto swim_pass = [&](uint32_t u, bool eat_too, Acc& acc) {
       uint32_t mb = 0, ek = 0;
-      const PairState B = state(u, u);
-      if (u == T)
-        block_pass<true, false, false, true>(B, np, nf, c, ph, acc, mb, ek);
-      else
-        block_pass<true, false, false, false>(B, np, nf, c, ph, acc, mb, ek);
+      c.t = static_cast<uint32_t>(a.base_step + u);
+      const PairState B = state(u - 1, u);
+      if (!eat_too) {
+        if (u == T)
+          block_pass<false, true, true, false>(B, np, nf, c, ph, acc, mb, ek, fish_threads);
+        else
+          block_pass<false, true, false, false>(B, np, nf, c, ph, acc, mb, ek, fish_threads);
+      } else {
+        if (u == T)
+          block_pass<true, true, true, false>(B, np, nf, c, ph, acc, mb, ek, fish_threads);
+        else
+          block_pass<true, true, false, false>(B, np, nf, c, ph, acc, mb, ek, fish_threads);
+      }
+      mb = warp_max(mb);
+      ek = warp_max(ek);
+      if (lane == 0) {
+        atomicMax(&s_bmax[u & 1u], mb);
+        atomicMax(&s_bkey[u & 1u], ek);
+      }
+    };
+    auto put_partial = [&](uint32_t u, const Acc& acc) {
+      ResPart3<Part> wp;
+      wp.w = warp_tree(acc.pw());
+      wp.x = warp_tree(acc.px());
+      wp.y = warp_tree(acc.py());
+      if (lane == 0) s_wpart[u & 1u][warp] = wp;
+    };
+    {
+      Acc unused;
+      swim_pass(1, false, unused);
+      named_arrive(kBarMax + 1, nthreads);
     }
-    ResPart3<Part> wp;
-    wp.w = warp_tree(acc.pw());
-    wp.x = warp_tree(acc.px());
-    wp.y = warp_tree(acc.py());
-    if (lane == 0) s_wpart[u & 1u][warp] = wp;
-    if (WSWIM && has_next) {
-      __syncthreads();
-      if (tid == 0) publish(u + 1);
+    for (uint32_t u = 1; u <= T; ++u) {
+      const bool has_next = u < T;
+      // ---- A: swim of step u + 1 while the grid settles M_u
+      if (!WSWIM && has_next) {
+        Acc unused;
+        swim_pass(u + 1, false, unused);
+        named_arrive(kBarMax + ((u + 1) & 1u), nthreads);
+      }
+      // ---- B: M_u from the synchronisation warp
+      named_sync(kBarM + (u & 1u), nthreads);
+      if (s_abort) return;
+      c.N = ph.feed_mode ? key_to_value(s_E[u & 1u], 0.f) : __uint_as_float(s_M[u & 1u]);
+      // ---- C: eat of step u (fused with the swim of step u + 1 for WSWIM)
+      Acc acc;
+      if (WSWIM && has_next) {
+        swim_pass(u + 1, true, acc);
+        put_partial(u, acc);
+        named_arrive(kBarMax + ((u + 1) & 1u), nthreads);
+      } else {
+        uint32_t mb = 0, ek = 0;
+        const PairState B = state(u, u);
+        if (u == T)
+          block_pass<true, false, false, true>(B, np, nf, c, ph, acc, mb, ek, fish_threads);
+        else
+          block_pass<true, false, false, false>(B, np, nf, c, ph, acc, mb, ek, fish_threads);
+        put_partial(u, acc);
+      }
     }
   }
 
-  // ---- the last step's partial, then write the state back
+  // ---- the last partials, then write the state back
   __syncthreads();
-  if (warp == 0 && T > 0) fold_sums(T);
-  for (uint32_t e = tid; e < np; e += blockDim.x) {
+  if (sync_warp) {
+    // steps T - 1 (if not folded in the loop) and T
+    for (uint32_t u = T > 1 ? T - 1 : 1; u <= T; ++u) {
+      const ResPart3<Part>* wp = s_wpart[u & 1u];
+      Part w = lane < nw ? wp[lane].w : part_zero<Part>();
+      Part x = lane < nw ? wp[lane].x : part_zero<Part>();
+      Part y = lane < nw ? wp[lane].y : part_zero<Part>();
+      w = warp_merge(w);
+      x = warp_merge(x);
+      y = warp_merge(y);
+      if (lane == 0) {
+        double* p = a.sums + (static_cast<uint64_t>(u - 1) * gridDim.x + blockIdx.x) * 3;
+        p[0] = raw_sum(w);
+        p[1] = raw_sum(x);
+        p[2] = raw_sum(y);
+      }
+    }
+  }
+  for (uint32_t e = tid; e < np; e += nthreads) {
     const float2 xv = (T & 1u ? X1 : X0)[e], yv = (T & 1u ? Y1 : Y0)[e], wv = W[e];
     const float2 pv = T ? (T & 1u ? D1 : D0)[e] : F[e];
     const uint32_t i = lo + 2 * e;
@@ -295,16 +352,17 @@ __global__ void __launch_bounds__(kResThreads, 1) resident_kernel(ResidentArgs a
   // ---- final barrier (every block's partials are out), then fold the
   // barycentre partials step by step
   __syncthreads();
-  if (tid == 0 && multi) {
+  if (tid == nthreads - 32 && multi) {  // the lane that wrote the partials
     grid_arrive(a);
     if (!grid_wait(a, T + 1)) s_abort = 1;
   }
   __syncthreads();
   if (s_abort) return;
+  const int nw_all = nthreads >> 5;
   __shared__ Sum f_w[32], f_x[32], f_y[32];
   for (uint32_t s = blockIdx.x; s < T; s += gridDim.x) {
     Sum fw = Sum(0), fx = Sum(0), fy = Sum(0);
-    for (uint32_t b = tid; b < gridDim.x; b += blockDim.x) {
+    for (uint32_t b = tid; b < gridDim.x; b += nthreads) {
       const double* p = a.sums + (static_cast<uint64_t>(s) * gridDim.x + b) * 3;
       fw = sum2(fw, raw_to_sum<ACC>(__ldcg(p + 0)));
       fx = sum2(fx, raw_to_sum<ACC>(__ldcg(p + 1)));
@@ -321,9 +379,9 @@ __global__ void __launch_bounds__(kResThreads, 1) resident_kernel(ResidentArgs a
     }
     __syncthreads();
     if (warp == 0) {
-      fw = lane < nw ? f_w[lane] : Sum(0);
-      fx = lane < nw ? f_x[lane] : Sum(0);
-      fy = lane < nw ? f_y[lane] : Sum(0);
+      fw = lane < nw_all ? f_w[lane] : Sum(0);
+      fx = lane < nw_all ? f_x[lane] : Sum(0);
+      fy = lane < nw_all ? f_y[lane] : Sum(0);
       fw = warp_sum(fw);
       fx = warp_sum(fx);
       fy = warp_sum(fy);
@@ -375,7 +433,7 @@ int resident_blocks_per_sm(int fpt, int acc, int block, int swim_mode) {
   }
   int nb = 0;
   const size_t smem = resident_smem_bytes(static_cast<uint64_t>(fpt) * block);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block, smem) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block + 32, smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -420,7 +478,7 @@ cudaError_t launch_resident(const ResidentLaunch& L, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(L.grid);
-  cfg.blockDim = dim3(L.block);
+  cfg.blockDim = dim3(L.block + 32);  // the fish threads and the synchronisation warp
   cfg.dynamicSmemBytes = resident_smem_bytes(L.slice);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
