@@ -14,6 +14,73 @@
 
 namespace fsb {
 
+// ------------------------------------------------- raw per-step partials --
+// A partial in the bits of one binary64 word, unconverted: binary32 in the
+// low word; a compensated pair with hi in the low word and lo in the high
+// word; binary64 as is.  raw_to_sum completes one (binary64 arithmetic,
+// slow on this GPU) where its cost is off the per-step path.
+__device__ __forceinline__ double raw_sum(float v) {
+  return __longlong_as_double(static_cast<long long>(__float_as_uint(v)));
+}
+__device__ __forceinline__ double raw_sum(double v) { return v; }
+__device__ __forceinline__ double raw_sum(F2 v) {
+  return __longlong_as_double(static_cast<long long>(
+      (static_cast<unsigned long long>(__float_as_uint(v.lo)) << 32) | __float_as_uint(v.hi)));
+}
+__device__ __forceinline__ void raw_parts(double r, float& hi, float& lo) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(r));
+  hi = __uint_as_float(static_cast<uint32_t>(b));
+  lo = __uint_as_float(static_cast<uint32_t>(b >> 32));
+}
+
+// The value of a raw partial of accumulation mode ACC, in that mode's Sum
+// type (the compensated pair as hi + lo in binary64).
+template <int ACC>
+__device__ __forceinline__ typename SumAcc<ACC>::Sum raw_to_sum(double r);
+template <>
+__device__ __forceinline__ float raw_to_sum<kAccPlain32>(double r) {
+  float hi, lo;
+  raw_parts(r, hi, lo);
+  return hi;
+}
+template <>
+__device__ __forceinline__ double raw_to_sum<kAccKahan32>(double r) {
+  float hi, lo;
+  raw_parts(r, hi, lo);
+  return to_double(F2{hi, lo});
+}
+template <>
+__device__ __forceinline__ double raw_to_sum<kAccF64>(double r) { return r; }
+
+// ----------------------------------------------- barycentre terms of a pair --
+// The two fish of one swim pair into the accumulator: plain binary32 and
+// binary64 add them one by one; compensated binary32 forms the pair's
+// binary32 sums (one rounding each, exact when one weight is zero) and adds
+// each with one compensated step.
+__device__ __forceinline__ void add_pair(SumAcc<kAccPlain32>& acc, float w0, float x0, float y0,
+                                         float w1, float x1, float y1) {
+  acc.add(w0, x0, y0);
+  acc.add(w1, x1, y1);
+}
+__device__ __forceinline__ void add_pair(SumAcc<kAccF64>& acc, float w0, float x0, float y0,
+                                         float w1, float x1, float y1) {
+  acc.add(w0, x0, y0);
+  acc.add(w1, x1, y1);
+}
+__device__ __forceinline__ void add_pair(SumAcc<kAccKahan32>& acc, float w0, float x0, float y0,
+                                         float w1, float x1, float y1) {
+  using K = SumAcc<kAccKahan32>;
+  K::kadd(acc.sw, acc.cw, __fadd_rn(w0, w1));
+  K::kadd(acc.sx, acc.cx, __fadd_rn(__fmul_rn(w0, x0), __fmul_rn(w1, x1)));
+  K::kadd(acc.sy, acc.cy, __fadd_rn(__fmul_rn(w0, y0), __fmul_rn(w1, y1)));
+}
+
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 // A block's fish.  Positions and the feeding input are read from the source
 // arrays and written to the destination arrays (the same arrays for an
 // in-place pass; a double-buffered pass keeps step u's positions and input
@@ -64,7 +131,7 @@ __device__ __forceinline__ void pair_pass(const PairState& B, uint32_t e, bool t
       wv.x = eat(wv.x, g0, c.N, ph);
       wv.y = eat(wv.y, g1, c.N, ph);
     }
-    acc.add2(wv.x, xv.x, yv.x, two ? wv.y : 0.f, xv.y, yv.y);
+    add_pair(acc, wv.x, xv.x, yv.x, two ? wv.y : 0.f, xv.y, yv.y);
     B.W[e] = wv;
   }
   if (SWIM) {

@@ -71,24 +71,6 @@ __device__ __forceinline__ double to_double(double v) { return v; }
 __device__ __forceinline__ double to_double(F2 v) {
   return static_cast<double>(v.hi) + static_cast<double>(v.lo);
 }
-// A partial in the bits of one binary64 word, unconverted: binary32 in the
-// low word; a compensated pair with hi in the low word and lo in the high
-// word; binary64 as is.  raw_to_sum completes one (binary64 arithmetic) where
-// its cost is off the per-step path.
-__device__ __forceinline__ double raw_sum(float v) {
-  return __longlong_as_double(static_cast<long long>(__float_as_uint(v)));
-}
-__device__ __forceinline__ double raw_sum(double v) { return v; }
-__device__ __forceinline__ double raw_sum(F2 v) {
-  return __longlong_as_double(static_cast<long long>(
-      (static_cast<unsigned long long>(__float_as_uint(v.lo)) << 32) | __float_as_uint(v.hi)));
-}
-__device__ __forceinline__ void raw_parts(double r, float& hi, float& lo) {
-  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(r));
-  hi = __uint_as_float(static_cast<uint32_t>(b));
-  lo = __uint_as_float(static_cast<uint32_t>(b >> 32));
-}
-
 template <typename T>
 __device__ __forceinline__ T part_zero();
 template <>
@@ -116,11 +98,6 @@ struct SumAcc<kAccPlain32> {
                                        const float (&yi)[4]) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) add(wi[q], xi[q], yi[q]);
-  }
-  __device__ __forceinline__ void add2(float w0, float x0, float y0, float w1, float x1,
-                                       float y1) {
-    add(w0, x0, y0);
-    add(w1, x1, y1);
   }
   __device__ __forceinline__ float rw() const { return w; }
   __device__ __forceinline__ float rx() const { return x; }
@@ -160,14 +137,6 @@ struct SumAcc<kAccKahan32> {
     kadd(sx, cx, px);
     kadd(sy, cy, py);
   }
-  // Two fish (one swim pair): binary32 pair sums (one rounding each, exact
-  // when one weight is zero), then one compensated add per quantity.
-  __device__ __forceinline__ void add2(float w0, float x0, float y0, float w1, float x1,
-                                       float y1) {
-    kadd(sw, cw, __fadd_rn(w0, w1));
-    kadd(sx, cx, __fadd_rn(__fmul_rn(w0, x0), __fmul_rn(w1, x1)));
-    kadd(sy, cy, __fadd_rn(__fmul_rn(w0, y0), __fmul_rn(w1, y1)));
-  }
   __device__ __forceinline__ double rw() const { return double(sw) - double(cw); }
   __device__ __forceinline__ double rx() const { return double(sx) - double(cx); }
   __device__ __forceinline__ double ry() const { return double(sy) - double(cy); }
@@ -196,11 +165,6 @@ struct SumAcc<kAccF64> {
 #pragma unroll
     for (int q = 0; q < 4; ++q) add(wi[q], xi[q], yi[q]);
   }
-  __device__ __forceinline__ void add2(float w0, float x0, float y0, float w1, float x1,
-                                       float y1) {
-    add(w0, x0, y0);
-    add(w1, x1, y1);
-  }
   __device__ __forceinline__ double rw() const { return w; }
   __device__ __forceinline__ double rx() const { return x; }
   __device__ __forceinline__ double ry() const { return y; }
@@ -208,25 +172,6 @@ struct SumAcc<kAccF64> {
   __device__ __forceinline__ Part px() const { return x; }
   __device__ __forceinline__ Part py() const { return y; }
 };
-
-// The value of a raw partial of accumulation mode ACC, in that mode's Sum
-// type (the compensated pair as hi + lo in binary64).
-template <int ACC>
-__device__ __forceinline__ typename SumAcc<ACC>::Sum raw_to_sum(double r);
-template <>
-__device__ __forceinline__ float raw_to_sum<kAccPlain32>(double r) {
-  float hi, lo;
-  raw_parts(r, hi, lo);
-  return hi;
-}
-template <>
-__device__ __forceinline__ double raw_to_sum<kAccKahan32>(double r) {
-  float hi, lo;
-  raw_parts(r, hi, lo);
-  return to_double(F2{hi, lo});
-}
-template <>
-__device__ __forceinline__ double raw_to_sum<kAccF64>(double r) { return r; }
 
 __device__ __forceinline__ float sum2(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ double sum2(double a, double b) { return __dadd_rn(a, b); }
@@ -266,11 +211,6 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
 __device__ __forceinline__ int ld_relaxed_gpu(const int* p) {
   int v;
   asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ unsigned ld_relaxed_gpu(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
 

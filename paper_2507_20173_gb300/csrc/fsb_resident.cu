@@ -210,8 +210,8 @@ __global__ void __launch_bounds__(kResThreads + 32, 1) resident_kernel(ResidentA
         uint32_t m, e;
         if (multi) {
           ok = grid_wait(a, u);
-          m = ld_relaxed_gpu(&a.rctl->max_slot[u % 3]);
-          e = ld_relaxed_gpu(&a.rctl->ekey_slot[u % 3]);
+          m = ld_relaxed_u32(&a.rctl->max_slot[u % 3]);
+          e = ld_relaxed_u32(&a.rctl->ekey_slot[u % 3]);
           // slot (u + 2) % 3 was last read before barrier u and is next
           // written after barrier u + 1
           if (ok && blockIdx.x == 0) {
