@@ -187,11 +187,12 @@ __device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int r
 
   const uint32_t last = T + (nb > 1 ? 1u : 0u);  // a cluster's last fold needs one more barrier
   const uint64_t t0 = *a.base_step_ptr;
+  const float scaled = exact_scaled_width(ph.step);
   float N = 0.f;  // feeding normaliser of the pass's eat
   for (uint32_t p = 0; p <= last; ++p) {
     const bool do_eat = p >= 1 && p <= T;
     const bool do_swim = p < T;
-    PassCtx c{key, school, pair0, static_cast<uint32_t>(t0 + p + 1), N};
+    PassCtx c{key, school, pair0, static_cast<uint32_t>(t0 + p + 1), N, scaled};
     uint32_t mb = 0, ek = 0;
     Acc acc;
     if (p == 0 && T > 1)

@@ -55,30 +55,102 @@ __device__ __forceinline__ double raw_to_sum<kAccF64>(double r) { return r; }
 // ----------------------------------------------- barycentre terms of a pair --
 // The two fish of one swim pair into the accumulator: plain binary32 and
 // binary64 add them one by one; compensated binary32 forms the pair's
-// binary32 sums (one rounding each, exact when one weight is zero) and adds
-// each with one compensated step.
-__device__ __forceinline__ void add_pair(SumAcc<kAccPlain32>& acc, float w0, float x0, float y0,
-                                         float w1, float x1, float y1) {
-  acc.add(w0, x0, y0);
-  acc.add(w1, x1, y1);
+// binary32 sums (w0 + w1, w0 x0 + w1 x1, w0 y0 + w1 y1: one rounding each,
+// exact when one weight is zero) and adds each with one compensated step.
+__device__ __forceinline__ void acc_pair(SumAcc<kAccPlain32>& acc, float2 wv, float2 xv,
+                                         float2 yv) {
+  acc.add(wv.x, xv.x, yv.x);
+  acc.add(wv.y, xv.y, yv.y);
 }
-__device__ __forceinline__ void add_pair(SumAcc<kAccF64>& acc, float w0, float x0, float y0,
-                                         float w1, float x1, float y1) {
-  acc.add(w0, x0, y0);
-  acc.add(w1, x1, y1);
+__device__ __forceinline__ void acc_pair(SumAcc<kAccF64>& acc, float2 wv, float2 xv, float2 yv) {
+  acc.add(wv.x, xv.x, yv.x);
+  acc.add(wv.y, xv.y, yv.y);
 }
-__device__ __forceinline__ void add_pair(SumAcc<kAccKahan32>& acc, float w0, float x0, float y0,
-                                         float w1, float x1, float y1) {
+__device__ __forceinline__ void acc_pair(SumAcc<kAccKahan32>& acc, float2 wv, float2 xv,
+                                         float2 yv) {
   using K = SumAcc<kAccKahan32>;
-  K::kadd(acc.sw, acc.cw, __fadd_rn(w0, w1));
-  K::kadd(acc.sx, acc.cx, __fadd_rn(__fmul_rn(w0, x0), __fmul_rn(w1, x1)));
-  K::kadd(acc.sy, acc.cy, __fadd_rn(__fmul_rn(w0, y0), __fmul_rn(w1, y1)));
+  K::kadd(acc.sw, acc.cw, __fadd_rn(wv.x, wv.y));
+  K::kadd(acc.sx, acc.cx, __fadd_rn(__fmul_rn(wv.x, xv.x), __fmul_rn(wv.y, xv.y)));
+  K::kadd(acc.sy, acc.cy, __fadd_rn(__fmul_rn(wv.x, yv.x), __fmul_rn(wv.y, yv.y)));
 }
 
 __device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
   unsigned v;
   asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
+}
+
+// ------------------------------------------------ paired binary32 arithmetic --
+// One instruction for the same addition or subtraction on both fish of a
+// pair: each lane is rounded to nearest even on its own, subnormals kept,
+// exactly as the scalar __fadd_rn / __fsub_rn (the f32x2 forms of sm_100
+// and later).  Products stay scalar (__fmul_rn): a paired multiply may be
+// fused by the code generator with a dependent paired add into one fused
+// multiply-add, which rounds once, so it is never used.
+__device__ __forceinline__ float2 add_x2(float2 a, float2 b) {
+  float2 r;
+  asm("{\n\t.reg .b64 pa, pb, pr;\n\t"
+      "mov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+      "add.rn.f32x2 pr, pa, pb;\n\tmov.b64 {%0, %1}, pr;\n\t}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+__device__ __forceinline__ float2 sub_x2(float2 a, float2 b) {
+  float2 r;
+  asm("{\n\t.reg .b64 pa, pb, pr;\n\t"
+      "mov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+      "sub.rn.f32x2 pr, pa, pb;\n\tmov.b64 {%0, %1}, pr;\n\t}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+__device__ __forceinline__ float2 clamp_x2(float2 v, float lo, float hi) {
+  return make_float2(fminf(fmaxf(v.x, lo), hi), fminf(fmaxf(v.y, lo), hi));
+}
+
+// The swim (Sec. 2.1.2) of a fish pair: fish 0 moves by draw words 0 and 1,
+// fish 1 by words 2 and 3, each coordinate by (2u - 1) * width, clamped to
+// [-P, P] -- the per-fish swim() of fsb_device.cuh for two fish.
+// (2u - 1) * width is formed as v * (width * 2^-23) with the integer
+// v = (r >> 8) - 2^23, which equals the two-rounding form
+// (v * 2^-23) * width bit for bit whenever width * 2^-23 is exact: v * 2^-23
+// is exact, so both are one rounding of the same real product.  `scaled` is
+// that exact width * 2^-23 for the default swim (both fish share the width),
+// or 0 to use the two-rounding form with the per-fish widths `width`.
+__device__ __forceinline__ void swim_pair(float2& xv, float2& yv, const Words4& r, float scaled,
+                                          float2 width, float P) {
+  const float vx0 = __int2float_rn(static_cast<int>(r.v[0] >> 8) - (1 << 23));
+  const float vy0 = __int2float_rn(static_cast<int>(r.v[1] >> 8) - (1 << 23));
+  const float vx1 = __int2float_rn(static_cast<int>(r.v[2] >> 8) - (1 << 23));
+  const float vy1 = __int2float_rn(static_cast<int>(r.v[3] >> 8) - (1 << 23));
+  float2 dx, dy;
+  if (scaled != 0.f) {
+    dx = make_float2(__fmul_rn(vx0, scaled), __fmul_rn(vx1, scaled));
+    dy = make_float2(__fmul_rn(vy0, scaled), __fmul_rn(vy1, scaled));
+  } else {
+    dx = make_float2(__fmul_rn(__fmul_rn(vx0, 0x1p-23f), width.x),
+                     __fmul_rn(__fmul_rn(vx1, 0x1p-23f), width.y));
+    dy = make_float2(__fmul_rn(__fmul_rn(vy0, 0x1p-23f), width.x),
+                     __fmul_rn(__fmul_rn(vy1, 0x1p-23f), width.y));
+  }
+  xv = clamp_x2(add_x2(xv, dx), -P, P);
+  yv = clamp_x2(add_x2(yv, dy), -P, P);
+}
+
+// Objective (Sec. 2.1.1) of both fish of a pair: sqrt((x * x) + (y * y)).
+__device__ __forceinline__ float2 objective_pair(float2 xv, float2 yv) {
+  const float2 xx = make_float2(__fmul_rn(xv.x, xv.x), __fmul_rn(xv.y, xv.y));
+  const float2 yy = make_float2(__fmul_rn(yv.x, yv.x), __fmul_rn(yv.y, yv.y));
+  const float2 s = add_x2(xx, yy);
+  return make_float2(__fsqrt_rn(s.x), __fsqrt_rn(s.y));
+}
+
+// width * 2^-23 when exact (width = 0, or |width| >= 2^-103 so the product
+// is normal), else 0: the swim then keeps the two-rounding form.
+__device__ __forceinline__ float exact_scaled_width(float width) {
+  const float a = fabsf(width);
+  return (a >= 0x1p-103f) ? __fmul_rn(width, 0x1p-23f) : 0.f;
 }
 
 // A block's fish.  Positions and the feeding input are read from the source
@@ -107,6 +179,7 @@ struct PassCtx {
   uint32_t pair0;  // in-school pair index of element 0
   uint32_t t;      // step counter of the pass's swim
   float N;         // feeding normaliser of the pass's eat (no feeding if <= 0)
+  float scaled;    // exact s * 2^-23 for the default swim, else 0 (swim_pair)
 };
 
 // One fish pair of a pass: the eat of step p and its barycentre terms (EAT),
@@ -122,36 +195,34 @@ __device__ __forceinline__ void pair_pass(const PairState& B, uint32_t e, bool t
   float2 wv = (EAT || ph.swim_mode) ? B.W[e] : make_float2(0.f, 0.f);
   if (EAT) {
     const float2 dv = B.Ds[e];
-    float g0 = dv.x, g1 = dv.y;
-    if (LAST_EAT) {
-      g0 = ph.feed_mode ? __fsub_rn(dv.x, fv.x) : __fsub_rn(fv.x, dv.x);
-      g1 = ph.feed_mode ? __fsub_rn(dv.y, fv.y) : __fsub_rn(fv.y, dv.y);
-    }
+    float2 g = dv;
+    if (LAST_EAT) g = ph.feed_mode ? sub_x2(dv, fv) : sub_x2(fv, dv);
     if (c.N > 0.f) {
-      wv.x = eat(wv.x, g0, c.N, ph);
-      wv.y = eat(wv.y, g1, c.N, ph);
+      // w <- clamp(w + g / N, w_min, w_max), one rounding per operation
+      const float2 q = make_float2(__fdiv_rn(g.x, c.N), __fdiv_rn(g.y, c.N));
+      wv = clamp_x2(add_x2(wv, q), ph.w_min, ph.w_max);
     }
-    add_pair(acc, wv.x, xv.x, yv.x, two ? wv.y : 0.f, xv.y, yv.y);
+    if (!two) wv.y = 0.f;  // a half pair's absent fish carries no weight
+    acc_pair(acc, wv, xv, yv);
     B.W[e] = wv;
   }
   if (SWIM) {
     const Words4 r = pair_draw(c.key, c.school, c.pair0 + e, c.t);
-    const float o0 = fv.x, o1 = fv.y;
-    swim(xv.x, yv.x, r.v[0], r.v[1], swim_width(ph, wv.x), ph);
-    swim(xv.y, yv.y, r.v[2], r.v[3], swim_width(ph, wv.y), ph);
-    fv.x = objective(xv.x, yv.x);
-    fv.y = objective(xv.y, yv.y);
-    const float i0 = __fsub_rn(o0, fv.x), i1 = __fsub_rn(o1, fv.y);  // prev - cur
-    const float d0 = __fsub_rn(fv.x, o0), d1 = __fsub_rn(fv.y, o1);  // delta
-    const uint32_t m0 = abs_bits(d0), q0 = order_key(i0);
-    const uint32_t m1 = two ? abs_bits(d1) : 0u, q1 = two ? order_key(i1) : 0u;
+    const float2 o = fv;
+    const float2 width = ph.swim_mode ? make_float2(swim_width(ph, wv.x), swim_width(ph, wv.y))
+                                      : make_float2(ph.step, ph.step);
+    swim_pair(xv, yv, r, ph.swim_mode ? 0.f : c.scaled, width, ph.pond_half);
+    fv = objective_pair(xv, yv);
+    const float2 i = sub_x2(o, fv);  // prev - cur
+    const float2 d = sub_x2(fv, o);  // delta
+    const uint32_t m0 = abs_bits(d.x), q0 = order_key(i.x);
+    const uint32_t m1 = two ? abs_bits(d.y) : 0u, q1 = two ? order_key(i.y) : 0u;
     mb = max(mb, max(m0, m1));
     ek = max(ek, max(q0, q1));
     B.Xd[e] = xv;
     B.Yd[e] = yv;
     B.F[e] = fv;
-    B.Dd[e] = LAST_SWIM ? make_float2(o0, o1)
-                        : (ph.feed_mode ? make_float2(i0, i1) : make_float2(d0, d1));
+    B.Dd[e] = LAST_SWIM ? o : (ph.feed_mode ? i : d);
   }
 }
 

@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(kResThreads + 32, 1) resident_kernel(ResidentA
     }
   } else {
     // ---- the fish warps
-    PassCtx c{a.key, a.school, lo / 2, 0u, 0.f};
+    PassCtx c{a.key, a.school, lo / 2, 0u, 0.f, exact_scaled_width(ph.step)};
     // swim of step u from buffer (u - 1) & 1 into buffer u & 1 (fused with
     // the eat of step u - 1 when eat_too); the warps' maxima into
     // s_bmax[u & 1], then the handover to the synchronisation warp
