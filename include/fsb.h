@@ -354,9 +354,12 @@ int fsb_set_fault_injection(fsb_handle h, int block, uint32_t step, uint64_t tim
  *                        (kernel 3: consumer threads; the block has 32 more)
  *   stream_blocks_per_sm blocks per SM of the streaming grid (capped by
  *                        occupancy)
- *   resident_fpt         fish per thread of the resident kernel: 4, 8, 12, 16
- *   resident_block       threads per block of the resident kernel (multiple
- *                        of 32, at most the variant's compiled maximum)
+ *   resident_fpt         most fish per thread of the resident kernel: 4, 8,
+ *                        12, 16 (a block's slice is also bounded by its
+ *                        shared memory, 7168 fish)
+ *   resident_block       fish threads per block of the resident kernel
+ *                        (multiple of 32, at most 512; one synchronisation
+ *                        warp is added)
  *   stream_stages        bulk-copy kernels: shared-memory tiles in flight per
  *                        block, 2, 3 or 4 (kernel 3: 2 or 3)
  * A combination that cannot run returns FSB_ERR_INVALID_ARG and leaves the

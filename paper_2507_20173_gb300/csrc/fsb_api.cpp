@@ -374,12 +374,11 @@ bool resident_config(int sms, int acc, int swim_mode, uint64_t n, fsb::ResidentL
   const int fpts[] = {4, 8, 12, 16};
   for (int fpt : fpts) {
     if (want_fpt && fpt != want_fpt) continue;
-    int maxb = fsb::resident_max_block(fpt);
-    if (want_block) {
-      if (want_block % 32 || want_block > maxb) return false;
-      maxb = want_block;
-    }
-    const uint64_t per_block = static_cast<uint64_t>(maxb) * fpt;
+    const int maxb = fsb::resident_max_block(fpt);
+    if (want_block && (want_block % 32 || want_block > maxb)) return false;
+    // a block holds at most fpt fish per thread of its largest block (or of
+    // the requested one), within the shared memory
+    const uint64_t per_block = fsb::resident_max_slice(fpt, want_block ? want_block : maxb);
     uint64_t grid = (n + per_block - 1) / per_block;
     if (grid > static_cast<uint64_t>(sms)) continue;
     if (grid < 1) grid = 1;
@@ -390,9 +389,11 @@ bool resident_config(int sms, int acc, int swim_mode, uint64_t n, fsb::ResidentL
     if (grid < most) grid = most;
     // even, so no fish pair (one swim block) straddles two blocks
     const uint64_t slice = ((n + grid - 1) / grid + 1) & ~1ull;
-    const uint64_t threads = (slice + fpt - 1) / fpt;
-    const int block = static_cast<int>(((threads + 31) / 32) * 32);
-    if (block > maxb) continue;
+    // the requested block, else the largest one with a pair for every thread
+    const uint64_t pairs32 = ((slice / 2 + 31) / 32) * 32;
+    const int block = want_block ? want_block
+                                 : static_cast<int>(pairs32 < static_cast<uint64_t>(maxb) ? pairs32 : maxb);
+    if (slice > fsb::resident_max_slice(fpt, block)) continue;
     if (fsb::resident_blocks_per_sm(fpt, acc, block, swim_mode) < 1) continue;
     R->fpt = fpt;
     R->block = block;

@@ -141,9 +141,10 @@ struct ResidentLaunch {
   int swim_mode;    // 1: weight-scaled swim (swims each step after the eat)
   int feed_mode;
   int acc;          // AccMode
-  int fpt;          // fish per thread a block can hold: 4, 8, 12 or 16
-  int block;        // threads per block (<= resident_max_block(fpt));
-                    // slice <= fpt * block
+  int fpt;          // at most this many fish per thread: 4, 8, 12 or 16
+  int block;        // fish threads per block (<= resident_max_block(fpt); one
+                    // synchronisation warp more is launched);
+                    // slice <= resident_max_slice(fpt, block)
   int grid;         // blocks, all co-resident (cooperative launch)
   uint64_t base_step;
   uint32_t n_steps;
@@ -158,6 +159,7 @@ struct ResidentLaunch {
 
 cudaError_t launch_resident(const ResidentLaunch& L, cudaStream_t s);
 int resident_max_block(int fpt);
+uint64_t resident_max_slice(int fpt, int block);
 int resident_blocks_per_sm(int fpt, int acc, int block, int swim_mode);
 size_t resident_smem_bytes(uint64_t slice);
 

@@ -411,12 +411,18 @@ const void* pick(int acc, bool wswim) {
 
 }  // namespace
 
-// Largest block for `fpt` fish per thread: at most kResThreads threads, and
-// fpt times the block within the largest slice.
+// Largest block (fish threads) for `fpt`: every variant runs up to
+// kResThreads fish threads.
 int resident_max_block(int fpt) {
   if (fpt != 4 && fpt != 8 && fpt != 12 && fpt != 16) return 0;
-  const int by_smem = static_cast<int>(kResMaxSlice / fpt) / 32 * 32;
-  return by_smem < kResThreads ? by_smem : kResThreads;
+  return kResThreads;
+}
+
+// Largest slice of a block of `block` fish threads holding at most `fpt`
+// fish per thread, within the shared memory.
+uint64_t resident_max_slice(int fpt, int block) {
+  const uint64_t by_threads = static_cast<uint64_t>(fpt) * block;
+  return by_threads < kResMaxSlice ? by_threads : kResMaxSlice;
 }
 
 size_t resident_smem_bytes(uint64_t slice) { return kResSmemPerFish * slice; }
@@ -432,7 +438,7 @@ int resident_blocks_per_sm(int fpt, int acc, int block, int swim_mode) {
     return 0;
   }
   int nb = 0;
-  const size_t smem = resident_smem_bytes(static_cast<uint64_t>(fpt) * block);
+  const size_t smem = resident_smem_bytes(resident_max_slice(fpt, block));
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block + 32, smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -442,9 +448,8 @@ int resident_blocks_per_sm(int fpt, int acc, int block, int swim_mode) {
 
 cudaError_t launch_resident(const ResidentLaunch& L, cudaStream_t s) {
   const void* fn = pick(L.acc, L.swim_mode != 0);
-  if (!fn || L.grid < 1 || L.block < 32 || L.block > resident_max_block(L.fpt) ||
-      L.slice < 2 || L.slice % 2 || L.slice > kResMaxSlice ||
-      L.slice > static_cast<uint64_t>(L.fpt) * L.block ||
+  if (!fn || L.grid < 1 || L.block < 32 || L.block % 32 || L.block > resident_max_block(L.fpt) ||
+      L.slice < 2 || L.slice % 2 || L.slice > resident_max_slice(L.fpt, L.block) ||
       static_cast<uint64_t>(L.grid) * L.slice < L.n)
     return cudaErrorInvalidValue;
   ResidentArgs a;
