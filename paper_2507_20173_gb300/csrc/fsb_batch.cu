@@ -268,7 +268,7 @@ __device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int r
 
   for (uint32_t e = tid; e < np; e += kBatchThreads) {
     const float2 xv = B.Xs[e], yv = B.Ys[e], wv = B.W[e];
-    const float2 pv = T ? B.Ds[e] : B.F[e];
+    const float2 pv = T ? B.De[e] : B.F[e];
     const uint64_t g = s_lo + lo + 2 * e;
     a.x[g] = xv.x;
     a.y[g] = yv.x;
@@ -292,7 +292,8 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs a) {
   float2* const X = state_smem;
   float2* const Y = state_smem + kBlockPairs;
   float2* const D = state_smem + 4 * kBlockPairs;
-  const PairState B{X, Y, D, X, Y, D, state_smem + 3 * kBlockPairs, state_smem + 2 * kBlockPairs};
+  const PairState B = pair_state(X, Y, D, X, Y, D, state_smem + 3 * kBlockPairs,
+                                 state_smem + 2 * kBlockPairs);
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = static_cast<int>(cluster.block_rank());
   if (threadIdx.x < 3) {

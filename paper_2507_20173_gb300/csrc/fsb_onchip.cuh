@@ -153,24 +153,35 @@ __device__ __forceinline__ float exact_scaled_width(float width) {
   return (a >= 0x1p-103f) ? __fmul_rn(width, 0x1p-23f) : 0.f;
 }
 
-// A block's fish.  Positions and the feeding input are read from the source
-// arrays and written to the destination arrays (the same arrays for an
-// in-place pass; a double-buffered pass keeps step u's positions and input
-// for the eat of step u while the swim of step u + 1 writes the others).
-// D holds a step's feeding input (delta, or prev - cur when feeding follows
-// the paper's eat() value) -- except after the school's last swim, when it
-// holds that swim's starting objective (the state's prevObjective) and the
-// final eat forms the input from F and D.
+// A block's fish.  The eat of a pass reads positions Xe, Ye and the
+// feeding input De; the swim reads positions Xs, Ys and writes Xd, Yd and
+// the next feeding input Dd.  An in-place pass uses one set of arrays for
+// all; the resident kernel's pipelined pass eats step u from one buffer
+// while the swim of step u + 2 reads the other (step u + 1's positions) and
+// overwrites the first, pair by pair after its eat.  D holds a step's
+// feeding input (delta, or prev - cur when feeding follows the paper's
+// eat() value) -- except after the school's last swim, when it holds that
+// swim's starting objective (the state's prevObjective) and the final eat
+// forms the input from F and D.
 struct PairState {
+  const float2* Xe;
+  const float2* Ye;
+  const float2* De;
   const float2* Xs;
   const float2* Ys;
-  const float2* Ds;
   float2* Xd;
   float2* Yd;
   float2* Dd;
   float2* F;  // currentObjective
   float2* W;
 };
+
+// The same arrays for the eat and the swim (an in-place or one-buffer pass).
+__device__ __forceinline__ PairState pair_state(const float2* Xs, const float2* Ys,
+                                                const float2* Ds, float2* Xd, float2* Yd,
+                                                float2* Dd, float2* F, float2* W) {
+  return PairState{Xs, Ys, Ds, Xs, Ys, Xd, Yd, Dd, F, W};
+}
 
 // Per-pass context of one block.
 struct PassCtx {
@@ -187,14 +198,16 @@ struct PassCtx {
 // LAST_SWIM: D keeps the swim's starting objectives; LAST_EAT: the feeding
 // input comes from F and D.  `two`: the pair's second fish is in the school
 // (a half pair's second fish is computed but neither summed nor maximised).
-template <bool EAT, bool SWIM, bool LAST_SWIM, bool LAST_EAT, typename Acc>
+// AHEAD: the eat reads its own positions (Xe, Ye), else the swim's.
+template <bool EAT, bool SWIM, bool LAST_SWIM, bool LAST_EAT, bool AHEAD, typename Acc>
 __device__ __forceinline__ void pair_pass(const PairState& B, uint32_t e, bool two,
                                           const PassCtx& c, const Physics<float>& ph, Acc& acc,
                                           uint32_t& mb, uint32_t& ek) {
   float2 xv = B.Xs[e], yv = B.Ys[e], fv = B.F[e];
   float2 wv = (EAT || ph.swim_mode) ? B.W[e] : make_float2(0.f, 0.f);
   if (EAT) {
-    const float2 dv = B.Ds[e];
+    const float2 dv = B.De[e];
+    const float2 xe = AHEAD ? B.Xe[e] : xv, ye = AHEAD ? B.Ye[e] : yv;
     float2 g = dv;
     if (LAST_EAT) g = ph.feed_mode ? sub_x2(dv, fv) : sub_x2(fv, dv);
     if (c.N > 0.f) {
@@ -203,7 +216,7 @@ __device__ __forceinline__ void pair_pass(const PairState& B, uint32_t e, bool t
       wv = clamp_x2(add_x2(wv, q), ph.w_min, ph.w_max);
     }
     if (!two) wv.y = 0.f;  // a half pair's absent fish carries no weight
-    acc_pair(acc, wv, xv, yv);
+    acc_pair(acc, wv, xe, ye);
     B.W[e] = wv;
   }
   if (SWIM) {
@@ -230,17 +243,18 @@ __device__ __forceinline__ void pair_pass(const PairState& B, uint32_t e, bool t
 // threadIdx.x + step, ... below np (nf fish), where step is the number of
 // threads that share the pass (threads 0 .. step - 1), two per iteration so
 // that two independent draws overlap.
-template <bool EAT, bool SWIM, bool LAST_SWIM, bool LAST_EAT, typename Acc>
+template <bool EAT, bool SWIM, bool LAST_SWIM, bool LAST_EAT, bool AHEAD = false, typename Acc>
 __device__ __forceinline__ void block_pass(const PairState& B, uint32_t np, uint32_t nf,
                                            const PassCtx& c, const Physics<float>& ph, Acc& acc,
                                            uint32_t& mb, uint32_t& ek, uint32_t step) {
   uint32_t e = threadIdx.x;
   for (; e + step < np; e += 2 * step) {
-    pair_pass<EAT, SWIM, LAST_SWIM, LAST_EAT>(B, e, true, c, ph, acc, mb, ek);
+    pair_pass<EAT, SWIM, LAST_SWIM, LAST_EAT, AHEAD>(B, e, true, c, ph, acc, mb, ek);
     const uint32_t e2 = e + step;
-    pair_pass<EAT, SWIM, LAST_SWIM, LAST_EAT>(B, e2, 2 * e2 + 1 < nf, c, ph, acc, mb, ek);
+    pair_pass<EAT, SWIM, LAST_SWIM, LAST_EAT, AHEAD>(B, e2, 2 * e2 + 1 < nf, c, ph, acc, mb, ek);
   }
-  if (e < np) pair_pass<EAT, SWIM, LAST_SWIM, LAST_EAT>(B, e, 2 * e + 1 < nf, c, ph, acc, mb, ek);
+  if (e < np)
+    pair_pass<EAT, SWIM, LAST_SWIM, LAST_EAT, AHEAD>(B, e, 2 * e + 1 < nf, c, ph, acc, mb, ek);
 }
 
 }  // namespace fsb

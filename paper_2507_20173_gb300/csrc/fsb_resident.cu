@@ -6,20 +6,22 @@
 // it with the compact per-pair passes of fsb_onchip.cuh.  Each step follows
 // the paper's order (Sec. 2.1.2 swim, Sec. 2.1.1 objective, delta, the
 // Sec. 2.3.2 max reduction, feeding, barycentre), with the phases of
-// consecutive steps overlapped:
-//   A. swim + objective + delta of step u+1 for every fish (positions do not
-//      depend on weights) into the other half of double-buffered position
-//      and feeding-input arrays, while the grid is still agreeing on M_u; the
-//      warps' maxima of step u+1 meet in shared memory by atomics;
-//   B. thread 0 waits for barrier u (one arrival per block on a monotonic
-//      counter; the wait is bounded by a %globaltimer deadline and gives up
-//      with FSB_ERR_TIMEOUT, so a missing block can never hang the GPU),
-//      reads M_u and the eat() value max(prev - cur) from a rotating slot
-//      that every block fed with one atomicMax (exact, order-free), then at
-//      once hands the block's maxima of step u+1 to the grid and arrives at
-//      barrier u+1; warp 0 folds the block's barycentre partial of step u-1;
-//   C. eat of step u from the kept (delta, x, y) of step u and the warps'
-//      barycentre partials of step u.
+// consecutive steps overlapped.  Positions do not depend on weights, so the
+// swims run two steps ahead of the eats: one pass over a block's fish eats
+// step u (reading step u's positions and feeding input from one half of
+// double-buffered arrays) and swims step u + 2 (from step u + 1's positions
+// in the other half, written back over step u's pair by pair), and the
+// warps' maxima of step u + 2 meet in shared memory by atomics.  One
+// synchronisation warp per block does all the grid-wide work beside them:
+// it waits for barrier u (one arrival per block on a monotonic counter; the
+// wait is bounded by a %globaltimer deadline and gives up with
+// FSB_ERR_TIMEOUT, so a missing block can never hang the GPU), reads M_u and
+// the eat() value max(prev - cur) from a rotating slot that every block fed
+// with one atomicMax (exact, order-free), hands the block's maxima of step
+// u + 1 to the grid, arrives at barrier u + 1 and folds the block's
+// barycentre partials -- so M_{u+1} has a whole pass to cross the grid.
+// The weight-scaled swim (its width depends on the eaten weight) cannot run
+// ahead; its passes eat step u and swim step u + 1.
 // After the last step the state is written back, a final barrier is taken
 // and the per-step partials are folded in a fixed order into the statistics
 // ring.  If any wait gives up, every block leaves without writing state, so
@@ -140,9 +142,16 @@ __global__ void __launch_bounds__(kResThreads + 32, 1) resident_kernel(ResidentA
   // buffer k holds the positions after (and the feeding input of) the steps
   // of parity k
   auto state = [&](uint32_t from, uint32_t to) -> PairState {
-    return PairState{from & 1u ? X1 : X0, from & 1u ? Y1 : Y0, from & 1u ? D1 : D0,
-                     to & 1u ? X1 : X0,   to & 1u ? Y1 : Y0,   to & 1u ? D1 : D0,
-                     F,                   W};
+    return pair_state(from & 1u ? X1 : X0, from & 1u ? Y1 : Y0, from & 1u ? D1 : D0,
+                      to & 1u ? X1 : X0, to & 1u ? Y1 : Y0, to & 1u ? D1 : D0, F, W);
+  };
+  // the pipelined pass of step u: eat step u from buffer u & 1 while the
+  // swim of step u + 2 reads buffer (u + 1) & 1 and overwrites buffer u & 1
+  auto ahead_state = [&](uint32_t u) -> PairState {
+    float2* const Xu = u & 1u ? X1 : X0;
+    float2* const Yu = u & 1u ? Y1 : Y0;
+    float2* const Du = u & 1u ? D1 : D0;
+    return PairState{Xu, Yu, Du, u & 1u ? X0 : X1, u & 1u ? Y0 : Y1, Xu, Yu, Du, F, W};
   };
   const Physics<float> ph = a.ph;
   const uint32_t T = a.n_steps;
@@ -282,26 +291,44 @@ __global__ void __launch_bounds__(kResThreads + 32, 1) resident_kernel(ResidentA
       Acc unused;
       swim_pass(1, false, unused);
       named_arrive(kBarMax + 1, nthreads);
+      if (!WSWIM && T >= 2) {
+        swim_pass(2, false, unused);
+        named_arrive(kBarMax + 0, nthreads);
+      }
     }
     for (uint32_t u = 1; u <= T; ++u) {
-      const bool has_next = u < T;
-      // ---- A: swim of step u + 1 while the grid settles M_u
-      if (!WSWIM && has_next) {
-        Acc unused;
-        swim_pass(u + 1, false, unused);
-        named_arrive(kBarMax + ((u + 1) & 1u), nthreads);
-      }
-      // ---- B: M_u from the synchronisation warp
+      // ---- M_u from the synchronisation warp
       named_sync(kBarM + (u & 1u), nthreads);
       if (s_abort) return;
       c.N = ph.feed_mode ? key_to_value(s_E[u & 1u], 0.f) : __uint_as_float(s_M[u & 1u]);
-      // ---- C: eat of step u (fused with the swim of step u + 1 for WSWIM)
       Acc acc;
-      if (WSWIM && has_next) {
+      if (WSWIM && u < T) {
+        // eat of step u fused with the swim of step u + 1 (the swim needs
+        // the eaten weights)
         swim_pass(u + 1, true, acc);
         put_partial(u, acc);
         named_arrive(kBarMax + ((u + 1) & 1u), nthreads);
+      } else if (!WSWIM && u + 2 <= T) {
+        // eat of step u fused with the swim of step u + 2: positions do not
+        // depend on weights, so the swims run two steps ahead and M_{u+2}
+        // has a whole pass to cross the grid
+        uint32_t mb = 0, ek = 0;
+        c.t = static_cast<uint32_t>(a.base_step + u + 2);
+        const PairState B = ahead_state(u);
+        if (u + 2 == T)
+          block_pass<true, true, true, false, true>(B, np, nf, c, ph, acc, mb, ek, fish_threads);
+        else
+          block_pass<true, true, false, false, true>(B, np, nf, c, ph, acc, mb, ek, fish_threads);
+        mb = warp_max(mb);
+        ek = warp_max(ek);
+        if (lane == 0) {
+          atomicMax(&s_bmax[u & 1u], mb);  // step u + 2 has the parity of u
+          atomicMax(&s_bkey[u & 1u], ek);
+        }
+        put_partial(u, acc);
+        named_arrive(kBarMax + (u & 1u), nthreads);
       } else {
+        // eat of step u alone
         uint32_t mb = 0, ek = 0;
         const PairState B = state(u, u);
         if (u == T)
