@@ -70,8 +70,9 @@ struct Part3 {
   Part w, x, y;
 };
 
-constexpr int kBatchThreads = 512;
+constexpr int kBatchThreads = 512;                // fish threads
 constexpr int kBatchWarps = kBatchThreads / 32;
+constexpr int kBlockThreads = kBatchThreads + 32;  // and one helper warp
 constexpr int kBlockFish = 8192;              // fish one block holds
 constexpr int kBlockPairs = kBlockFish / 2;
 constexpr int kMaxCluster = 8;
@@ -127,22 +128,26 @@ __device__ __forceinline__ void put_sums(fsb_step_stats* st, Part w, Part x, Par
 // contain exactly nb blocks that all call this with the same school, and
 // rank 0's slots must be zero (they are again on return).
 //
-// Pass p = 0 .. T over the block's fish pairs: the eat of step p with
-// normaliser N_p and its barycentre terms (p >= 1), then the swim of step
-// p + 1 with its objective and maxima (p < T).  One barrier follows each
-// pass (a cluster barrier for nb > 1):
-//   before it: each warp's maxima of step p + 1 into rank 0's slots
+// Pass p = 0 .. T over the block's fish pairs (the fish warps): the eat of
+// step p with normaliser N_p and its barycentre terms (p >= 1), then the
+// swim of step p + 1 with its objective and maxima (p < T).  One barrier
+// follows each pass (a cluster barrier for nb > 1):
+//   before it: each fish warp's maxima of step p + 1 into rank 0's slots
 //              (atomics) and its barycentre partial of step p;
-//   after it:  rank 0 zeroes the slots of step p + 3; warp 0 folds the
-//              block's partial of step p (nb = 1: the step's sums; else into
-//              rank 0's block_part), rank 0 folds the blocks' partials of
-//              step p - 1, and every thread reads M_{p+1} and E_{p+1}.
+//   after it:  the fish warps read M_{p+1} and E_{p+1} and start the next
+//              pass, while the block's helper warp zeroes the slots of step
+//              p + 3 (rank 0), folds the block's partial of step p (nb = 1:
+//              the step's sums; else into rank 0's block_part), folds the
+//              blocks' partials of step p - 1 (rank 0) and writes the step's
+//              maxima -- work that would otherwise hold one fish warp back
+//              at every barrier.
 template <int ACC, bool VAR>
 __device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int rank, int nb,
                                            BatchShared<ACC>& S, const PairState& B) {
   using Acc = SumAcc<ACC>;
   using Part = typename Acc::Part;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool helper = warp == kBatchWarps;
   const uint64_t s_lo = a.offsets[k];
   // in-school fish indices fit 32 bits (schools hold at most C * 8192 fish)
   const uint32_t n = static_cast<uint32_t>(a.offsets[k + 1] - s_lo);
@@ -163,7 +168,7 @@ __device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int r
   const uint32_t T = a.n_steps;
 
   // load (or initialise) the slice; the second fish of a half pair is zero
-  for (uint32_t e = tid; e < np; e += kBatchThreads) {
+  for (uint32_t e = tid; e < np; e += kBlockThreads) {
     float xv[2] = {0.f, 0.f}, yv[2] = {0.f, 0.f}, wv[2] = {0.f, 0.f}, fv[2] = {0.f, 0.f};
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -192,43 +197,45 @@ __device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int r
   for (uint32_t p = 0; p <= last; ++p) {
     const bool do_eat = p >= 1 && p <= T;
     const bool do_swim = p < T;
-    PassCtx c{key, school, pair0, static_cast<uint32_t>(t0 + p + 1), N, scaled};
-    uint32_t mb = 0, ek = 0;
-    Acc acc;
-    if (p == 0 && T > 1)
-      block_pass<false, true, false, false>(B, np, nf, c, ph, acc, mb, ek, kBatchThreads);
-    else if (p == 0 && T == 1)
-      block_pass<false, true, true, false>(B, np, nf, c, ph, acc, mb, ek, kBatchThreads);
-    else if (p + 1 < T)
-      block_pass<true, true, false, false>(B, np, nf, c, ph, acc, mb, ek, kBatchThreads);
-    else if (p + 1 == T)
-      block_pass<true, true, true, false>(B, np, nf, c, ph, acc, mb, ek, kBatchThreads);
-    else if (p == T)
-      block_pass<true, false, false, true>(B, np, nf, c, ph, acc, mb, ek, kBatchThreads);
-    if (do_swim) {
-      mb = warp_max(mb);
-      ek = warp_max(ek);
-      if (lane == 0) {
-        atomicMax(&S0->slot_max[(p + 1) % 3], mb);
-        atomicMax(&S0->slot_ekey[(p + 1) % 3], ek);
+    if (!helper) {
+      PassCtx c{key, school, pair0, static_cast<uint32_t>(t0 + p + 1), N, scaled};
+      uint32_t mb = 0, ek = 0;
+      Acc acc;
+      if (p == 0 && T > 1)
+        block_pass<false, true, false, false>(B, np, nf, c, ph, acc, mb, ek, kBatchThreads);
+      else if (p == 0 && T == 1)
+        block_pass<false, true, true, false>(B, np, nf, c, ph, acc, mb, ek, kBatchThreads);
+      else if (p + 1 < T)
+        block_pass<true, true, false, false>(B, np, nf, c, ph, acc, mb, ek, kBatchThreads);
+      else if (p + 1 == T)
+        block_pass<true, true, true, false>(B, np, nf, c, ph, acc, mb, ek, kBatchThreads);
+      else if (p == T)
+        block_pass<true, false, false, true>(B, np, nf, c, ph, acc, mb, ek, kBatchThreads);
+      if (do_swim) {
+        mb = warp_max(mb);
+        ek = warp_max(ek);
+        if (lane == 0) {
+          atomicMax(&S0->slot_max[(p + 1) % 3], mb);
+          atomicMax(&S0->slot_ekey[(p + 1) % 3], ek);
+        }
       }
-    }
-    if (do_eat) {
-      Part3<Part> wp;
-      wp.w = warp_tree(acc.pw());
-      wp.x = warp_tree(acc.px());
-      wp.y = warp_tree(acc.py());
-      if (lane == 0) S.warp_part[p & 1][warp] = wp;
+      if (do_eat) {
+        Part3<Part> wp;
+        wp.w = warp_tree(acc.pw());
+        wp.x = warp_tree(acc.px());
+        wp.y = warp_tree(acc.py());
+        if (lane == 0) S.warp_part[p & 1][warp] = wp;
+      }
     }
     if (nb > 1)
       cluster.sync();
     else
       __syncthreads();
-    if (rank == 0 && tid == 0) {
-      S.slot_max[p % 3] = 0u;
-      S.slot_ekey[p % 3] = 0u;
-    }
-    if (warp == 0) {
+    if (helper) {
+      if (rank == 0 && lane == 0) {
+        S.slot_max[p % 3] = 0u;
+        S.slot_ekey[p % 3] = 0u;
+      }
       if (do_eat) {
         const Part3<Part> bp = fold_warps(S.warp_part[p & 1]);
         if (lane == 0) {
@@ -249,24 +256,21 @@ __device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int r
         }
         put_sums(st + (p - 2), fw, fx, fy);
       }
-    }
-    if (do_swim) {
-      const float M = __uint_as_float(S0->slot_max[(p + 1) % 3]);
-      const uint32_t E_key = S0->slot_ekey[(p + 1) % 3];
-      const float E = key_to_value(E_key, 0.f);
-      // feeding normaliser: M, or the paper's eat() value E
-      N = ph.feed_mode ? E : M;
-      if (rank == 0 && tid == 0) {
-        st[p].max_abs_delta = static_cast<double>(M);
-        st[p].eat_max_diff = static_cast<double>(E);
+      if (do_swim && rank == 0 && lane == 0) {
+        st[p].max_abs_delta = static_cast<double>(__uint_as_float(S.slot_max[(p + 1) % 3]));
+        st[p].eat_max_diff = static_cast<double>(key_to_value(S.slot_ekey[(p + 1) % 3], 0.f));
       }
+    } else if (do_swim) {
+      // feeding normaliser of the next pass: M, or the paper's eat() value E
+      N = ph.feed_mode ? key_to_value(S0->slot_ekey[(p + 1) % 3], 0.f)
+                       : __uint_as_float(S0->slot_max[(p + 1) % 3]);
     }
   }
   // rank 0 has read every block's partials, and its slots are zero, before
   // any block leaves for the next school
   if (nb > 1) cluster.sync();
 
-  for (uint32_t e = tid; e < np; e += kBatchThreads) {
+  for (uint32_t e = tid; e < np; e += kBlockThreads) {
     const float2 xv = B.Xs[e], yv = B.Ys[e], wv = B.W[e];
     const float2 pv = T ? B.De[e] : B.F[e];
     const uint64_t g = s_lo + lo + 2 * e;
@@ -285,7 +289,7 @@ __device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int r
 }
 
 template <int CLUSTER, int ACC, bool VAR>
-__global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(kBlockThreads, 1) batch_kernel(BatchArgs a) {
   __shared__ BatchShared<ACC> S;
   __shared__ uint32_t s_pick;
   extern __shared__ float2 state_smem[];
@@ -363,7 +367,7 @@ const void* pick(int cluster, int acc, bool var = false) {
 cudaLaunchConfig_t make_config(int cluster, int grid, cudaStream_t s, cudaLaunchAttribute* attr) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(kBatchThreads);
+  cfg.blockDim = dim3(kBlockThreads);
   cfg.dynamicSmemBytes = kStateSmem;
   cfg.stream = s;
   attr[0].id = cudaLaunchAttributeClusterDimension;
