@@ -54,7 +54,73 @@ struct CollArgs {
   fsb_step_stats* ring;
   CollRec* coll;
   uint32_t n_steps;
+  int vec2;            // every array aligned to 2 elements: pair loads
 };
+
+// One fish pair's state as loaded: fish 2p (and 2p + 1 when nf = 2).
+template <typename Real>
+struct PairIn {
+  Real x[2], y[2], w[2], pv[2];
+  int nf;
+};
+
+template <typename Real>
+struct Vec2;
+template <>
+struct Vec2<float> {
+  using type = float2;
+};
+template <>
+struct Vec2<double> {
+  using type = double2;
+};
+
+// Loads the fields a pass reads for pair p: one two-element vector per
+// field when the arrays allow it, else element by element.
+template <typename Real, int PASS>
+__device__ __forceinline__ PairIn<Real> load_pair(const CollArgs<Real>& a, uint64_t p) {
+  using V = typename Vec2<Real>::type;
+  PairIn<Real> d;
+  const uint64_t i0 = 2 * p;
+  d.nf = i0 + 1 < a.n ? 2 : 1;
+  const bool need_w = PASS == kCSwim0 || PASS == kCEat || a.ph.swim_mode != 0;
+  const bool need_pv = PASS == kCEat;
+  if (a.vec2 && d.nf == 2) {
+    const V xv = reinterpret_cast<const V*>(a.x)[p];
+    const V yv = reinterpret_cast<const V*>(a.y)[p];
+    d.x[0] = xv.x;
+    d.x[1] = xv.y;
+    d.y[0] = yv.x;
+    d.y[1] = yv.y;
+    if (need_w) {
+      const V wv = reinterpret_cast<const V*>(a.w)[p];
+      d.w[0] = wv.x;
+      d.w[1] = wv.y;
+    } else {
+      d.w[0] = d.w[1] = Real(0);
+    }
+    if (need_pv) {
+      const V pvv = reinterpret_cast<const V*>(a.pv)[p];
+      d.pv[0] = pvv.x;
+      d.pv[1] = pvv.y;
+    } else {
+      d.pv[0] = d.pv[1] = Real(0);
+    }
+    return d;
+  }
+#pragma unroll
+  for (int f = 0; f < 2; ++f) {
+    if (f < d.nf) {
+      d.x[f] = a.x[i0 + f];
+      d.y[f] = a.y[i0 + f];
+      d.w[f] = need_w ? a.w[i0 + f] : Real(0);
+      d.pv[f] = need_pv ? a.pv[i0 + f] : Real(0);
+    } else {
+      d.x[f] = d.y[f] = d.w[f] = d.pv[f] = Real(0);
+    }
+  }
+  return d;
+}
 
 // One term of an exact school sum: v * 2^k rounded to the nearest integer,
 // ties to even, without a 64-bit float-to-integer conversion (that runs on
@@ -206,21 +272,14 @@ __global__ void __launch_bounds__(kCollBlock, 4) coll_kernel(CollArgs<Real> a) {
   long long q[4] = {0, 0, 0, 0};
   const uint64_t n_pairs = (a.n + 1) / 2;
   const uint64_t stride = static_cast<uint64_t>(gridDim.x) * kCollBlock;
-  for (uint64_t p = static_cast<uint64_t>(blockIdx.x) * kCollBlock + threadIdx.x; p < n_pairs;
-       p += stride) {
+  // the work on one loaded pair (its stores included)
+  auto run_pair = [&](uint64_t p, PairIn<Real>& d) {
     const uint64_t i0 = 2 * p;
-    const int nf = i0 + 1 < a.n ? 2 : 1;
-    Real x[2], y[2], w[2], pv[2];
-#pragma unroll
-    for (int f = 0; f < 2; ++f) {
-      if (f < nf) {
-        x[f] = a.x[i0 + f];
-        y[f] = a.y[i0 + f];
-        const bool need_w = PASS == kCSwim0 || PASS == kCEat || a.ph.swim_mode != 0;
-        w[f] = need_w ? a.w[i0 + f] : Real(0);
-        pv[f] = PASS == kCEat ? a.pv[i0 + f] : Real(0);
-      }
-    }
+    const int nf = d.nf;
+    Real* x = d.x;
+    Real* y = d.y;
+    Real* w = d.w;
+    Real* pv = d.pv;
     if (PASS == kCSwim0) {
       const Words4 r = pair_draw(a.key, a.school, p, t_swim);
 #pragma unroll
@@ -228,11 +287,8 @@ __global__ void __launch_bounds__(kCollBlock, 4) coll_kernel(CollArgs<Real> a) {
         if (f < nf) {
           q[3] += grid_term(w[f], a.g_w);  // the school's weight before the first eat
           Real cur = objective(x[f], y[f]);
-          const Real before = cur;
+          pv[f] = cur;                     // prevObjective after this swim
           swim_fish(x[f], y[f], cur, w[f], r.v[2 * f], r.v[2 * f + 1], a, maxb, ekey, q);
-          a.x[i0 + f] = x[f];
-          a.y[i0 + f] = y[f];
-          a.pv[i0 + f] = before;
         }
       }
     } else if (PASS == kCEat) {
@@ -248,9 +304,6 @@ __global__ void __launch_bounds__(kCollBlock, 4) coll_kernel(CollArgs<Real> a) {
           q[0] += grid_term(w[f], a.g_w);
           q[1] += grid_term(A::mul(w[f], x[f]), a.g_w);
           q[2] += grid_term(A::mul(w[f], y[f]), a.g_w);
-          a.x[i0 + f] = x[f];
-          a.y[i0 + f] = y[f];
-          a.w[i0 + f] = w[f];
         }
       }
     } else {
@@ -280,22 +333,51 @@ __global__ void __launch_bounds__(kCollBlock, 4) coll_kernel(CollArgs<Real> a) {
         for (int f = 0; f < 2; ++f) {
           if (f < nf) {
             Real cur = objective(x[f], y[f]);
-            const Real before = cur;
+            pv[f] = cur;  // prevObjective after this swim
             swim_fish(x[f], y[f], cur, w[f], r.v[2 * f], r.v[2 * f + 1], a, maxb, ekey, q);
-            a.x[i0 + f] = x[f];
-            a.y[i0 + f] = y[f];
-            a.pv[i0 + f] = before;
-          }
-        }
-      } else {
-#pragma unroll
-        for (int f = 0; f < 2; ++f) {
-          if (f < nf) {
-            a.x[i0 + f] = x[f];
-            a.y[i0 + f] = y[f];
           }
         }
       }
+    }
+    // stores: positions always; the weights after an eat; prevObjective
+    // after a swim
+    const bool put_w = PASS == kCEat;
+    const bool put_pv = PASS == kCSwim0 || PASS == kCMove;
+    if (a.vec2 && nf == 2) {
+      using V = typename Vec2<Real>::type;
+      reinterpret_cast<V*>(a.x)[p] = V{x[0], x[1]};
+      reinterpret_cast<V*>(a.y)[p] = V{y[0], y[1]};
+      if (put_w) reinterpret_cast<V*>(a.w)[p] = V{w[0], w[1]};
+      if (put_pv) reinterpret_cast<V*>(a.pv)[p] = V{pv[0], pv[1]};
+    } else {
+#pragma unroll
+      for (int f = 0; f < 2; ++f) {
+        if (f < nf) {
+          a.x[i0 + f] = x[f];
+          a.y[i0 + f] = y[f];
+          if (put_w) a.w[i0 + f] = w[f];
+          if (put_pv) a.pv[i0 + f] = pv[f];
+        }
+      }
+    }
+  };
+  // binary32: two pairs per iteration, both loaded before either is worked
+  // on, so twice the bytes are in flight (binary64 state keeps one: its
+  // registers would spill)
+  const uint64_t first = static_cast<uint64_t>(blockIdx.x) * kCollBlock + threadIdx.x;
+  if (sizeof(Real) == 4) {
+    for (uint64_t p = first; p < n_pairs; p += 2 * stride) {
+      const uint64_t p2 = p + stride;
+      PairIn<Real> d1 = load_pair<Real, PASS>(a, p);
+      PairIn<Real> d2;
+      if (p2 < n_pairs) d2 = load_pair<Real, PASS>(a, p2);
+      run_pair(p, d1);
+      if (p2 < n_pairs) run_pair(p2, d2);
+    }
+  } else {
+    for (uint64_t p = first; p < n_pairs; p += stride) {
+      PairIn<Real> d = load_pair<Real, PASS>(a, p);
+      run_pair(p, d);
     }
   }
 
@@ -500,6 +582,11 @@ CollArgs<Real> make_args(const CollLaunch& L, uint32_t n_steps) {
   a.ring = L.ring;
   a.coll = L.coll;
   a.n_steps = n_steps;
+  const uintptr_t align = 2 * sizeof(Real);
+  a.vec2 = (reinterpret_cast<uintptr_t>(L.x) % align == 0 &&
+            reinterpret_cast<uintptr_t>(L.y) % align == 0 &&
+            reinterpret_cast<uintptr_t>(L.w) % align == 0 &&
+            reinterpret_cast<uintptr_t>(L.pv) % align == 0) ? 1 : 0;
   return a;
 }
 
