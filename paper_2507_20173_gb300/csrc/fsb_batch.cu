@@ -189,6 +189,7 @@ __device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int r
     B.W[e] = make_float2(wv[0], wv[1]);
     B.F[e] = make_float2(fv[0], fv[1]);
   }
+  __syncthreads();  // the passes take the pairs in another thread order
 
   const uint32_t last = T + (nb > 1 ? 1u : 0u);  // a cluster's last fold needs one more barrier
   const uint64_t t0 = *a.base_step_ptr;

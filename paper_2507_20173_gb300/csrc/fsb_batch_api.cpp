@@ -116,10 +116,10 @@ int plan_batch(fsb_batch* b, int forced) {
   const int slots = fsb::batch_max_clusters(1, L.acc);  // resident single blocks
   if (slots < 1) return bfail(FSB_ERR_UNSUPPORTED, "batch kernel cannot be resident");
   // Work of a queue: its fish times the relative cost per fish-step of its
-  // cluster width, measured on GB300 for each width alone (the per-step
-  // cluster barrier costs more across 8 blocks; single blocks carry the
-  // smallest schools, whose steps are latency-bound).
-  const double cost[fsb::kBatchQueues] = {1.15, 1.0, 1.0, 1.05};
+  // cluster width, measured on GB300 with the shared-memory kernel (single
+  // blocks carry the smallest schools, whose steps are latency-bound; a
+  // cluster of 2 holds schools filled from one half up).
+  const double cost[fsb::kBatchQueues] = {1.0, 0.95, 1.1, 1.2};
   double work[fsb::kBatchQueues], total = 0.0;
   for (int t = 0; t < fsb::kBatchQueues; ++t) {
     work[t] = cost[t] * static_cast<double>(fish[t]);
