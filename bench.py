@@ -677,7 +677,10 @@ def run_ours(args, world, rank, local, pg):
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cn, cs = min(n, 1 << 20), 20 if n >= (1 << 20) else wl.steps
+        # about 10 s of single-thread oracle work (~3.3e7 fish-steps/s on
+        # the machine's host core): up to 2^22 fish, as many steps as that takes
+        cn = min(n, 1 << 22)
+        cs = max(1, min(100_000, int(round(3.2e8 / cn))))
         rate, dt = cpu_oracle_rate(cn, wl.seed, cs, collective=coll)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "%d fish x %d steps of the %s school (same init rule), %.1f s"
