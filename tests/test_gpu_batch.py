@@ -225,3 +225,37 @@ def test_forced_cluster_size_and_back_to_the_default_plan():
     fsb.fsb_batch_step(b, 4, stats)
     fsb.fsb_batch_destroy(b)
     check_batch(tmpl, offsets, seeds, read_state(ts), stats, 4, tmpl.precision)
+
+
+def test_explicit_plans_give_the_same_trajectories():
+    """Explicit launch plans (one cluster of 8 alone, a few blocks per
+    launch, the tuned shares, a wide single-block launch) change which block
+    runs which school and in what order; every plan must give every school
+    its single-school trajectory."""
+    sizes = np.array([65536, 40000, 33000, 20000, 16385, 9000, 8193, 8192, 5000, 700, 31, 1, 2,
+                      4097], dtype=np.uint64)
+    offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    seeds = (5000 + np.arange(sizes.size)).astype(np.uint64)
+    tmpl = fsb.fsb_config_init(1, 0, step=1.5, init_weight_mode=1)
+    steps = 4
+    plans = [[(8, 8)], [(8, 16), (1, 3)], [(8, 8), (4, 4), (2, 2), (1, 1)],
+             [(8, 80), (4, 32), (2, 20), (1, 20)], [(8, 8), (1, 100)]]
+    refs = [oracle_school(tmpl, int(offsets[k + 1] - offsets[k]), seeds[k], k, steps)
+            for k in range(sizes.size)]
+    for plan in plans:
+        ts, state = make_state(offsets[-1])
+        b = fsb.fsb_batch_create(tmpl, offsets, seeds, state, init=True)
+        fsb.fsb_batch_set_plan(b, plan)
+        stats = np.zeros(sizes.size * steps, fsb.STATS_DTYPE)
+        fsb.fsb_batch_step(b, steps, stats)
+        fsb.fsb_batch_destroy(b)
+        got = read_state(ts)
+        for k, (ref, ref_stats) in enumerate(refs):
+            lo, hi = int(offsets[k]), int(offsets[k + 1])
+            sub = {"x": got["x"][lo:hi], "y": got["y"][lo:hi], "w": got["w"][lo:hi],
+                   "prev": got["prev"][lo:hi],
+                   "cur": np.sqrt(got["x"][lo:hi] * got["x"][lo:hi] +
+                                  got["y"][lo:hi] * got["y"][lo:hi])}
+            what = "plan %s school %d (N=%d)" % (plan, k, hi - lo)
+            assert_state_equal(sub, ref, what)
+            assert_stats_match(stats[k * steps:(k + 1) * steps], ref_stats, tmpl.precision, what)
