@@ -116,9 +116,9 @@ int plan_batch(fsb_batch* b, int forced) {
   const int slots = fsb::batch_max_clusters(1, L.acc);  // resident single blocks
   if (slots < 1) return bfail(FSB_ERR_UNSUPPORTED, "batch kernel cannot be resident");
   // Work of a queue: its fish times the relative cost per fish-step of its
-  // cluster width, measured on GB300 with the shared-memory kernel (single
-  // blocks carry the smallest schools, whose steps are latency-bound; a
-  // cluster of 2 holds schools filled from one half up).
+  // cluster width, fitted on GB300 to the best plans of a sweep of explicit
+  // plans over a log-uniform ensemble (single blocks carry the smallest
+  // schools, whose steps are latency-bound, so a fish costs most there).
   const double cost[fsb::kBatchQueues] = {1.0, 0.95, 1.1, 1.2};
   double work[fsb::kBatchQueues], total = 0.0;
   for (int t = 0; t < fsb::kBatchQueues; ++t) {
