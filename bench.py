@@ -139,8 +139,10 @@ def kernel_source_hash():
 
 # Sources of the two on-chip kernels, whose roofline is instruction issue.
 ALU_KERNEL_SOURCES = {
-    "resident": ("fsb_resident.cu", "fsb_onchip.cuh", "fsb_device.cuh", "fsb_reduce.cuh"),
-    "batch": ("fsb_batch.cu", "fsb_onchip.cuh", "fsb_device.cuh", "fsb_reduce.cuh"),
+    "resident": ("fsb_resident.cu", "fsb_onchip.cuh", "fsb_check.cuh", "fsb_device.cuh",
+                 "fsb_reduce.cuh"),
+    "batch": ("fsb_batch.cu", "fsb_onchip.cuh", "fsb_check.cuh", "fsb_device.cuh",
+              "fsb_reduce.cuh"),
     "collective": ("fsb_collective.cu", "fsb_device.cuh", "fsb_reduce.cuh"),
 }
 

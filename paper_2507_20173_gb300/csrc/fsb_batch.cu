@@ -34,6 +34,7 @@
 
 #include <cooperative_groups.h>
 
+#include "fsb_check.cuh"
 #include "fsb_device.cuh"
 #include "fsb_internal.h"
 #include "fsb_onchip.cuh"
@@ -155,8 +156,12 @@ __device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int r
   const uint32_t slice = ((n + nb - 1) / nb + 1) & ~1u;
   const uint32_t lo = static_cast<uint32_t>(rank) * slice;
   const uint32_t hi = lo + slice < n ? lo + slice : n;
-  const uint32_t nf = hi > lo ? hi - lo : 0u;     // this block's fish
-  const uint32_t np = (nf + 1) / 2;               // ... and pairs; the last may be half
+  // this block's fish (at most one block's worth: the plan gives a school
+  // a cluster that holds it) and pairs, the last possibly half
+  const uint32_t nf0 = hi > lo ? hi - lo : 0u;
+  const uint32_t nf = fsb_check(nf0 <= kBlockFish, &a.bctl->status, &a.bctl->site, 1u)
+                          ? nf0 : kBlockFish;
+  const uint32_t np = (nf + 1) / 2;
   const uint32_t pair0 = lo / 2;                  // in-school pair index of element 0
   const Key key{static_cast<uint32_t>(a.seeds[k]), static_cast<uint32_t>(a.seeds[k] >> 32)};
   const uint32_t school = k;

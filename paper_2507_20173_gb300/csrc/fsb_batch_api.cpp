@@ -377,6 +377,10 @@ int fsb_batch_step(fsb_batch_handle b, uint32_t n_steps, fsb_step_stats* host_st
                           cudaMemcpyDeviceToHost, b->stream));
     BCUDA(cudaStreamSynchronize(b->stream));
     fsb::batch_finish_stats(host_stats, count, b->L.acc);
+    // the debug build's invariant checks (always 0 in the release build)
+    int status = 0;
+    BCUDA(cudaMemcpy(&status, &b->d_bctl->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status != 0) return bfail(FSB_ERR_STATE, "batch kernel invariant check failed");
   }
   return FSB_OK;
 }

@@ -170,6 +170,8 @@ constexpr int kBatchQueues = 4;
 constexpr int kBatchMaxLaunches = 4;
 struct alignas(16) BatchCtl {
   unsigned next[kBatchQueues];
+  int status;     // debug build: a failed invariant check (FSB_ERR_STATE)
+  unsigned site;  // ... and where
 };
 
 // Queue of the schools that need clusters of c blocks (c = 1, 2, 4, 8).

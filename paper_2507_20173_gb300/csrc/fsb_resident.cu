@@ -28,6 +28,7 @@
 // a failed call leaves the school as it was.
 #include <cstdint>
 
+#include "fsb_check.cuh"
 #include "fsb_device.cuh"
 #include "fsb_internal.h"
 #include "fsb_onchip.cuh"
@@ -128,9 +129,13 @@ __global__ void __launch_bounds__(kResThreads + 32, 1) resident_kernel(ResidentA
   // bits; the slice (hence lo) is even, so no swim pair straddles two blocks
   const uint32_t lo = static_cast<uint32_t>(blockIdx.x * a.slice);
   const uint32_t hi = static_cast<uint32_t>(lo + a.slice < a.n ? lo + a.slice : a.n);
-  const uint32_t nf = hi > lo ? hi - lo : 0u;
-  const uint32_t np = (nf + 1) / 2;
   const uint32_t cap = static_cast<uint32_t>(a.slice / 2);  // pairs per array
+  // the slice fits the arrays, and the grid covers the school (host-checked)
+  const uint32_t nf0 = hi > lo ? hi - lo : 0u;
+  const bool fits = fsb_check(nf0 <= 2 * cap && static_cast<uint64_t>(gridDim.x) * a.slice >= a.n,
+                              &a.ctl->status, &a.ctl->timeout_site, 0xB0u);
+  const uint32_t nf = fits ? nf0 : (nf0 < 2 * cap ? nf0 : 2 * cap);
+  const uint32_t np = (nf + 1) / 2;
   float2* const X0 = res_smem;
   float2* const X1 = res_smem + cap;
   float2* const Y0 = res_smem + 2 * cap;
