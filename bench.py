@@ -52,6 +52,9 @@ def parse_args():
     ap.add_argument("--workload", choices=["stream", "small", "resident", "batch", "precision",
                                            "eat", "collective"],
                     default="stream")
+    ap.add_argument("--precision-schools", type=int, default=1,
+                    help="precision study: time this many schools of the 64-school "
+                         "ensemble (seeds 100 + k) per mode; errors on the first")
     ap.add_argument("--batch-schools", type=int, default=None,
                     help="use only the first N schools of the batched ensemble")
     ap.add_argument("--batch-cluster", type=int, default=0)
@@ -390,10 +393,11 @@ def exact_sums(w, x, y):
 
 
 def run_precision(args, world, rank, local):
-    """Precision study: one school of N = 2^24 fish (seed 100, a member of
-    the 64-school study ensemble), T = 1000 steps, in each arithmetic mode.
-    Reports each mode's throughput, the error of its barycentre sums at
-    steps 1, 10, 100 and 1000 against the exact sums of the read-back state
+    """Precision study: schools of N = 2^24 fish from the 64-school study
+    ensemble (seeds 100 + k; --precision-schools of them, one by default),
+    T = 1000 steps, in each arithmetic mode.  Reports each mode's throughput
+    over those schools, the error of the first school's barycentre sums at
+    steps 1, 10, 100 and 1000 against the exact sums of its read-back state
     (normalised by sum |w x|), and the drift between the binary32 and the
     binary64 trajectories (the same draws, different rounding)."""
     import torch
@@ -437,7 +441,21 @@ def run_precision(args, world, rank, local):
                 "bary_x_abs_err": abs(last["sum_wx"] / last["sum_w"] - ex["sum_wx"] / ex["sum_w"])}
         finals[name] = got
         s.destroy()
-        modes[name] = {"fish_steps_per_s": n * total / elapsed, "errors": errs}
+        # the ensemble's other schools, timed over the whole call
+        for k in range(1, max(1, args.precision_schools)):
+            cfg_k = fsb.fsb_config_init(n, 100 + k, precision=getattr(fsb, "FSB_" + name),
+                                        path=fsb.FSB_PATH_STREAM)
+            sk = fsb.School.create(cfg_k, stream=stream)
+            torch.cuda.synchronize()
+            start.record(stream)
+            sk.step(total)
+            stop.record(stream)
+            torch.cuda.synchronize()
+            elapsed += start.elapsed_time(stop) / 1e3
+            sk.destroy()
+        schools = max(1, args.precision_schools)
+        modes[name] = {"fish_steps_per_s": schools * n * total / elapsed, "errors": errs,
+                       "schools_timed": schools}
     drift = {f: float(np.max(np.abs(finals["FP32_KAHAN"][f].astype(np.float64) -
                                     finals["FP64_STATE"][f])))
              for f in ("x", "y", "w")}
@@ -448,10 +466,12 @@ def run_precision(args, world, rank, local):
                 "value": modes["FP32_KAHAN"]["fish_steps_per_s"], "unit": UNIT, "n_gpus": 1,
                 "steps": total, "warmup": 0, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
-                "config": {"workload": "precision N=2^%d T=%d seed 100" % (n.bit_length() - 1,
-                                                                          total),
-                           "note": "one school of the 64-school ensemble; errors against exact "
-                                   "host sums of the read-back state"},
+                "config": {"workload": "precision %d x N=2^%d T=%d seeds 100+k"
+                                       % (max(1, args.precision_schools), n.bit_length() - 1,
+                                          total),
+                           "note": "schools of the 64-school ensemble, timed per mode; errors "
+                                   "of the first against exact host sums of its read-back "
+                                   "state"},
                 "modes": modes, "trajectory_drift_fp32_vs_fp64_state": drift}
         print(json.dumps(line), flush=True)
 
