@@ -382,9 +382,12 @@ bool resident_config(int sms, int acc, int swim_mode, uint64_t n, fsb::ResidentL
     uint64_t grid = (n + per_block - 1) / per_block;
     if (grid > static_cast<uint64_t>(sms)) continue;
     if (grid < 1) grid = 1;
-    // spread over more SMs while every block keeps at least 2048 fish (a
-    // block's step is latency-bound below that)
-    const uint64_t spread = (n + 2047) / 2048;
+    // spread over more SMs while every block keeps at least fpt * 256 fish
+    // (a block's step is latency-bound below some slice; the fish-per-thread
+    // setting picks that floor, 1024 to 4096, so the autotuner can trade a
+    // cheaper grid barrier against more work per block)
+    const uint64_t floor_fish = static_cast<uint64_t>(fpt) * 256;
+    const uint64_t spread = (n + floor_fish - 1) / floor_fish;
     const uint64_t most = spread < static_cast<uint64_t>(sms) ? spread : sms;
     if (grid < most) grid = most;
     // even, so no fish pair (one swim block) straddles two blocks
