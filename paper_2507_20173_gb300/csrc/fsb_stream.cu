@@ -78,7 +78,11 @@ __global__ void __launch_bounds__(BLOCK, MINB) stream_pass_kernel(StreamArgs<Rea
   const uint64_t ngroups = a.n / VEC;
   const uint64_t stride = static_cast<uint64_t>(gridDim.x) * BLOCK;
   const uint64_t tid = static_cast<uint64_t>(blockIdx.x) * BLOCK + threadIdx.x;
-  for (uint64_t g = tid; g < ngroups; g += stride) {
+  // consecutive passes sweep the school in opposite directions, so a pass
+  // starts on the groups the previous one touched last (still in L2)
+  const bool backward = (j & 1u) != 0u;
+  for (uint64_t gi = tid; gi < ngroups; gi += stride) {
+    const uint64_t g = backward ? ngroups - 1 - gi : gi;
     Real x[VEC], y[VEC], w[VEC], pv[VEC];
     vload<Real, VEC>(x, a.x, g);
     vload<Real, VEC>(y, a.y, g);
