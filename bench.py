@@ -144,8 +144,8 @@ def kernel_source_hash():
 ALU_KERNEL_SOURCES = {
     "resident": ("fsb_resident.cu", "fsb_onchip.cuh", "fsb_check.cuh", "fsb_device.cuh",
                  "fsb_reduce.cuh"),
-    "batch": ("fsb_batch.cu", "fsb_onchip.cuh", "fsb_check.cuh", "fsb_device.cuh",
-              "fsb_reduce.cuh"),
+    "batch": ("fsb_batch.cu", "fsb_batch_wide.cu", "fsb_batch_kernel.cuh", "fsb_onchip.cuh",
+              "fsb_check.cuh", "fsb_device.cuh", "fsb_reduce.cuh"),
     "collective": ("fsb_collective.cu", "fsb_device.cuh", "fsb_reduce.cuh"),
 }
 

@@ -266,15 +266,16 @@ int fsb_batch_create(const fsb_config* tmpl, uint32_t n_schools, const uint64_t*
 int fsb_batch_step(fsb_batch_handle b, uint32_t n_steps, fsb_step_stats* stats);
 
 /* Cluster size of the batch's schools.
- *   0 (default): each school runs on the smallest cluster of 1, 2, 4 or 8
- *     blocks (8192 fish per block) that holds it.  One persistent launch per
- *     cluster size in use runs concurrently with the others, each on a share
- *     of the SMs proportional to its schools' fish; single-block schools
- *     take the SMs left over, and every launch helps with the schools of
- *     smaller clusters once its own are done.
- *   1, 2, 4, 8: every school larger than one block runs on clusters of this
+ *   0 (default): each school runs on the smallest cluster (1 to 8 blocks of
+ *     8192 fish) that holds it.  One persistent launch per cluster size in
+ *     use runs concurrently with the others, each on a share of the SMs
+ *     proportional to its schools' fish; single-block schools take the SMs
+ *     left over, and every launch helps with the schools of smaller clusters
+ *     once its own are done.
+ *   1 to 8: every school larger than one block runs on clusters of this
  *     size (one launch on every SM it can hold, single blocks beside it).
- * Too small for the largest school -> FSB_ERR_UNSUPPORTED.  Synchronises. */
+ * Too small for the largest school -> FSB_ERR_UNSUPPORTED; another value ->
+ * FSB_ERR_INVALID_ARG.  Synchronises. */
 int fsb_batch_set_cluster(fsb_batch_handle b, int cluster);
 
 /* Launch shape and step counter of a batch (any pointer may be NULL): the
@@ -284,18 +285,19 @@ int fsb_batch_set_cluster(fsb_batch_handle b, int cluster);
 int fsb_batch_info(fsb_batch_handle b, int* cluster, int* n_clusters, int* filler_blocks,
                    uint32_t* n_big, uint64_t* step);
 
-/* The batch's launch plan (any pointer may be NULL): n_launches (1 to 4)
+/* The batch's launch plan (any pointer may be NULL): n_launches (1 to 8)
  * concurrent persistent launches, launch i running clusters of cluster[i]
- * blocks on a grid of blocks[i] blocks (arrays of 4; entries past
- * n_launches are 0), and queue_schools[t] (array of 4) schools in the work
- * queue of clusters of 8, 4, 2 and 1 block(s). */
+ * blocks on a grid of blocks[i] blocks (arrays of 8; entries past
+ * n_launches are 0), and queue_schools[t] (array of 8) schools in the work
+ * queue of clusters of 8 - t blocks (t = 0 .. 6) and of single blocks
+ * (t = 7). */
 int fsb_batch_plan(fsb_batch_handle b, int* n_launches, int* cluster, int* blocks,
                    uint32_t* queue_schools);
 
 /* Replace the batch's launches, keeping its work queues (set by
- * fsb_batch_set_cluster): n_launches (1 to 4) launches in decreasing cluster
- * size, launch i running clusters of cluster[i] (1, 2, 4 or 8) blocks on a
- * grid of blocks[i] (a positive multiple of cluster[i]).  The widest launch
+ * fsb_batch_set_cluster): n_launches (1 to 8) launches in decreasing cluster
+ * size, launch i running clusters of cluster[i] (1 to 8) blocks on a grid
+ * of blocks[i] (a positive multiple of cluster[i]).  The widest launch
  * must be at least as wide as the widest non-empty queue.  Any other
  * combination -> FSB_ERR_INVALID_ARG, handle unchanged.  Synchronises. */
 int fsb_batch_set_plan(fsb_batch_handle b, int n_launches, const int* cluster,

@@ -295,14 +295,14 @@ def fsb_batch_info(handle: int) -> dict:
 
 def fsb_batch_plan(handle: int) -> dict:
     """The batch's concurrent launches (cluster size, grid) and the schools
-    in each work queue (clusters of 8, 4, 2, 1 blocks)."""
+    in each work queue, keyed by the queue's cluster size (8 down to 1)."""
     n = ctypes.c_int()
-    c, b = (ctypes.c_int * 4)(), (ctypes.c_int * 4)()
-    q = (ctypes.c_uint32 * 4)()
+    c, b = (ctypes.c_int * 8)(), (ctypes.c_int * 8)()
+    q = (ctypes.c_uint32 * 8)()
     _check(lib().fsb_batch_plan(ctypes.c_void_p(handle), ctypes.byref(n), c, b, q),
            "fsb_batch_plan")
     return {"launches": [{"cluster": c[i], "blocks": b[i]} for i in range(n.value)],
-            "queue_schools": {8: q[0], 4: q[1], 2: q[2], 1: q[3]}}
+            "queue_schools": {8 - t: q[t] for t in range(7)} | {1: q[7]}}
 
 
 def fsb_batch_set_plan(handle: int, launches) -> None:

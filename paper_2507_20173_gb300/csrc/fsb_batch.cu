@@ -32,331 +32,10 @@
 #include <cstdint>
 #include <cstring>
 
-#include <cooperative_groups.h>
-
-#include "fsb_check.cuh"
-#include "fsb_device.cuh"
-#include "fsb_internal.h"
-#include "fsb_onchip.cuh"
-#include "fsb_reduce.cuh"
+#include "fsb_batch_kernel.cuh"
 
 namespace fsb {
 namespace {
-
-namespace cg = cooperative_groups;
-
-struct BatchArgs {
-  float* __restrict__ x;
-  float* __restrict__ y;
-  float* __restrict__ w;
-  float* __restrict__ pv;
-  const unsigned long long* __restrict__ offsets;  // n_schools + 1
-  const unsigned long long* __restrict__ seeds;    // n_schools
-  const uint32_t* __restrict__ order;              // queues 0..3, each largest first
-  uint32_t queue_lo[kBatchQueues + 1];             // queue t: order[queue_lo[t] .. queue_lo[t+1])
-  int first_queue;                                 // whole-cluster queue this launch starts at
-  uint32_t n_schools;
-  Physics<float> ph;
-  int init;                                        // initialise each school before stepping
-  int weight_mode;
-  const unsigned long long* base_step_ptr;
-  uint32_t n_steps;
-  BatchCtl* bctl;
-  fsb_step_stats* stats;                           // n_schools * n_steps, school-major
-};
-
-// Barycentre partials of one step: a warp's, a block's.
-template <typename Part>
-struct Part3 {
-  Part w, x, y;
-};
-
-constexpr int kBatchThreads = 512;                // fish threads
-constexpr int kBatchWarps = kBatchThreads / 32;
-constexpr int kBlockThreads = kBatchThreads + 32;  // and one helper warp
-constexpr int kBlockFish = 8192;              // fish one block holds
-constexpr int kBlockPairs = kBlockFish / 2;
-constexpr int kMaxCluster = 8;
-// The block's fish in shared memory: five arrays of kBlockPairs float2
-// (fish 2p and 2p + 1 of the block's slice share element p).
-constexpr size_t kStateSmem = 5 * sizeof(float2) * kBlockPairs;
-
-// Shared-memory exchange of one block.  The step maxima go into rank 0's
-// slots by atomics (three slots rotate by step: a slot is read after the
-// barrier that ends its step's swim, and zeroed three steps ahead of its
-// next use).  Barycentre partials are double-buffered by step parity: the
-// warps' partials of step p are folded into the block's after the barrier
-// that ends step p's eat, and, on a cluster, the blocks' partials in rank 0
-// one barrier later.
-template <int ACC>
-struct BatchShared {
-  using Part = typename SumAcc<ACC>::Part;
-  uint32_t slot_max[3], slot_ekey[3];
-  Part3<Part> warp_part[2][kBatchWarps];
-  Part3<Part> block_part[2][kMaxCluster];
-};
-
-// Fold of the warps' partials by one warp, a fixed xor tree over the
-// kBatchWarps partials (lanes beyond them repeat them); the result is valid
-// in every lane.
-template <typename Part>
-__device__ __forceinline__ Part3<Part> fold_warps(const Part3<Part>* wp) {
-  static_assert(kBatchWarps <= 32 && (kBatchWarps & (kBatchWarps - 1)) == 0,
-                "fold tree over a power-of-two warp count");
-  const int lane = threadIdx.x & 31;
-  Part3<Part> r = wp[lane & (kBatchWarps - 1)];
-#pragma unroll
-  for (int off = kBatchWarps / 2; off > 0; off >>= 1) {
-    r.w = merge(r.w, shfl_xor(r.w, off));
-    r.x = merge(r.x, shfl_xor(r.x, off));
-    r.y = merge(r.y, shfl_xor(r.y, off));
-  }
-  return r;
-}
-
-// A step's barycentre sums go out as raw partials (raw_sum) and the host
-// converts them after the copy-out (batch_finish_stats), which keeps
-// binary64 arithmetic, slow on this GPU, off the per-step critical path.
-template <typename Part>
-__device__ __forceinline__ void put_sums(fsb_step_stats* st, Part w, Part x, Part y) {
-  st->sum_w = raw_sum(w);
-  st->sum_wx = raw_sum(x);
-  st->sum_wy = raw_sum(y);
-}
-
-// Runs one school on `nb` blocks (this block is rank `rank`): load or
-// initialise, all steps, write back.  For nb > 1 the caller's cluster must
-// contain exactly nb blocks that all call this with the same school, and
-// rank 0's slots must be zero (they are again on return).
-//
-// Pass p = 0 .. T over the block's fish pairs (the fish warps): the eat of
-// step p with normaliser N_p and its barycentre terms (p >= 1), then the
-// swim of step p + 1 with its objective and maxima (p < T).  One barrier
-// follows each pass (a cluster barrier for nb > 1):
-//   before it: each fish warp's maxima of step p + 1 into rank 0's slots
-//              (atomics) and its barycentre partial of step p;
-//   after it:  the fish warps read M_{p+1} and E_{p+1} and start the next
-//              pass, while the block's helper warp zeroes the slots of step
-//              p + 3 (rank 0), folds the block's partial of step p (nb = 1:
-//              the step's sums; else into rank 0's block_part), folds the
-//              blocks' partials of step p - 1 (rank 0) and writes the step's
-//              maxima -- work that would otherwise hold one fish warp back
-//              at every barrier.
-template <int ACC, bool VAR>
-__device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int rank, int nb,
-                                           BatchShared<ACC>& S, const PairState& B) {
-  using Acc = SumAcc<ACC>;
-  using Part = typename Acc::Part;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const bool helper = warp == kBatchWarps;
-  const uint64_t s_lo = a.offsets[k];
-  // in-school fish indices fit 32 bits (schools hold at most C * 8192 fish)
-  const uint32_t n = static_cast<uint32_t>(a.offsets[k + 1] - s_lo);
-  // an even slice keeps each fish pair (one swim block) in one block
-  const uint32_t slice = ((n + nb - 1) / nb + 1) & ~1u;
-  const uint32_t lo = static_cast<uint32_t>(rank) * slice;
-  const uint32_t hi = lo + slice < n ? lo + slice : n;
-  // this block's fish (at most one block's worth: the plan gives a school
-  // a cluster that holds it) and pairs, the last possibly half
-  const uint32_t nf0 = hi > lo ? hi - lo : 0u;
-  const uint32_t nf = fsb_check(nf0 <= kBlockFish, &a.bctl->status, &a.bctl->site, 1u)
-                          ? nf0 : kBlockFish;
-  const uint32_t np = (nf + 1) / 2;
-  const uint32_t pair0 = lo / 2;                  // in-school pair index of element 0
-  const Key key{static_cast<uint32_t>(a.seeds[k]), static_cast<uint32_t>(a.seeds[k] >> 32)};
-  const uint32_t school = k;
-  const Physics<float> ph = kernel_physics<VAR>(a.ph);
-  cg::cluster_group cluster = cg::this_cluster();
-  // rank 0's exchange (this block's own for nb = 1)
-  BatchShared<ACC>* S0 = nb > 1 ? cluster.map_shared_rank(&S, 0) : &S;
-  fsb_step_stats* const st = a.stats + static_cast<uint64_t>(k) * a.n_steps;
-  const uint32_t T = a.n_steps;
-
-  // load (or initialise) the slice; the second fish of a half pair is zero
-  for (uint32_t e = tid; e < np; e += kBlockThreads) {
-    float xv[2] = {0.f, 0.f}, yv[2] = {0.f, 0.f}, wv[2] = {0.f, 0.f}, fv[2] = {0.f, 0.f};
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const uint32_t i = lo + 2 * e + h;  // index in school
-      if (2 * e + h < nf) {
-        if (a.init) {
-          init_fish(key, school, i, a.weight_mode, ph, xv[h], yv[h], wv[h]);
-        } else {
-          xv[h] = a.x[s_lo + i];
-          yv[h] = a.y[s_lo + i];
-          wv[h] = a.w[s_lo + i];
-        }
-        fv[h] = objective(xv[h], yv[h]);
-      }
-    }
-    B.Xd[e] = make_float2(xv[0], xv[1]);
-    B.Yd[e] = make_float2(yv[0], yv[1]);
-    B.W[e] = make_float2(wv[0], wv[1]);
-    B.F[e] = make_float2(fv[0], fv[1]);
-  }
-  __syncthreads();  // the passes take the pairs in another thread order
-
-  const uint32_t last = T + (nb > 1 ? 1u : 0u);  // a cluster's last fold needs one more barrier
-  const uint64_t t0 = *a.base_step_ptr;
-  const float scaled = exact_scaled_width(ph.step);
-  float N = 0.f;  // feeding normaliser of the pass's eat
-  for (uint32_t p = 0; p <= last; ++p) {
-    const bool do_eat = p >= 1 && p <= T;
-    const bool do_swim = p < T;
-    if (!helper) {
-      PassCtx c{key, school, pair0, static_cast<uint32_t>(t0 + p + 1), N, scaled};
-      uint32_t mb = 0, ek = 0;
-      Acc acc;
-      if (p == 0 && T > 1)
-        block_pass<false, true, false, false>(B, np, nf, c, ph, acc, mb, ek, kBatchThreads);
-      else if (p == 0 && T == 1)
-        block_pass<false, true, true, false>(B, np, nf, c, ph, acc, mb, ek, kBatchThreads);
-      else if (p + 1 < T)
-        block_pass<true, true, false, false>(B, np, nf, c, ph, acc, mb, ek, kBatchThreads);
-      else if (p + 1 == T)
-        block_pass<true, true, true, false>(B, np, nf, c, ph, acc, mb, ek, kBatchThreads);
-      else if (p == T)
-        block_pass<true, false, false, true>(B, np, nf, c, ph, acc, mb, ek, kBatchThreads);
-      if (do_swim) {
-        mb = warp_max(mb);
-        ek = warp_max(ek);
-        if (lane == 0) {
-          atomicMax(&S0->slot_max[(p + 1) % 3], mb);
-          atomicMax(&S0->slot_ekey[(p + 1) % 3], ek);
-        }
-      }
-      if (do_eat) {
-        Part3<Part> wp;
-        wp.w = warp_tree(acc.pw());
-        wp.x = warp_tree(acc.px());
-        wp.y = warp_tree(acc.py());
-        if (lane == 0) S.warp_part[p & 1][warp] = wp;
-      }
-    }
-    if (nb > 1)
-      cluster.sync();
-    else
-      __syncthreads();
-    if (helper) {
-      if (rank == 0 && lane == 0) {
-        S.slot_max[p % 3] = 0u;
-        S.slot_ekey[p % 3] = 0u;
-      }
-      if (do_eat) {
-        const Part3<Part> bp = fold_warps(S.warp_part[p & 1]);
-        if (lane == 0) {
-          if (nb == 1)
-            put_sums(st + (p - 1), bp.w, bp.x, bp.y);
-          else
-            S0->block_part[p & 1][rank] = bp;
-        }
-      }
-      // the blocks' partials of step p - 1, in rank order
-      if (nb > 1 && rank == 0 && lane == 0 && p >= 2) {
-        const Part3<Part>* src = S.block_part[(p - 1) & 1];
-        Part fw = part_zero<Part>(), fx = part_zero<Part>(), fy = part_zero<Part>();
-        for (int r = 0; r < nb; ++r) {
-          fw = merge(fw, src[r].w);
-          fx = merge(fx, src[r].x);
-          fy = merge(fy, src[r].y);
-        }
-        put_sums(st + (p - 2), fw, fx, fy);
-      }
-      if (do_swim && rank == 0 && lane == 0) {
-        st[p].max_abs_delta = static_cast<double>(__uint_as_float(S.slot_max[(p + 1) % 3]));
-        st[p].eat_max_diff = static_cast<double>(key_to_value(S.slot_ekey[(p + 1) % 3], 0.f));
-      }
-    } else if (do_swim) {
-      // feeding normaliser of the next pass: M, or the paper's eat() value E
-      N = ph.feed_mode ? key_to_value(S0->slot_ekey[(p + 1) % 3], 0.f)
-                       : __uint_as_float(S0->slot_max[(p + 1) % 3]);
-    }
-  }
-  // rank 0 has read every block's partials, and its slots are zero, before
-  // any block leaves for the next school
-  if (nb > 1) cluster.sync();
-
-  for (uint32_t e = tid; e < np; e += kBlockThreads) {
-    const float2 xv = B.Xs[e], yv = B.Ys[e], wv = B.W[e];
-    const float2 pv = T ? B.De[e] : B.F[e];
-    const uint64_t g = s_lo + lo + 2 * e;
-    a.x[g] = xv.x;
-    a.y[g] = yv.x;
-    a.w[g] = wv.x;
-    a.pv[g] = pv.x;
-    if (2 * e + 1 < nf) {
-      a.x[g + 1] = xv.y;
-      a.y[g + 1] = yv.y;
-      a.w[g + 1] = wv.y;
-      a.pv[g + 1] = pv.y;
-    }
-  }
-  __syncthreads();  // the slice's shared state is free for the next school
-}
-
-template <int CLUSTER, int ACC, bool VAR>
-__global__ void __launch_bounds__(kBlockThreads, 1) batch_kernel(BatchArgs a) {
-  __shared__ BatchShared<ACC> S;
-  __shared__ uint32_t s_pick;
-  extern __shared__ float2 state_smem[];
-  float2* const X = state_smem;
-  float2* const Y = state_smem + kBlockPairs;
-  float2* const D = state_smem + 4 * kBlockPairs;
-  const PairState B = pair_state(X, Y, D, X, Y, D, state_smem + 3 * kBlockPairs,
-                                 state_smem + 2 * kBlockPairs);
-  cg::cluster_group cluster = cg::this_cluster();
-  const int rank = static_cast<int>(cluster.block_rank());
-  if (threadIdx.x < 3) {
-    S.slot_max[threadIdx.x] = 0u;  // visible to the cluster after the first pick's barriers
-    S.slot_ekey[threadIdx.x] = 0u;
-  }
-
-  // Phase 1 (whole cluster per school) through the multi-block queues from
-  // this launch's own on, then phase 2 (each block on its own) through the
-  // single-block queue.  The queue index is uniform across the cluster
-  // (every pick is broadcast from rank 0).  One call site keeps one inlined
-  // copy of the per-school loop.
-  constexpr int kSingle = kBatchQueues - 1;
-  int t = CLUSTER > 1 ? a.first_queue : kSingle;
-  for (;;) {
-    const bool whole_cluster = t < kSingle;
-    uint32_t idx;
-    if (whole_cluster) {
-      if (rank == 0 && threadIdx.x == 0) s_pick = atomicAdd(&a.bctl->next[t], 1u);
-      cluster.sync();
-      idx = *cluster.map_shared_rank(&s_pick, 0);
-      cluster.sync();  // every block has read rank 0's pick
-    } else {
-      if (threadIdx.x == 0) s_pick = atomicAdd(&a.bctl->next[kSingle], 1u);
-      __syncthreads();
-      idx = s_pick;
-      __syncthreads();
-    }
-    if (idx >= a.queue_lo[t + 1] - a.queue_lo[t]) {
-      if (t == kSingle) break;
-      ++t;
-      continue;
-    }
-    run_school<ACC, VAR>(a, a.order[a.queue_lo[t] + idx], whole_cluster ? rank : 0,
-                         whole_cluster ? CLUSTER : 1, S, B);
-  }
-}
-
-template <int CLUSTER, int ACC>
-const void* kernel_ptr(bool var) {
-  if (var) return reinterpret_cast<const void*>(&batch_kernel<CLUSTER, ACC, true>);
-  return reinterpret_cast<const void*>(&batch_kernel<CLUSTER, ACC, false>);
-}
-
-template <int CLUSTER>
-const void* pick_acc(int acc, bool var) {
-  switch (acc) {
-    case kAccPlain32: return kernel_ptr<CLUSTER, kAccPlain32>(var);
-    case kAccKahan32: return kernel_ptr<CLUSTER, kAccKahan32>(var);
-    case kAccF64: return kernel_ptr<CLUSTER, kAccF64>(var);
-    default: return nullptr;
-  }
-}
 
 // The variant kernels (var) share the default ones' block, register bound
 // and shared memory, hence their occupancy.
@@ -364,8 +43,12 @@ const void* pick(int cluster, int acc, bool var = false) {
   switch (cluster) {
     case 1: return pick_acc<1>(acc, var);
     case 2: return pick_acc<2>(acc, var);
+    case 3: return pick_acc<3>(acc, var);
     case 4: return pick_acc<4>(acc, var);
-    case 8: return pick_acc<8>(acc, var);
+    case 5:
+    case 6:
+    case 7:
+    case 8: return batch_kernel_wide(cluster, acc, var);
     default: return nullptr;
   }
 }

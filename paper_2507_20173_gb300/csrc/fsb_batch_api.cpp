@@ -86,21 +86,20 @@ namespace {
 // left over.
 int plan_batch(fsb_batch* b, int forced) {
   const uint64_t cap = fsb::batch_block_capacity();
-  if (forced != 0 && forced != 1 && forced != 2 && forced != 4 && forced != 8)
-    return bfail(FSB_ERR_INVALID_ARG, "batch cluster size must be 1, 2, 4 or 8");
-  const int widest = forced ? forced : 8;
+  if (forced < 0 || forced > fsb::kMaxBatchCluster)
+    return bfail(FSB_ERR_INVALID_ARG, "batch cluster size must be 0 to %d", fsb::kMaxBatchCluster);
+  const int widest = forced ? forced : fsb::kMaxBatchCluster;
   if (static_cast<uint64_t>(widest) * cap < b->max_school)
     return bfail(FSB_ERR_UNSUPPORTED,
                  "largest school (%llu fish) exceeds a cluster of %d blocks (%llu fish)",
                  static_cast<unsigned long long>(b->max_school), widest,
                  static_cast<unsigned long long>(widest * cap));
   std::vector<uint32_t> queue[fsb::kBatchQueues];
-  uint64_t fish[fsb::kBatchQueues] = {0, 0, 0, 0};
+  uint64_t fish[fsb::kBatchQueues] = {};
   for (uint32_t k : b->sizes_sorted) {
     const uint64_t n = b->offsets[k + 1] - b->offsets[k];
-    int need = 1;
-    while (static_cast<uint64_t>(need) * cap < n) need *= 2;
-    const int t = fsb::batch_queue_of(need == 1 ? 1 : (forced ? forced : need));
+    const int need = static_cast<int>((n + cap - 1) / cap);  // blocks that hold it
+    const int t = fsb::batch_queue_of(need <= 1 ? 1 : (forced ? forced : need));
     queue[t].push_back(k);
     fish[t] += n;
   }
@@ -115,18 +114,20 @@ int plan_batch(fsb_batch* b, int forced) {
 
   const int slots = fsb::batch_max_clusters(1, L.acc);  // resident single blocks
   if (slots < 1) return bfail(FSB_ERR_UNSUPPORTED, "batch kernel cannot be resident");
-  // Work of a queue: its fish times the relative cost per fish-step of its
-  // cluster width, fitted on GB300 to the best plans of a sweep of explicit
-  // plans over a log-uniform ensemble (single blocks carry the smallest
-  // schools, whose steps are latency-bound, so a fish costs most there).
-  const double cost[fsb::kBatchQueues] = {1.0, 0.95, 1.1, 1.2};
+  // Work of a queue: its fish times a weight per cluster width, fitted on
+  // GB300 to the best of a sweep of explicit plans over a log-uniform
+  // ensemble (every launch helps the narrower queues once its own is empty,
+  // so the single-block queue needs less than its share; index: cluster
+  // size).
+  const double cost[fsb::kMaxBatchCluster + 1] = {0.0, 0.8, 1.0, 1.1, 1.1, 1.1, 1.0, 0.9, 1.0};
   double work[fsb::kBatchQueues], total = 0.0;
   for (int t = 0; t < fsb::kBatchQueues; ++t) {
-    work[t] = cost[t] * static_cast<double>(fish[t]);
+    const int c = t == fsb::kBatchQueues - 1 ? 1 : fsb::kMaxBatchCluster - t;
+    work[t] = cost[c] * static_cast<double>(fish[t]);
     total += work[t];
   }
   int n = 0, used = 0;
-  for (int c = 8; c >= 2; c /= 2) {
+  for (int c = fsb::kMaxBatchCluster; c >= 2; --c) {
     const int t = fsb::batch_queue_of(c);
     if (queue[t].empty()) continue;
     const int max_clusters = fsb::batch_max_clusters(c, L.acc);
@@ -139,7 +140,10 @@ int plan_batch(fsb_batch* b, int forced) {
       const double share = static_cast<double>(slots) * work[t] / total / c;
       clusters = n == 0 ? static_cast<int>(std::ceil(share)) : static_cast<int>(share);
       clusters = clusters < 1 ? 1 : (clusters > max_clusters ? max_clusters : clusters);
+      // never more blocks than the SMs left
+      while (clusters > 1 && used + clusters * c > slots) --clusters;
     }
+    if (used + clusters * c > slots && n > 0) continue;  // no room: a wider launch serves it
     L.cluster[n] = c;
     L.blocks[n] = clusters * c;
     used += L.blocks[n];
@@ -416,8 +420,9 @@ int fsb_batch_set_plan(fsb_batch_handle b, int n_launches, const int* cluster,
   fsb::BatchLaunch& L = b->L;
   for (int i = 0; i < n_launches; ++i) {
     const int c = cluster[i];
-    if (c != 1 && c != 2 && c != 4 && c != 8)
-      return bfail(FSB_ERR_INVALID_ARG, "launch %d: cluster size must be 1, 2, 4 or 8", i);
+    if (c < 1 || c > fsb::kMaxBatchCluster)
+      return bfail(FSB_ERR_INVALID_ARG, "launch %d: cluster size must be 1 to %d", i,
+                   fsb::kMaxBatchCluster);
     if (i > 0 && c >= cluster[i - 1])
       return bfail(FSB_ERR_INVALID_ARG, "launches must be in decreasing cluster size");
     if (blocks[i] < c || blocks[i] % c)
@@ -429,9 +434,9 @@ int fsb_batch_set_plan(fsb_batch_handle b, int n_launches, const int* cluster,
   // every multi-block queue needs a launch of at least its cluster size (a
   // launch serves its own queue, then the smaller ones)
   for (int t = 0; t < fsb::kBatchQueues - 1; ++t)
-    if (L.queue_lo[t + 1] > L.queue_lo[t] && cluster[0] < (8 >> t))
+    if (L.queue_lo[t + 1] > L.queue_lo[t] && cluster[0] < fsb::kMaxBatchCluster - t)
       return bfail(FSB_ERR_INVALID_ARG, "schools need clusters of %d blocks; the widest launch "
-                   "has %d", 8 >> t, cluster[0]);
+                   "has %d", fsb::kMaxBatchCluster - t, cluster[0]);
   BCUDA(cudaStreamSynchronize(b->stream));
   L.n_launches = n_launches;
   for (int i = 0; i < n_launches; ++i) {

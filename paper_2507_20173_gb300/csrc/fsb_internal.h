@@ -163,19 +163,20 @@ uint64_t resident_max_slice(int fpt, int block);
 int resident_blocks_per_sm(int fpt, int acc, int block, int swim_mode);
 size_t resident_smem_bytes(uint64_t slice);
 
-// Work queues of a batch: queue t (t = 0, 1, 2) holds the schools run on
-// whole clusters of 8 >> t blocks, queue 3 the schools one block runs; each
+// Work queues of a batch: queue t (t = 0 .. 6) holds the schools run on
+// whole clusters of 8 - t blocks, queue 7 the schools one block runs; each
 // queue largest first.  One counter per queue, zeroed before every call.
-constexpr int kBatchQueues = 4;
-constexpr int kBatchMaxLaunches = 4;
+constexpr int kMaxBatchCluster = 8;  // widest cluster of a batch (portable limit)
+constexpr int kBatchQueues = kMaxBatchCluster;
+constexpr int kBatchMaxLaunches = kMaxBatchCluster;
 struct alignas(16) BatchCtl {
   unsigned next[kBatchQueues];
   int status;     // debug build: a failed invariant check (FSB_ERR_STATE)
   unsigned site;  // ... and where
 };
 
-// Queue of the schools that need clusters of c blocks (c = 1, 2, 4, 8).
-inline int batch_queue_of(int c) { return c >= 8 ? 0 : c >= 4 ? 1 : c >= 2 ? 2 : 3; }
+// Queue of the schools that need clusters of c blocks (c = 1 .. 8).
+inline int batch_queue_of(int c) { return c >= 8 ? 0 : (c <= 1 ? 7 : 8 - c); }
 
 // Launch description of the batched (many schools) kernel, binary32 state.
 struct BatchLaunch {
@@ -185,7 +186,7 @@ struct BatchLaunch {
   void* pv;
   const unsigned long long* offsets;  // device, n_schools + 1
   const unsigned long long* seeds;    // device, n_schools
-  const uint32_t* order;              // device, queues 0..3 back to back
+  const uint32_t* order;              // device, queues 0..7 back to back
   uint32_t queue_lo[kBatchQueues + 1];  // queue t is order[queue_lo[t] .. queue_lo[t + 1])
   uint32_t n_schools;
   double pond_half, step, w0, w_min, w_max;
@@ -212,6 +213,8 @@ struct BatchLaunch {
 // join[0..]).
 cudaError_t launch_batch(const BatchLaunch& L, cudaStream_t s, const cudaStream_t* side,
                          cudaEvent_t fork, const cudaEvent_t* join);
+// The batch kernels for clusters of 5 to 8 blocks (fsb_batch_wide.cu).
+const void* batch_kernel_wide(int cluster, int acc, bool var);
 int batch_max_clusters(int cluster, int acc);
 uint64_t batch_block_capacity();
 // Host side: completes the barycentre sums of `count` records copied out of

@@ -62,7 +62,7 @@ def check_batch(tmpl, offsets, seeds, got, stats, steps, precision):
                                "school %d" % k)
 
 
-@pytest.mark.parametrize("cluster", [2, 4, 8])
+@pytest.mark.parametrize("cluster", [2, 3, 4, 5, 6, 7, 8])
 def test_edge_size_batch_every_cluster_size(cluster):
     sizes = np.array(EDGE_SIZES, dtype=np.uint64)
     if cluster * 8192 < sizes.max():
@@ -172,6 +172,9 @@ def test_batch_argument_errors():
     with pytest.raises(fsb.FsbError) as e:
         fsb.fsb_batch_set_cluster(b, 1)          # 10000 fish do not fit one block
     assert e.value.status == fsb.FSB_ERR_UNSUPPORTED
+    with pytest.raises(fsb.FsbError) as e:
+        fsb.fsb_batch_set_cluster(b, 9)          # beyond the widest cluster
+    assert e.value.status == fsb.FSB_ERR_INVALID_ARG
     fsb.fsb_batch_step(b, 2)
     fsb.fsb_batch_destroy(b)
 
@@ -189,10 +192,11 @@ def test_default_plan_runs_each_school_on_the_cluster_that_holds_it():
     ts, state = make_state(offsets[-1])
     b = fsb.fsb_batch_create(tmpl, offsets, seeds, state, init=True)
     plan = fsb.fsb_batch_plan(b)
-    need = [1 if n <= 8192 else 2 if n <= 16384 else 4 if n <= 32768 else 8 for n in sizes]
-    assert plan["queue_schools"] == {c: need.count(c) for c in (8, 4, 2, 1)}
+    need = [max(1, -(-int(n) // 8192)) for n in sizes]   # blocks of 8192 fish that hold it
+    assert plan["queue_schools"] == {c: need.count(c) for c in range(8, 0, -1)}
     clusters = [l["cluster"] for l in plan["launches"]]
-    assert clusters[:3] == [8, 4, 2] and clusters == sorted(clusters, reverse=True)
+    assert clusters[0] == max(need) and clusters == sorted(clusters, reverse=True)
+    assert all(need.count(c) > 0 for c in clusters if c > 1)
     for l in plan["launches"]:
         assert l["blocks"] >= l["cluster"] and l["blocks"] % l["cluster"] == 0
     info = fsb.fsb_batch_info(b)
@@ -211,7 +215,7 @@ def test_forced_cluster_size_and_back_to_the_default_plan():
     tmpl = fsb.fsb_config_init(1, 0)
     ts, state = make_state(offsets[-1])
     b = fsb.fsb_batch_create(tmpl, offsets, seeds, state, init=True)
-    assert [l["cluster"] for l in fsb.fsb_batch_plan(b)["launches"]][:2] == [4, 2]
+    assert [l["cluster"] for l in fsb.fsb_batch_plan(b)["launches"]][:3] == [4, 3, 2]
     fsb.fsb_batch_set_cluster(b, 8)
     plan = fsb.fsb_batch_plan(b)
     assert plan["launches"][0]["cluster"] == 8 and plan["queue_schools"][8] == 3
@@ -220,7 +224,8 @@ def test_forced_cluster_size_and_back_to_the_default_plan():
     assert e.value.status == fsb.FSB_ERR_UNSUPPORTED
     assert fsb.fsb_batch_plan(b)["launches"][0]["cluster"] == 8   # unchanged
     fsb.fsb_batch_set_cluster(b, 0)
-    assert fsb.fsb_batch_plan(b)["queue_schools"] == {8: 0, 4: 2, 2: 1, 1: 1}
+    assert fsb.fsb_batch_plan(b)["queue_schools"] == {8: 0, 7: 0, 6: 0, 5: 0, 4: 1, 3: 1,
+                                                      2: 1, 1: 1}
     stats = np.zeros(sizes.size * 4, fsb.STATS_DTYPE)
     fsb.fsb_batch_step(b, 4, stats)
     fsb.fsb_batch_destroy(b)
