@@ -9,7 +9,8 @@
 // per step -- the eat of step p fused with the swim of step p + 1, as in the
 // streaming kernel -- so the step's code stays small and a school of a few
 // hundred fish costs little more than its own pairs.  A school goes to the
-// queue of the smallest cluster that holds it (8, 4, 2 or 1 blocks):
+// queue of the narrowest cluster that holds it (ceil(n / 8192) blocks, 1 to
+// 8, so every block is at least half full):
 //   - a cluster first takes schools from the queue of its own size, then
 //     from the queues of smaller multi-block clusters; the warps of its C
 //     blocks combine the per-step maxima by atomics in rank 0's shared
@@ -26,9 +27,12 @@
 // so no block can be left waiting for another.
 //
 // One persistent launch per cluster size in use runs concurrently with the
-// others, each on a share of the SMs in proportion to its queue's fish (a
-// launch of single blocks takes the SMs the clusters leave over); all of
-// them share the queues, so the launches that finish first help the rest.
+// others, each on a share of the SMs in proportion to its queue's weighted
+// fish (a launch of single blocks takes the SMs the clusters leave over);
+// all of them share the queues, so the launches that finish first help the
+// rest.  The kernel itself is in fsb_batch_kernel.cuh: this file
+// instantiates it for clusters of 1 to 4 blocks, fsb_batch_wide.cu for 5 to
+// 8, so the halves compile in parallel.
 #include <cstdint>
 #include <cstring>
 
