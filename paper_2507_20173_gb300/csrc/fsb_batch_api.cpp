@@ -94,12 +94,20 @@ int plan_batch(fsb_batch* b, int forced) {
                  "largest school (%llu fish) exceeds a cluster of %d blocks (%llu fish)",
                  static_cast<unsigned long long>(b->max_school), widest,
                  static_cast<unsigned long long>(widest * cap));
+  // the narrowest resident width at least c (0: none up to the widest)
+  int width_for[fsb::kMaxBatchCluster + 1] = {};
+  for (int c = fsb::kMaxBatchCluster, next = 0; c >= 1; --c) {
+    if (c == 1 || fsb::batch_max_clusters(c, b->L.acc) >= 1) next = c;
+    width_for[c] = next;
+  }
   std::vector<uint32_t> queue[fsb::kBatchQueues];
   uint64_t fish[fsb::kBatchQueues] = {};
   for (uint32_t k : b->sizes_sorted) {
     const uint64_t n = b->offsets[k + 1] - b->offsets[k];
     const int need = static_cast<int>((n + cap - 1) / cap);  // blocks that hold it
-    const int t = fsb::batch_queue_of(need <= 1 ? 1 : (forced ? forced : need));
+    const int c = need <= 1 ? 1 : (forced ? forced : width_for[need]);
+    if (c < 1) return bfail(FSB_ERR_UNSUPPORTED, "no resident cluster holds %d blocks", need);
+    const int t = fsb::batch_queue_of(c);
     queue[t].push_back(k);
     fish[t] += n;
   }
