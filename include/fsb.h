@@ -269,8 +269,8 @@ int fsb_batch_step(fsb_batch_handle b, uint32_t n_steps, fsb_step_stats* stats);
  *   0 (default): each school runs on the smallest cluster (1 to 8 blocks of
  *     8192 fish) that holds it.  One persistent launch per cluster size in
  *     use runs concurrently with the others, each on a share of the SMs
- *     proportional to its schools' fish; single-block schools take the SMs
- *     left over, and every launch helps with the schools of smaller clusters
+ *     proportional to its schools' fish times a measured cost per fish of
+ *     that width; single-block schools take the SMs left over, and every launch helps with the schools of smaller clusters
  *     once its own are done.
  *   1 to 8: every school larger than one block runs on clusters of this
  *     size (one launch on every SM it can hold, single blocks beside it).

@@ -701,7 +701,10 @@ int fsb_create(const fsb_config* cfg, const fsb_state_dev* buffers, const fsb_st
       FSB_CUDA(cudaMalloc(&h->rctl, sizeof(fsb::ResCtl)));
       R.rctl = h->rctl;
     }
+    // per-call scratch for calls of up to 1024 steps, so that such a call
+    // allocates nothing (a longer one grows it, synchronising once)
     int r = ensure_ring(h, 1024);
+    if (r == FSB_OK && h->path == FSB_PATH_RESIDENT) r = ensure_sums(h, 1024);
     if (r != FSB_OK) return r;
     StreamLaunch& L2 = h->launch;
 
