@@ -265,6 +265,46 @@ def cpu_oracle_rate(n_fish, seed, steps, collective=False):
     return n_fish * steps / dt, dt
 
 
+def host_cpu():
+    """The host's CPU model (lscpu's "Model name", else /proc/cpuinfo's
+    "model name", else the machine type) and its core counts."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None and os.path.exists("/proc/cpuinfo"):
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    import platform
+    return {"model": model or platform.machine(), "machine": platform.machine(),
+            "nproc": os.cpu_count(), "usable": len(os.sched_getaffinity(0))}
+
+
+def cpu_openmp_rate(n_fish, seed, seconds=8.0):
+    """Time the oracle's step on every host core (its per-fish loops on
+    OpenMP threads, the paper's parallelisation): a two-step probe sizes a
+    run of about `seconds`.  Returns (rate, seconds, steps, threads)."""
+    import oracle
+    threads = len(os.sched_getaffinity(0))
+    cfg = oracle.Config(n_fish=n_fish, seed=seed)
+    school = oracle.init(cfg)
+    t0 = time.perf_counter()
+    oracle.run_omp(cfg, school, 0, 2, threads=threads)
+    per_step = (time.perf_counter() - t0) / 2
+    steps = max(1, min(100_000, int(round(seconds / per_step))))
+    t0 = time.perf_counter()
+    oracle.run_omp(cfg, school, 2, steps, threads=threads)
+    dt = time.perf_counter() - t0
+    return n_fish * steps / dt, dt, steps, threads
+
+
 def run_batch(args, world, rank, local, pg):
     """The ragged ensemble (4096 schools, log-uniform sizes in [256, 65536],
     T = 500): one graph-captured persistent launch, against the same schools
@@ -714,7 +754,16 @@ def run_ours(args, world, rank, local, pg):
         rate, dt = cpu_oracle_rate(cn, wl.seed, cs, collective=coll)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "%d fish x %d steps of the %s school (same init rule), %.1f s"
-                         % (cn, cs, wl.name, dt)}
+                         % (cn, cs, wl.name, dt), "host": host_cpu()}
+        if not coll:
+            # the multi-core CPU baseline beside it: the same per-fish step
+            # on every host core
+            orate, odt, osteps, othreads = cpu_openmp_rate(cn, wl.seed)
+            cpu["openmp"] = {"value": orate, "unit": UNIT, "cores": othreads,
+                             "kind": "oracle step, per-fish loops on OpenMP threads "
+                                     "(static schedule, max reductions)",
+                             "sample": "%d fish x %d steps of the %s school, %.1f s"
+                                       % (cn, osteps, wl.name, odt)}
 
     clocks = clk.summary()
     if roof.get("bound") == "alu":

@@ -9,7 +9,9 @@ method's arithmetic.
 The arithmetic lives in plain C (``fsb_oracle.c``, ``philox.c``), built with
 ``-O2 -ffp-contract=off -fno-fast-math`` so that every binary32 / binary64
 operation rounds once, to nearest-even.  This module only marshals numpy
-arrays into it.
+arrays into it.  ``run_omp`` is the same step with its per-fish loops on
+OpenMP threads (the paper's own parallelisation), a multi-core CPU baseline
+for ``bench.py``; ``run`` stays the reference every test compares against.
 
 Paper passages followed: Sec. 2.1.1 (Fish structure, initialisation,
 objective = distance to the pond centre), Sec. 2.1.2 (200x200 pond, random
@@ -57,16 +59,20 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB_PATH) >= newest_src):
         return _LIB_PATH
     objs = []
+    # -fopenmp only enables fsbo_run_omp_*, the multi-core baseline; the
+    # serial functions carry no OpenMP construct
     units = [("philox.c", [], "philox.o"), ("collective.c", [], "collective.o"),
-             ("fsb_oracle.c", ["-DFSBO_REAL=float", "-DFSBO_SFX=f32"], "oracle_f32.o"),
-             ("fsb_oracle.c", ["-DFSBO_REAL=double", "-DFSBO_SFX=f64"], "oracle_f64.o")]
+             ("fsb_oracle.c", ["-DFSBO_REAL=float", "-DFSBO_SFX=f32", "-fopenmp"],
+              "oracle_f32.o"),
+             ("fsb_oracle.c", ["-DFSBO_REAL=double", "-DFSBO_SFX=f64", "-fopenmp"],
+              "oracle_f64.o")]
     for src, defs, obj in units:
         out = os.path.join(_BUILD, obj)
         subprocess.run(["gcc", *CFLAGS, *defs, "-c", os.path.join(_HERE, src),
                         "-o", out], check=True)
         objs.append(out)
     tmp = _LIB_PATH + ".tmp%d" % os.getpid()
-    subprocess.run(["gcc", "-shared", *objs, "-o", tmp, "-lm"], check=True)
+    subprocess.run(["gcc", "-shared", "-fopenmp", *objs, "-o", tmp, "-lm"], check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -127,6 +133,9 @@ def lib():
             getattr(L, "fsbo_run_" + sfx).argtypes = [cfgp, ctypes.c_uint64,
                                                       ctypes.c_uint32, P, P, P]
             getattr(L, "fsbo_run_" + sfx).restype = ctypes.c_int
+            getattr(L, "fsbo_run_omp_" + sfx).argtypes = [cfgp, ctypes.c_uint64,
+                                                          ctypes.c_uint32, P, P, ctypes.c_int]
+            getattr(L, "fsbo_run_omp_" + sfx).restype = ctypes.c_int
             getattr(L, "fsbo_track_fish_" + sfx).argtypes = [
                 cfgp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, P, P, P, P]
         L.fsbo_eat_fish_f32.argtypes = [cfgp, ctypes.c_float, ctypes.c_uint32, P, P, P]
@@ -205,6 +214,23 @@ def run(cfg: Config, school: np.ndarray, t0: int, n_steps: int,
     c = cfg.c()
     rc = getattr(lib(), "fsbo_run_" + precision)(
         ctypes.byref(c), t0, n_steps, _ptr(school), _ptr(stats), dptr)
+    if rc != 0:
+        raise ValueError("oracle rejected the arguments")
+    return stats
+
+
+def run_omp(cfg: Config, school: np.ndarray, t0: int, n_steps: int,
+            threads: int = 0) -> np.ndarray:
+    """``run`` with the per-fish loops on ``threads`` OpenMP threads (0: the
+    OpenMP default), the paper's own parallelisation (Sec. 2.3) as a
+    multi-core CPU baseline.  Same per-fish state and maxima as ``run``;
+    barycentre sums equal to rounding."""
+    precision = "f32" if school.dtype == FISH_F32 else "f64"
+    assert school.dtype == _fish_dtype(precision) and school.size == cfg.n_fish
+    stats = np.zeros(n_steps, dtype=STATS)
+    c = cfg.c()
+    rc = getattr(lib(), "fsbo_run_omp_" + precision)(
+        ctypes.byref(c), t0, n_steps, _ptr(school), _ptr(stats), int(threads))
     if rc != 0:
         raise ValueError("oracle rejected the arguments")
     return stats

@@ -384,6 +384,115 @@ int FN(fsbo_run)(const fsbo_config* cfg, uint64_t t0, uint32_t n_steps,
     return 0;
 }
 
+#ifdef _OPENMP
+#include <omp.h>
+
+/* fsbo_run's step with its per-fish loops shared among OpenMP threads, the
+ * parallelisation the paper studies (Sec. 2.3): a static schedule, and the
+ * two maxima taken by OpenMP max reductions (Sec. 2.3.2's reduction
+ * construct).  Each fish's arithmetic is fsbo_run's, so the per-fish state
+ * and both maxima equal fsbo_run's bit for bit; the barycentre sums are
+ * compensated per thread and the partials added in thread order, so they
+ * agree with fsbo_run's to a few units in 2^-53 of the sum of magnitudes.
+ * A multi-core CPU baseline only: no injected draws and no collective
+ * movements (returns -1).  n_threads <= 0 takes OpenMP's default. */
+int FN(fsbo_run_omp)(const fsbo_config* cfg, uint64_t t0, uint32_t n_steps,
+                     FISH* school, fsbo_stats* stats, int n_threads)
+{
+    if (!config_ok(cfg) || !school || cfg->collective_mode != 0) return -1;
+    if (t0 + (uint64_t)n_steps > 0xFFFFFFFFull) return -1;
+    const int64_t N = (int64_t)cfg->n_fish;
+    const real P = (real)cfg->pond_half;
+    const real s = (real)cfg->step;
+    const real w0 = (real)cfg->w0;
+    const real wmin = (real)cfg->w_min;
+    const real wmax = (real)cfg->w_max;
+    const int nt = n_threads > 0 ? n_threads : omp_get_max_threads();
+
+    real* delta = (real*)malloc(sizeof(real) * (size_t)N);
+    csum* part = (csum*)calloc((size_t)nt * 5, sizeof(csum));
+    if (!delta || !part) {
+        free(delta);
+        free(part);
+        return -1;
+    }
+
+    for (uint32_t k = 0; k < n_steps; ++k) {
+        const uint32_t t = (uint32_t)(t0 + k + 1);
+
+        /* swim, objective, delta; max |delta| and the eat() statistic */
+        double M = 0.0;
+        double eat_max = -INFINITY;
+#pragma omp parallel for schedule(static) num_threads(nt) reduction(max : M, eat_max)
+        for (int64_t i = 0; i < N; ++i) {
+            uint32_t r[2];
+            fsbo_swim_words(cfg, (uint64_t)i, t, r);
+            delta[i] = swim_one(&school[i], r[0], r[1], P,
+                                swim_width(cfg, s, w0, school[i].weight));
+            const double a = fabs((double)delta[i]);
+            if (a > M) M = a;
+            const double diff = (double)(school[i].prevObjective -
+                                         school[i].currentObjective);
+            if (diff > eat_max) eat_max = diff;
+        }
+
+        /* eat */
+        if (M > 0.0 && cfg->feed_mode == 0) {
+            const real Mr = (real)M;
+#pragma omp parallel for schedule(static) num_threads(nt)
+            for (int64_t i = 0; i < N; ++i)
+                school[i].weight = eat_one(school[i].weight, delta[i], Mr, wmin, wmax);
+        } else if (cfg->feed_mode == 1 && eat_max > 0.0) {
+            const real E = (real)eat_max;
+#pragma omp parallel for schedule(static) num_threads(nt)
+            for (int64_t i = 0; i < N; ++i)
+                school[i].weight = eat_one(school[i].weight,
+                                           school[i].prevObjective -
+                                               school[i].currentObjective,
+                                           E, wmin, wmax);
+        }
+
+        /* barycentre sums: one compensated partial per thread */
+        if (stats) {
+            memset(part, 0, sizeof(csum) * (size_t)nt * 5);
+#pragma omp parallel num_threads(nt)
+            {
+                csum q[5] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}};
+#pragma omp for schedule(static)
+                for (int64_t i = 0; i < N; ++i) {
+                    const double w = (double)school[i].weight;
+                    const double x = (double)school[i].x;
+                    const double y = (double)school[i].y;
+                    csum_add(&q[0], w);
+                    csum_add_product(&q[1], w, x);
+                    csum_add_product(&q[2], w, y);
+                    csum_add_product(&q[3], w, fabs(x));
+                    csum_add_product(&q[4], w, fabs(y));
+                }
+                memcpy(&part[(size_t)omp_get_thread_num() * 5], q, sizeof(q));
+            }
+            csum tot[5] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}};
+            for (int th = 0; th < nt; ++th)
+                for (int j = 0; j < 5; ++j) {
+                    csum_add(&tot[j], part[th * 5 + j].s);
+                    csum_add(&tot[j], part[th * 5 + j].c);
+                }
+            memset(&stats[k], 0, sizeof(stats[k]));
+            stats[k].max_abs_delta = M;
+            stats[k].eat_max_diff = eat_max;
+            stats[k].sum_w = tot[0].s + tot[0].c;
+            stats[k].sum_wx = tot[1].s + tot[1].c;
+            stats[k].sum_wy = tot[2].s + tot[2].c;
+            stats[k].sum_abs_wx = tot[3].s + tot[3].c;
+            stats[k].sum_abs_wy = tot[4].s + tot[4].c;
+        }
+    }
+    free(delta);
+    free(part);
+    return 0;
+}
+#endif
+
 /* Positions do not depend on weights only in swim_mode 0; this helper
  * follows one fish in that mode (the fish's weight is not touched). */
 void FN(fsbo_track_fish)(const fsbo_config* cfg, uint64_t i, uint64_t t0,

@@ -102,6 +102,15 @@ int fsbo_run_f64(const fsbo_config* cfg, uint64_t t0, uint32_t n_steps,
                  fsbo_fish_f64* school, fsbo_stats* stats,
                  const uint32_t* draws);
 
+/* fsbo_run with the per-fish loops on n_threads OpenMP threads (<= 0: the
+ * OpenMP default), the multi-core CPU baseline: per-fish state and maxima
+ * equal fsbo_run's bit for bit, barycentre sums to rounding.  No injected
+ * draws; collective_mode 1 -> -1. */
+int fsbo_run_omp_f32(const fsbo_config* cfg, uint64_t t0, uint32_t n_steps,
+                     fsbo_fish_f32* school, fsbo_stats* stats, int n_threads);
+int fsbo_run_omp_f64(const fsbo_config* cfg, uint64_t t0, uint32_t n_steps,
+                     fsbo_fish_f64* school, fsbo_stats* stats, int n_threads);
+
 /* One fish's positions and deltas over n_steps, starting from `fish` at
  * step t0 (positions do not depend on weights, so one fish can be followed
  * alone).  out_* hold n_steps values each; `fish` is advanced in place but
