@@ -364,27 +364,52 @@ def run_batch(args, world, rank, local, pg):
 
     per_school = None
     if not args.no_per_school:
+        # a stream of their own, so the calls can also be captured in a graph
+        ps_stream = torch.cuda.Stream()
         handles = []
         for k in range(n_schools):
             lo, hi = int(offsets[k]), int(offsets[k + 1])
             cfg = fsb.fsb_config_init(hi - lo, int(seeds[k]), school_id=k, precision=prec)
             bufs = fsb.FsbStateDev(*(t_.data_ptr() + 4 * lo for t_ in ts))
-            handles.append(fsb.fsb_create(cfg, bufs, None, 0, stream.cuda_stream))
+            handles.append(fsb.fsb_create(cfg, bufs, None, 0, ps_stream.cuda_stream))
         for h in handles:
             fsb.fsb_step(h, warmup)
         barrier()
-        start.record(stream)
+        start.record(ps_stream)
         for h in handles:
             fsb.fsb_step(h, steps)
-        stop.record(stream)
+        stop.record(ps_stream)
         torch.cuda.synchronize()
         ps_ms = start.elapsed_time(stop)
-        for h in handles:
-            fsb.fsb_destroy(h)
         per_school = {"value": total * steps / (ps_ms / 1e3), "unit": UNIT,
                       "ms": ps_ms, "launches": n_schools,
                       "what": "one fsb_step(T) launch per school on the single-school "
                               "path (library's choice: resident), serially on one stream"}
+        # the same calls captured once into a CUDA graph and replayed: no
+        # host launch cost between schools (a replay repeats the captured
+        # steps' counters on the evolved state; the work per school is the
+        # same)
+        try:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=ps_stream):
+                for h in handles:
+                    fsb.fsb_step(h, steps)
+            g.replay()
+            torch.cuda.synchronize()
+            start.record(ps_stream)
+            g.replay()
+            stop.record(ps_stream)
+            torch.cuda.synchronize()
+            gms = start.elapsed_time(stop)
+            per_school["graph"] = {"value": total * steps / (gms / 1e3), "unit": UNIT,
+                                   "ms": gms, "what": "the per-school calls captured in "
+                                                     "one CUDA graph, one replay timed"}
+            del g
+        except Exception as e:  # report, do not fail the bench line
+            torch.cuda.synchronize()
+            per_school["graph"] = {"unavailable": str(e).splitlines()[0][:200]}
+        for h in handles:
+            fsb.fsb_destroy(h)
     clocks = clk.summary()
     ipfs = alu_instr_per_fish_step("batch", args.precision)
     avg_s = (kms / kl) / 1e3 if kl else None
@@ -413,6 +438,8 @@ def run_batch(args, world, rank, local, pg):
                 "per_school": per_school,
                 "batched_over_per_school": (value / world) / per_school["value"]
                 if per_school else None,
+                "batched_over_per_school_graph": (value / world) / per_school["graph"]["value"]
+                if per_school and "value" in per_school.get("graph", {}) else None,
                 "cpu_baseline": None, "e2e": None,
                 "gpu_launches": len(plan["launches"]) + 1, "clocks": clocks}
         print(json.dumps(line), flush=True)
