@@ -361,7 +361,10 @@ int fsb_set_fault_injection(fsb_handle h, int block, uint32_t step, uint64_t tim
  *                        shared memory, 7168 fish)
  *   resident_block       fish threads per block of the resident kernel
  *                        (multiple of 32, at most 512; one synchronisation
- *                        warp is added)
+ *                        warp is added).  The library's choice: with 4 fish
+ *                        per thread, the smallest block that fits the school
+ *                        on one block per SM; otherwise the largest block
+ *                        with a fish pair for every thread
  *   stream_stages        bulk-copy kernels: shared-memory tiles in flight per
  *                        block, 2, 3 or 4 (kernel 3: 2 or 3)
  * A combination that cannot run returns FSB_ERR_INVALID_ARG and leaves the

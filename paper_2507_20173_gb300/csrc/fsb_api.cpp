@@ -376,9 +376,23 @@ bool resident_config(int sms, int acc, int swim_mode, uint64_t n, fsb::ResidentL
     if (want_fpt && fpt != want_fpt) continue;
     const int maxb = fsb::resident_max_block(fpt);
     if (want_block && (want_block % 32 || want_block > maxb)) return false;
+    // Four fish per thread without a requested block: the smallest block
+    // (a multiple of 32 threads) that holds the school on at most one block
+    // per SM.  A step costs the slowest block's pass plus the grid barrier,
+    // and on GB300 it shrinks with the blocks: 10^4 fish took 1.6 us per
+    // step on 79 blocks of 32 fish threads against 1.9-2.1 us on 10 blocks
+    // of 512, 10^3 fish 1.6 us on 8 blocks of 32 against 5.0 us on one of
+    // 512.  A school too large for that falls through to the rule below.
+    int small_block = 0;
+    if (fpt == 4 && !want_block) {
+      const uint64_t per_sm = (n + static_cast<uint64_t>(sms) - 1) / static_cast<uint64_t>(sms);
+      const uint64_t threads = ((per_sm + fpt - 1) / fpt + 31) / 32 * 32;
+      if (threads <= static_cast<uint64_t>(maxb)) small_block = threads < 32 ? 32 : static_cast<int>(threads);
+    }
     // a block holds at most fpt fish per thread of its largest block (or of
     // the requested one), within the shared memory
-    const uint64_t per_block = fsb::resident_max_slice(fpt, want_block ? want_block : maxb);
+    const int cap_block = want_block ? want_block : (small_block ? small_block : maxb);
+    const uint64_t per_block = fsb::resident_max_slice(fpt, cap_block);
     uint64_t grid = (n + per_block - 1) / per_block;
     if (grid > static_cast<uint64_t>(sms)) continue;
     if (grid < 1) grid = 1;
@@ -389,13 +403,15 @@ bool resident_config(int sms, int acc, int swim_mode, uint64_t n, fsb::ResidentL
     const uint64_t floor_fish = static_cast<uint64_t>(fpt) * 256;
     const uint64_t spread = (n + floor_fish - 1) / floor_fish;
     const uint64_t most = spread < static_cast<uint64_t>(sms) ? spread : sms;
-    if (grid < most) grid = most;
+    if (!small_block && grid < most) grid = most;
     // even, so no fish pair (one swim block) straddles two blocks
     const uint64_t slice = ((n + grid - 1) / grid + 1) & ~1ull;
-    // the requested block, else the largest one with a pair for every thread
+    // the requested block, the small block, else the largest one with a
+    // pair for every thread
     const uint64_t pairs32 = ((slice / 2 + 31) / 32) * 32;
     const int block = want_block ? want_block
-                                 : static_cast<int>(pairs32 < static_cast<uint64_t>(maxb) ? pairs32 : maxb);
+                      : small_block ? small_block
+                                    : static_cast<int>(pairs32 < static_cast<uint64_t>(maxb) ? pairs32 : maxb);
     if (slice > fsb::resident_max_slice(fpt, block)) continue;
     if (fsb::resident_blocks_per_sm(fpt, acc, block, swim_mode) < 1) continue;
     R->fpt = fpt;
