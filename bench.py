@@ -71,7 +71,7 @@ def parse_args():
     ap.add_argument("--reference-fish", type=int, default=1 << 22,
                     help="fish per bench step of the CPU reference arm")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--e2e-runs", type=int, default=3,
+    ap.add_argument("--e2e-runs", type=int, default=5,
                     help="end-to-end runs; the median is reported")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
