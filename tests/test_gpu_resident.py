@@ -103,6 +103,22 @@ def test_auto_path_picks_resident_for_small_binary32_schools():
     s.destroy()
 
 
+@pytest.mark.parametrize("n,block", [(1000, 32), (10_000, 32), (30_000, 64), (60_000, 128),
+                                     (100_000, 192), (1 << 20, 512)])
+def test_default_block_spreads_small_schools_over_the_sms(n, block):
+    """A school that fits at four fish per thread takes the smallest block
+    (a multiple of 32 fish threads) that puts it on at most one block per SM;
+    a larger one keeps a pair for every thread of 512."""
+    s = fsb.School.create(fsb.fsb_config_init(n, 1))
+    t = fsb.fsb_get_tuning(s.handle)
+    s.destroy()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    if sms != 152:
+        pytest.skip("block table measured for 152 SMs")
+    assert t["resident_block"] == block
+    assert t["resident_fpt"] == (4 if n <= 152 * 2048 else 16)
+
+
 def test_missing_barrier_arrival_times_out_without_hanging():
     """Failure detection without a GPU fault: one block withholds its
     arrival at a grid barrier (set from the host).  Every bounded wait runs
