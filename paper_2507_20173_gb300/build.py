@@ -47,7 +47,7 @@ def _headers() -> list[str]:
                  for f in os.listdir(os.path.join(ROOT, "include"))]
 
 
-def _compile(src: str, extra: list[str], out_dir: str = BUILD) -> str:
+def _compile(src: str, extra: list[str], out_dir: str = BUILD) -> tuple[str, str]:
     obj = os.path.join(out_dir, os.path.basename(src) + ".o")
     cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
     if src.endswith(".cpp"):
@@ -55,7 +55,7 @@ def _compile(src: str, extra: list[str], out_dir: str = BUILD) -> str:
     proc = subprocess.run(cmd, capture_output=True, text=True)
     if proc.returncode != 0:
         raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, " ".join(cmd), proc.stderr))
-    return obj
+    return obj, proc.stderr
 
 
 def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None,
@@ -70,7 +70,12 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     if not force and not extra and os.path.exists(lib) and os.path.getmtime(lib) >= newest:
         return lib
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, flags, out_dir), srcs))
+        done = list(ex.map(lambda s: _compile(s, flags, out_dir), srcs))
+    objs = [obj for obj, _ in done]
+    if verbose:  # compiler remarks, e.g. ptxas -v register and spill counts
+        for obj, log in done:
+            if log.strip():
+                print("== %s\n%s" % (os.path.basename(obj), log.rstrip()), file=sys.stderr)
     tmp = lib + ".tmp%d" % os.getpid()
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcuda"]
     proc = subprocess.run(cmd, capture_output=True, text=True)
