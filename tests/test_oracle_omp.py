@@ -44,3 +44,15 @@ def test_openmp_run_refuses_the_collective_movements():
     school = oracle.init(cfg, "f32")
     with pytest.raises(ValueError):
         oracle.run_omp(cfg, school, 0, 1)
+
+
+def test_bench_multicore_baseline_reports_its_threads():
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    rate, seconds, steps, threads = bench.cpu_openmp_rate(4096, 2, seconds=0.2)
+    assert rate > 0 and seconds > 0 and steps >= 1
+    assert threads == len(os.sched_getaffinity(0))
+    host = bench.host_cpu()
+    assert host["usable"] == threads and host["nproc"] >= threads and host["model"]
