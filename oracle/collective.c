@@ -7,15 +7,15 @@
  * nearest to v * 2^k (ties to even), and integers add exactly in any order
  * (reproducible summation by pre-rounding, after Demmel and Nguyen, with a
  * grid fixed by the school's configuration).  The grid exponent k is the
- * largest integer in [-100, 100] with max(n, 2^19) * bound * 2^k <= 2^62:
- * n terms bounded by `bound` stay below 2^62 in sum and each below 2^43.
+ * largest integer in [-100, 100] with n * bound * 2^k <= 2^62: the sum of n
+ * terms bounded by `bound` stays below 2^62 in magnitude.
  */
 #include "fsb_oracle.h"
 
 int fsbo_grid_exponent(uint64_t n, double bound)
 {
     const double lim = 4611686018427387904.0;  /* 2^62 */
-    double t = (double)(n < 524288u ? 524288u : n) * bound;
+    double t = (double)n * bound;
     int k = 0;
     if (t > lim) {
         while (t > lim && k > -100) {

@@ -63,8 +63,8 @@ typedef struct {
 } fsbo_stats;
 
 /* Fixed-point grid exponent of an exact school sum (collective movements):
- * the largest k in [-100, 100] with max(n, 2^19) * bound * 2^k <= 2^62
- * (the sum of n terms below 2^62, each term below 2^43). */
+ * the largest k in [-100, 100] with n * bound * 2^k <= 2^62 (the sum of
+ * n terms bounded by `bound` stays below 2^62). */
 int fsbo_grid_exponent(uint64_t n, double bound);
 
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): out = bijection of ctr
