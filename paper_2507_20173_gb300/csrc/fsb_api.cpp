@@ -73,12 +73,12 @@ int validate_config(const fsb_config* c) {
   return FSB_OK;
 }
 
-// Largest k in [-100, 100] with max(n, 2^19) * bound * 2^k <= 2^62: the
-// grid of an exact school sum of n terms bounded by `bound` (collective
-// movements); the sum stays below 2^62 and each term below 2^43.
+// Largest k in [-100, 100] with n * bound * 2^k <= 2^62: the grid of an
+// exact school sum of n terms bounded by `bound` (collective movements); the
+// sum stays below 2^62.
 int grid_exponent(uint64_t n, double bound) {
   const double lim = 4611686018427387904.0;  // 2^62
-  double t = static_cast<double>(n < 524288u ? 524288u : n) * bound;
+  double t = static_cast<double>(n) * bound;
   int k = 0;
   if (t > lim) {
     while (t > lim && k > -100) {

@@ -49,6 +49,7 @@ struct CollArgs {
   Real s_vol;
   Real g_p, g_g, g_w;  // grid scales 2^kp, 2^kg, 2^kw (exact)
   int kp, kg;
+  int wide;            // terms may exceed 2^43 (schools below 2^19 fish)
   Ctl* ctl;
   CollPartial* partials;
   fsb_step_stats* ring;
@@ -145,8 +146,9 @@ __device__ __forceinline__ long long round_shifted(uint64_t sig, int s, bool neg
   return neg ? -sq : sq;
 }
 
-// Binary32 terms round on the FMA pipe instead.  The grid keeps every term
-// x = v * 2^k (exact: a power-of-two scaling) within 2^43, so:
+// Binary32 terms round on the FMA pipe instead.  x = v * 2^k is exact (a
+// power-of-two scaling), and the grid bounds the whole sum, so |x| <= 2^62 / N.
+// When |x| <= 2^43 (every school of at least 2^19 fish):
 //  - adding and removing C = 1.5 * 2^45 rounds x to a multiple of 2^22
 //    (x + C lies in [2^45, 2^46), where the spacing is 2^22), to nearest,
 //    ties to even: x_hi;
@@ -155,7 +157,11 @@ __device__ __forceinline__ long long round_shifted(uint64_t sig, int s, bool neg
 //    lands in [2^23, 2^24), where the spacing is 1, so the sum is rounded to
 //    an integer, ties to even, and its bits minus M's bits are that integer.
 // x_hi is a multiple of 2^22 (even), so round(x) = x_hi + round(x_lo).
-__device__ __forceinline__ long long grid_term(float v, float scale) {
+// Smaller schools (`wide`, uniform over the launch) can have terms up to
+// 2^62.  A binary32 value of magnitude 2^23 or more is already an integer:
+// its 24-bit significand shifted left by (biased exponent - 150), at most 39
+// places.  Below 2^23 the FMA-pipe rounding above applies.
+__device__ __forceinline__ long long grid_term(float v, float scale, bool wide) {
   const float x = __fmul_rn(v, scale);
   const float c = 0x1.8p45f;
   const float m = 0x1.8p23f;
@@ -163,10 +169,19 @@ __device__ __forceinline__ long long grid_term(float v, float scale) {
   const float x_lo = __fsub_rn(x, x_hi);
   const int lo = __float_as_int(__fadd_rn(x_lo, m)) - __float_as_int(m);
   const int hi = __float_as_int(__fadd_rn(__fmul_rn(x_hi, 0x1p-22f), m)) - __float_as_int(m);
-  return static_cast<long long>(hi) * (1ll << 22) + lo;
+  long long r = static_cast<long long>(hi) * (1ll << 22) + lo;
+  if (wide) {
+    const uint32_t b = __float_as_uint(x);
+    const int e = static_cast<int>((b >> 23) & 0xFFu);
+    if (e >= 150) {
+      const long long mag = static_cast<long long>((b & 0x7FFFFFu) | 0x800000u) << (e - 150);
+      r = (b >> 31) ? -mag : mag;
+    }
+  }
+  return r;
 }
 
-__device__ __forceinline__ long long grid_term(double v, double scale) {
+__device__ __forceinline__ long long grid_term(double v, double scale, bool) {
   // scale = 2^k, a normal power of two (|k| <= 100): k from its exponent bits
   const int k =
       static_cast<int>((static_cast<uint64_t>(__double_as_longlong(scale)) >> 52) & 0x7FFull) -
@@ -224,9 +239,9 @@ __device__ __forceinline__ void swim_fish(Real& x, Real& y, Real& cur, Real w, u
   maxb = mb > maxb ? mb : maxb;
   ekey = ek > ekey ? ek : ekey;
   if (g > Real(0)) {
-    q[0] += grid_term(A::mul(A::sub(x, x0), g), a.g_p);
-    q[1] += grid_term(A::mul(A::sub(y, y0), g), a.g_p);
-    q[2] += grid_term(g, a.g_g);
+    q[0] += grid_term(A::mul(A::sub(x, x0), g), a.g_p, a.wide);
+    q[1] += grid_term(A::mul(A::sub(y, y0), g), a.g_p, a.wide);
+    q[2] += grid_term(g, a.g_g, a.wide);
   }
   cur = ncur;
 }
@@ -285,7 +300,7 @@ __global__ void __launch_bounds__(kCollBlock, 4) coll_kernel(CollArgs<Real> a) {
 #pragma unroll
       for (int f = 0; f < 2; ++f) {
         if (f < nf) {
-          q[3] += grid_term(w[f], a.g_w);  // the school's weight before the first eat
+          q[3] += grid_term(w[f], a.g_w, a.wide);  // the school's weight before the first eat
           Real cur = objective(x[f], y[f]);
           pv[f] = cur;                     // prevObjective after this swim
           swim_fish(x[f], y[f], cur, w[f], r.v[2 * f], r.v[2 * f + 1], a, maxb, ekey, q);
@@ -301,9 +316,9 @@ __global__ void __launch_bounds__(kCollBlock, 4) coll_kernel(CollArgs<Real> a) {
           acc.add(w[f], x[f], y[f]);
           x[f] = A::clamp(A::add(x[f], ix), -a.ph.pond_half, a.ph.pond_half);
           y[f] = A::clamp(A::add(y[f], iy), -a.ph.pond_half, a.ph.pond_half);
-          q[0] += grid_term(w[f], a.g_w);
-          q[1] += grid_term(A::mul(w[f], x[f]), a.g_w);
-          q[2] += grid_term(A::mul(w[f], y[f]), a.g_w);
+          q[0] += grid_term(w[f], a.g_w, a.wide);
+          q[1] += grid_term(A::mul(w[f], x[f]), a.g_w, a.wide);
+          q[2] += grid_term(A::mul(w[f], y[f]), a.g_w, a.wide);
         }
       }
     } else {
@@ -577,6 +592,9 @@ CollArgs<Real> make_args(const CollLaunch& L, uint32_t n_steps) {
   a.g_w = static_cast<Real>(ldexp(1.0, L.kw));
   a.kp = L.kp;
   a.kg = L.kg;
+  // every sum of N terms is within 2^62, so a term exceeds 2^43 only when
+  // N < 2^19
+  a.wide = L.n < (1ull << 19) ? 1 : 0;
   a.ctl = L.ctl;
   a.partials = L.partials;
   a.ring = L.ring;
