@@ -431,26 +431,34 @@ int fsb_handle_path(fsb_handle h, int* path_out);
  * hosts that own all device memory through their own arena and forbid later
  * cudaMalloc, and latency-bound pipelines in which cudaMalloc / cudaFree
  * (which can synchronise the whole device) would stall their other streams.
- * It runs the same streaming kernels as fsb_step; their scratch (control
- * word, per-block reduction partials, per-step statistics ring) lives in one
- * fixed file-scope __device__ array of about 210 KB that every GPU loading
- * the library holds until the process exits.
- *   cfg         as for fsb_create (path is ignored: always streaming)
+ * It runs the same streaming kernels, in the same launch shape, as fsb_step;
+ * their scratch (control word, per-block reduction partials, per-step
+ * statistics ring) lives in one fixed file-scope __device__ array of about
+ * 210 KB that every GPU loading the library holds until the process exits.
+ *   cfg         as for fsb_create (path is ignored: always streaming;
+ *               collective_mode 1 -> FSB_ERR_UNSUPPORTED)
  *   state       caller-owned device arrays (fsb_state_dev layout) holding the
  *               school at step start_step; advanced in place
- *   start_step  the state's step counter t
+ *   start_step  the state's step counter t; t + n_steps must stay below 2^32
  *   n_steps     1 .. 4096 (the statistics ring's size in the static array);
  *               larger values return FSB_ERR_INVALID_ARG with that reason in
  *               fsb_last_error() -- split longer runs into several calls
- *   stats_out   NULL, or n_steps records in host or device memory, written
- *               in stream order (synchronise the stream before reading them)
+ *   stats_out   NULL, or n_steps records.  In device (or managed) memory they
+ *               are written in stream order and the call stays asynchronous.
+ *               In host memory the call synchronises the stream, fills them
+ *               and returns the device status (below)
+ * Device-side errors (FSB_ERR_STATE from a pass-sequence or debug-build
+ * check) are latched in the static array.  A call that synchronises (host
+ * stats_out) returns the first such error latched on that device since the
+ * last one it reported -- by an earlier asynchronous call or by itself -- and
+ * clears it; an asynchronous call returns only host-side errors.  A call
+ * whose passes found an error leaves its school partly advanced.
  * The first call on each device looks up the array's device address (set-up
  * done once per device, with that device current); make that first call
  * before any stream capture.  All calls on a device share the one array and
  * rewrite it: calls whose kernels overlap on the GPU (different streams or
  * threads) race and corrupt each other's results, so serialise them.
- * Allocates nothing (no cudaMalloc, cudaFree, graph or event creation).
- * Asynchronous on cuda_stream. */
+ * Allocates nothing (no cudaMalloc, cudaFree, graph or event creation). */
 int fsb_step_static(const fsb_config* cfg, const fsb_state_dev* state, uint64_t start_step,
                     uint32_t n_steps, fsb_step_stats* stats_out, void* cuda_stream);
 

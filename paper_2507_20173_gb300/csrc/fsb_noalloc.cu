@@ -21,6 +21,12 @@
 //     control word first, so calls whose kernels overlap on the GPU (two
 //     streams, or two host threads) race and give wrong results: serialise
 //     them, e.g. on one stream.
+//
+// Errors found on the device (a status the kernels latch in the control word)
+// cannot be returned by an asynchronous call.  The next call's first kernel
+// keeps such a status in a carried slot of the array instead of clearing it,
+// and the first later call that synchronises (one given host memory for its
+// statistics) returns it, together with its own, and clears both.
 #include <cstdint>
 #include <cstdio>
 #include <mutex>
@@ -34,13 +40,15 @@ namespace {
 
 constexpr uint32_t kStaticMaxSteps = 4096;
 constexpr uint32_t kStaticMaxBlocks = 1024;
-constexpr size_t kCtlBytes = 256;
+constexpr size_t kCtlBytes = 256;  // the control word, the carried status, the report slot
+constexpr size_t kCarriedOffset = 64;
+constexpr size_t kReportOffset = 128;
 constexpr size_t kPartialBytes = sizeof(BlockPartial) * kStaticMaxBlocks;
 constexpr size_t kRingBytes = sizeof(fsb_step_stats) * kStaticMaxSteps;
 constexpr size_t kStaticScratchBytes = kCtlBytes + kPartialBytes + kRingBytes;
 constexpr int kMaxDevices = 64;
 
-static_assert(sizeof(Ctl) <= kCtlBytes, "control word does not fit its slot");
+static_assert(sizeof(Ctl) <= kCarriedOffset, "control word does not fit its slot");
 static_assert(kPartialBytes % 256 == 0, "ring must stay 256-byte aligned");
 
 // The shared scratch.  In host code `g_static_scratch` names a host-side
@@ -48,12 +56,23 @@ static_assert(kPartialBytes % 256 == 0, "ring must stay 256-byte aligned");
 // cudaGetSymbolAddress on the device in question.
 __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-// Clears the control word at the start of every call (the array keeps the
-// previous call's contents).
-__global__ void reset_ctl_kernel(Ctl* ctl, unsigned long long start_step) {
+// Resets the control word at the start of every call (the array keeps the
+// previous call's contents).  A status the previous call latched is kept in
+// the carried slot until a synchronising call reports it.
+__global__ void reset_ctl_kernel(Ctl* ctl, int* carried, unsigned long long start_step) {
+  if (*carried == 0) *carried = ctl->status;
   Ctl c{};
   c.base_step = start_step;
   *ctl = c;
+}
+
+// End of a synchronising call: the first error latched since the last report
+// (an earlier call's, else this call's) goes to the report slot, and both
+// slots are cleared.
+__global__ void take_status_kernel(Ctl* ctl, int* carried, int* report) {
+  *report = *carried != 0 ? *carried : ctl->status;
+  *carried = 0;
+  ctl->status = 0;
 }
 
 std::mutex g_setup_mutex;
@@ -108,7 +127,7 @@ extern "C" int fsb_step_static(const fsb_config* cfg, const fsb_state_dev* state
     return fail(FSB_ERR_INVALID_ARG,
                 "fsb_step_static: n_steps exceeds the static scratch limit of 4096 steps "
                 "per call; split the call");
-  if (start_step + n_steps > 0xFFFFFFFFull)
+  if (start_step > 0xFFFFFFFFull - n_steps)
     return fail(FSB_ERR_INVALID_ARG, "fsb_step_static: step counter would pass 2^32 - 1");
   const bool dbl = cfg->precision == FSB_FP64_STATE;
   const size_t elem = dbl ? 8 : 4;
@@ -139,7 +158,10 @@ extern "C" int fsb_step_static(const fsb_config* cfg, const fsb_state_dev* state
   const bool vec_ok = aligned(L.x, 16) && aligned(L.y, 16) && aligned(L.w, 16) &&
                       aligned(L.pv, 16);
   L.vec = vec_ok ? (dbl ? 2 : 4) : 1;
-  L.block = 512;
+  // fsb_step's default streaming shape: 256 threads, and for aligned binary32
+  // state the copy compiled for four blocks per SM (64 registers)
+  L.block = 256;
+  L.min_blocks = (!dbl && L.vec == 4) ? 4 : 1;
   L.pond_half = cfg->pond_half;
   L.step = cfg->step;
   L.w0 = cfg->w0;
@@ -165,7 +187,18 @@ extern "C" int fsb_step_static(const fsb_config* cfg, const fsb_state_dev* state
   L.grid = static_cast<int>(grid < 1 ? 1 : grid);
 
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-  reset_ctl_kernel<<<1, 1, 0, s>>>(L.ctl, start_step);
+  int* carried = reinterpret_cast<int*>(scratch + kCarriedOffset);
+  int* report = reinterpret_cast<int*>(scratch + kReportOffset);
+  // host statistics make the call synchronous, and it then reports the
+  // device status (device or managed statistics keep it asynchronous)
+  bool host_stats = false;
+  if (stats_out) {
+    cudaPointerAttributes pa{};
+    e = cudaPointerGetAttributes(&pa, stats_out);
+    if (e != cudaSuccess) return fail(FSB_ERR_INVALID_ARG, "fsb_step_static: stats_out", e);
+    host_stats = pa.type == cudaMemoryTypeHost || pa.type == cudaMemoryTypeUnregistered;
+  }
+  reset_ctl_kernel<<<1, 1, 0, s>>>(L.ctl, carried, start_step);
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(FSB_ERR_CUDA, "fsb_step_static: control reset", e);
   e = launch_stream_pass(L, kSwimOnly, s);
@@ -176,6 +209,19 @@ extern "C" int fsb_step_static(const fsb_config* cfg, const fsb_state_dev* state
     e = cudaMemcpyAsync(stats_out, L.ring, sizeof(fsb_step_stats) * n_steps, cudaMemcpyDefault,
                         s);
     if (e != cudaSuccess) return fail(FSB_ERR_CUDA, "fsb_step_static: statistics copy", e);
+  }
+  if (!host_stats) return FSB_OK;
+  take_status_kernel<<<1, 1, 0, s>>>(L.ctl, carried, report);
+  e = cudaGetLastError();
+  int status = 0;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&status, report, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(FSB_ERR_CUDA, "fsb_step_static: status read", e);
+  if (status != 0) {
+    char buf[128];
+    std::snprintf(buf, sizeof(buf), "fsb_step_static: device status word latched %d", status);
+    return record_error(status, buf);
   }
   return FSB_OK;
 }

@@ -19,10 +19,30 @@
 // the statistics ring and the control word.
 #include <cstdint>
 
+#include "fsb_check.cuh"
 #include "fsb_stream_common.cuh"
 
 namespace fsb {
 namespace {
+
+// Debug build: every fish a pass reads lies in the pond, |x|, |y| <= P (the
+// swim clamps at the bank, and the initial positions are drawn inside it), so
+// a state outside it -- or a NaN -- was not produced by the method.  A failed
+// check latches FSB_ERR_STATE; the pass still computes (the swim clamps the
+// fish back), and the call's later passes do nothing.
+template <typename Real>
+__device__ __forceinline__ void check_in_pond(Real x, Real y, const Physics<Real>& ph,
+                                              Ctl* ctl) {
+#ifdef FSB_DEBUG_BOUNDS
+  const Real P = ph.pond_half;
+  fsb_check(x >= -P && x <= P && y >= -P && y <= P, &ctl->status, &ctl->timeout_site, 10u);
+#else
+  (void)x;
+  (void)y;
+  (void)ph;
+  (void)ctl;
+#endif
+}
 
 // ----------------------------------------------------------- vectors --
 template <typename Real, int VEC>
@@ -88,6 +108,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) stream_pass_kernel(StreamArgs<Rea
     vload<Real, VEC>(y, a.y, g);
     if (load_w) vload<Real, VEC>(w, a.w, g);
     if (PASS != kSwimOnly) vload<Real, VEC>(pv, a.pv, g);
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) check_in_pond(x[v], y[v], ph, a.ctl);
     if constexpr (VEC == 4) {
       fish_pass4<Real, PASS>(x, y, w, pv, g * VEC, M, t, a.key, a.school, ph, acc, maxb, ekey);
     } else if constexpr (VEC == 2) {
@@ -111,6 +133,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) stream_pass_kernel(StreamArgs<Rea
       Real x = a.x[i], y = a.y[i], w = Real(0), pv = Real(0);
       if (load_w) w = a.w[i];
       if (PASS != kSwimOnly) pv = a.pv[i];
+      check_in_pond(x, y, ph, a.ctl);
       fish_pass<Real, PASS>(x, y, w, pv, i, M, t, a.key, a.school, ph, acc, maxb, ekey);
       if (PASS != kSettle) {
         a.x[i] = x;

@@ -78,3 +78,71 @@ def test_debug_library_checks_hold_and_matches_the_oracle():
                           timeout=1200)
     assert proc.returncode == 0, proc.stdout[-2000:] + proc.stderr[-4000:]
     assert "every check held" in proc.stdout
+
+
+ERRORS_CHILD = r'''
+import os, sys
+import numpy as np
+sys.path.insert(0, os.environ["FSB_ROOT"])
+import paper_2507_20173_gb300 as fsb
+from paper_2507_20173_gb300 import build
+import torch
+
+fsb.LIB_PATH = build.build(debug=True)
+fsb.lib()
+
+def expect(status, call):
+    try:
+        call()
+    except fsb.FsbError as e:
+        assert e.status == status, (e.status, status, str(e))
+        return
+    assert status == fsb.FSB_OK, "expected %s" % fsb.fsb_strerror(status)
+
+n = 4096
+cfg = fsb.fsb_config_init(n, 3, path=fsb.FSB_PATH_STREAM)
+good = fsb.School.create(cfg)
+st = good.read()
+good.destroy()
+bad = {k: st[k].copy() for k in ("x", "y", "w", "prev")}
+bad["x"][17] = np.float32(3 * cfg.pond_half)     # a fish outside the pond
+
+# the handle path reports the latched status at its synchronising call
+s = fsb.School.create(cfg, init={"x": bad["x"], "y": bad["y"], "w": bad["w"],
+                                 "prev_objective": bad["prev"]})
+expect(fsb.FSB_ERR_STATE, lambda: s.step(3, stats=True))
+s.destroy()
+
+# the allocation-free path: an asynchronous call (no or device statistics)
+# returns OK, and the next synchronising call (host statistics) reports the
+# carried status once
+stream = torch.cuda.current_stream().cuda_stream
+ts = [torch.from_numpy(bad[k]).cuda() for k in ("x", "y", "w", "prev")]
+state = fsb.FsbStateDev(*(t.data_ptr() for t in ts))
+host = np.zeros(3, fsb.STATS_DTYPE)
+dev = torch.zeros(3 * fsb.STATS_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+expect(fsb.FSB_OK, lambda: fsb.fsb_step_static(cfg, state, 0, 3, None, stream))
+expect(fsb.FSB_OK, lambda: fsb.fsb_step_static(cfg, state, 3, 3, dev.data_ptr(), stream))
+expect(fsb.FSB_ERR_STATE, lambda: fsb.fsb_step_static(cfg, state, 6, 3, host, stream))
+expect(fsb.FSB_OK, lambda: fsb.fsb_step_static(cfg, state, 9, 3, host, stream))
+# a synchronising call that fails itself reports its own status
+ts[0][17] = 3 * cfg.pond_half
+expect(fsb.FSB_ERR_STATE, lambda: fsb.fsb_step_static(cfg, state, 12, 3, host, stream))
+expect(fsb.FSB_OK, lambda: fsb.fsb_step_static(cfg, state, 15, 3, host, stream))
+print("device errors reported")
+'''
+
+
+def test_debug_library_reports_a_state_outside_the_pond():
+    """The debug build checks that every fish a streaming pass reads lies in
+    the pond (the method never leaves it).  A school with one fish outside is
+    reported as FSB_ERR_STATE: by fsb_step when it synchronises, and by
+    fsb_step_static at the first call given host statistics, whether the
+    failing call was that one or an earlier asynchronous one."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    env = dict(os.environ, FSB_ROOT=ROOT)
+    proc = subprocess.run([sys.executable, "-c", ERRORS_CHILD], env=env, capture_output=True,
+                          text=True, timeout=1200)
+    assert proc.returncode == 0, proc.stdout[-2000:] + proc.stderr[-4000:]
+    assert "device errors reported" in proc.stdout
