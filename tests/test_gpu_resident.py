@@ -187,3 +187,23 @@ def test_resident_school_2p20_t1000():
     x64 = got["x"].astype(np.float64)
     assert abs(st900["sum_wx"][-1] - np.sum(w64 * x64)) / np.sum(w64 * np.abs(x64)) \
         <= BARY_TOL[cfg.precision]
+
+
+def test_resident_school_2p20_t1000_every_step():
+    """N = 2^20, seed 1, T = 1000 in the launch configuration the resident
+    benchmark runs, against the whole school advanced by the oracle's step on
+    every host core (run_omp, pinned equal to run bit for bit): every step's
+    max|delta| and eat() value exactly, every step's barycentre sums within
+    the mode's tolerance, and every fish's final state bit for bit."""
+    n, seed, steps = 1 << 20, 1, 1000
+    cfg = fsb.fsb_config_init(n, seed)
+    s = fsb.School.create(cfg)
+    assert fsb.fsb_handle_path(s.handle) == fsb.FSB_PATH_RESIDENT
+    stats = s.step(steps, stats=True)
+    got = s.read()
+    s.destroy()
+    ocfg = oracle_config(cfg)
+    ref = oracle.init(ocfg)
+    ref_stats = oracle.run_omp(ocfg, ref, 0, steps)
+    assert_stats_match(stats, ref_stats, cfg.precision, "2^20 every step")
+    assert_state_equal(got, ref, "2^20 T=1000")

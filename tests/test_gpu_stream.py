@@ -4,6 +4,8 @@ Per-fish state (x, y, weight, prevObjective, currentObjective) and max|delta|
 must be bit-exact; the paper's eat() statistic max(prev - cur) too; the
 barycentre sums within the tolerance of the arithmetic mode.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -323,6 +325,33 @@ def test_full_size_stream_school_sampled():
     abs_x = np.sum(w64 * np.abs(got["x"].astype(np.float64)))
     assert abs(stats["sum_w"][-1] - ref_w) / ref_w <= BARY_TOL[cfg.precision]
     assert abs(stats["sum_wx"][-1] - ref_x) / abs_x <= BARY_TOL[cfg.precision]
+
+
+def host_free_bytes():
+    return os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+
+
+def test_full_size_stream_school_every_step():
+    """N = 2^28, seed 2, T = 100 in the launch configuration the benchmark
+    times, against the whole school advanced by the oracle's step on every
+    host core (run_omp: run's per-fish arithmetic and maxima, pinned equal to
+    run bit for bit): every step's max|delta| and eat() value exactly, every
+    step's barycentre sums within the mode's tolerance, and every fish's final
+    state bit for bit.  No GPU value feeds the oracle."""
+    n, steps, seed = 1 << 28, 100, 2
+    free, _ = torch.cuda.mem_get_info()
+    if free < 12 * (1 << 30) or host_free_bytes() < 24 * (1 << 30):
+        pytest.skip("needs ~12 GB of free device memory and ~24 GB of host memory")
+    cfg = stream_cfg(n, seed)
+    s = fsb.School.create(cfg)
+    stats = s.step(steps, stats=True)
+    got = s.read()
+    s.destroy()
+    ocfg = oracle_config(cfg)
+    ref = oracle.init(ocfg)
+    ref_stats = oracle.run_omp(ocfg, ref, 0, steps)
+    assert_stats_match(stats, ref_stats, cfg.precision, "2^28 every step")
+    assert_state_equal(got, ref, "2^28 T=100")
 
 
 @pytest.mark.parametrize("kernel,stages", [(2, 2), (2, 3), (3, 2), (3, 3)])
