@@ -74,6 +74,9 @@ def parse_args():
     ap.add_argument("--e2e-runs", type=int, default=5,
                     help="end-to-end runs; the median is reported")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="skip the sub-records (resident school, batched ensemble, "
+                         "allocation-free entry point) of the default line")
     return ap.parse_args()
 
 
@@ -177,9 +180,12 @@ def issue_peak(sms, clocks):
 
 
 def ncu_traffic(n_fish, precision, stream_kernel):
-    """DRAM bytes per fused-pass launch from the committed ncu summary,
-    scaled to this launch's fish count; None if the summary is for another
-    stream kernel or precision, or the kernels changed since."""
+    """DRAM bytes of one fused-pass launch of n_fish fish, from the committed
+    ncu fit (profiles/stream_fused_traffic.json): bytes = slope x N +
+    intercept, fitted to single launches captured at several school sizes
+    (the intercept is the L2-held remainder of a launch, which does not grow
+    with N).  None if no fit matches this stream kernel and precision, or the
+    kernels changed since it was taken."""
     p = os.path.join(ROOT, "profiles", "stream_fused_traffic.json")
     if not os.path.exists(p):
         return None
@@ -187,8 +193,8 @@ def ncu_traffic(n_fish, precision, stream_kernel):
         records = json.load(f)["records"]
     for d in records:
         if (d.get("kernel_source_hash") == kernel_source_hash() and d.get("precision") == precision
-                and d.get("stream_kernel") == stream_kernel):
-            return float(d["dram_bytes_per_fish"]) * n_fish
+                and d.get("stream_kernel") == stream_kernel and "slope_bytes_per_fish" in d):
+            return float(d["slope_bytes_per_fish"]) * n_fish + float(d["intercept_bytes"])
     return None
 
 
@@ -305,11 +311,11 @@ def cpu_openmp_rate(n_fish, seed, seconds=8.0):
     return n_fish * steps / dt, dt, steps, threads
 
 
-def run_batch(args, world, rank, local, pg):
+def measure_batch(args, world, rank, local, pg):
     """The ragged ensemble (4096 schools, log-uniform sizes in [256, 65536],
     T = 500): one graph-captured persistent launch, against the same schools
     run one launch per school (the single-school path, serially on one
-    stream)."""
+    stream).  Returns the bench line (every rank)."""
     import torch
 
     import paper_2507_20173_gb300 as fsb
@@ -421,27 +427,34 @@ def run_batch(args, world, rank, local, pg):
             "peak": issue_peak(sms, clocks), "unit": "Glane-instr/s", "traffic": None,
             "peak_source": "issue peak %d SMs x 128 lanes x measured median SM clock" % sms}
     roof["frac"] = roof["achieved"] / roof["peak"] if roof["achieved"] else None
+    del ts
+    torch.cuda.empty_cache()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": steps, "warmup": warmup, "ms_per_step": ms_max / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl.name if n_schools == wl.n_schools else
+                       "%s (first %d schools)" % (wl.name, n_schools),
+                       "n_schools": n_schools, "total_fish": total,
+                       "precision": args.precision, "batch": info,
+                       "launch_plan": plan,
+                       "l2": "state %.2f GB; each school's state stays on chip for the call"
+                             % (16 * total / 1e9),
+                       "parallelism": "replicas x%d" % world},
+            "roofline": roof,
+            "per_school": per_school,
+            "batched_over_per_school": (value / world) / per_school["value"]
+            if per_school else None,
+            "batched_over_per_school_graph": (value / world) / per_school["graph"]["value"]
+            if per_school and "value" in per_school.get("graph", {}) else None,
+            "cpu_baseline": None, "e2e": None,
+            "gpu_launches": len(plan["launches"]) + 1, "clocks": clocks}
+    return line
+
+
+def run_batch(args, world, rank, local, pg):
+    line = measure_batch(args, world, rank, local, pg)
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-                "steps": steps, "warmup": warmup, "ms_per_step": ms_max / steps,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32", "data": "synthetic",
-                "config": {"workload": wl.name if n_schools == wl.n_schools else
-                           "%s (first %d schools)" % (wl.name, n_schools),
-                           "n_schools": n_schools, "total_fish": total,
-                           "precision": args.precision, "batch": info,
-                           "launch_plan": plan,
-                           "l2": "state %.2f GB; each school's state stays on chip for the call"
-                                 % (16 * total / 1e9),
-                           "parallelism": "replicas x%d" % world},
-                "roofline": roof,
-                "per_school": per_school,
-                "batched_over_per_school": (value / world) / per_school["value"]
-                if per_school else None,
-                "batched_over_per_school_graph": (value / world) / per_school["graph"]["value"]
-                if per_school and "value" in per_school.get("graph", {}) else None,
-                "cpu_baseline": None, "e2e": None,
-                "gpu_launches": len(plan["launches"]) + 1, "clocks": clocks}
         print(json.dumps(line), flush=True)
 
 
@@ -616,6 +629,105 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def barrier(torch, pg):
+    torch.cuda.synchronize()
+    if pg is not None:
+        pg.barrier()
+    torch.cuda.synchronize()
+
+
+def time_single(fsb, torch, cfg, steps, warmup, local, pg, tuning):
+    """Device-resident timing of one school: `warmup` untimed steps, then one
+    fsb_step(steps) call bracketed by CUDA events on the school's stream,
+    with the clocks sampled meanwhile.  Each fused-pass (or resident) launch
+    is also bracketed by events on that stream (fsb_set_kernel_timing)."""
+    stream = torch.cuda.current_stream()
+    school = fsb.School.create(cfg, stream=stream)
+    if any(tuning.values()):
+        fsb.fsb_set_tuning(school.handle, **tuning)
+    tuning = fsb.fsb_get_tuning(school.handle)
+    # the warm-up runs timed too, so the timed call reuses its timing events;
+    # enabling again clears the warm-up's times
+    fsb.fsb_set_kernel_timing(school.handle, True)
+    school.step(warmup)
+    fsb.fsb_set_kernel_timing(school.handle, True)
+    fsb.fsb_kernel_time(school.handle)
+    barrier(torch, pg)
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        fsb.fsb_step(school.handle, steps)
+        stop.record(stream)
+        torch.cuda.synchronize()
+    barrier(torch, pg)
+    ms = start.elapsed_time(stop)
+    fused_ms, fused_n = fsb.fsb_kernel_time(school.handle)
+    path = fsb.fsb_handle_path(school.handle)
+    school.destroy()
+    return {"ms": ms, "fused_ms": fused_ms, "fused_n": fused_n, "path": path, "tuning": tuning,
+            "clocks": clk.summary()}
+
+
+def alu_roofline(kernel, name, precision, fish_steps_per_launch, avg_s, sms, clocks):
+    """Instruction-issue roofline of an on-chip kernel: fish-steps per launch
+    / the launch's event time x the lane-instructions per fish-step ncu
+    counted (profiles/<kernel>_instr.json), against the issue peak at the
+    median SM clock sampled during the timed region."""
+    ipfs = alu_instr_per_fish_step(kernel, precision)
+    rate = fish_steps_per_launch / avg_s if avg_s else None
+    roof = {"bound": "alu", "unit": "Glane-instr/s", "kernel": name,
+            "avg_launch_ms": avg_s * 1e3 if avg_s else None,
+            "fish_steps_per_launch": fish_steps_per_launch, "lane_instr_per_fish_step": ipfs,
+            "traffic": None, "achieved": rate * ipfs / 1e9 if (rate and ipfs) else None,
+            "peak": issue_peak(sms, clocks),
+            "peak_source": "issue peak %d SMs x 128 lanes x measured median SM clock" % sms}
+    roof["frac"] = roof["achieved"] / roof["peak"] if roof["achieved"] else None
+    return roof
+
+
+def resident_record(fsb, torch, local, pg):
+    """The resident school of the metric's configurations (N = 2^20, seed 1,
+    T = 1000, the on-chip kernel): one call timed as the main line's."""
+    wl = workloads.RESIDENT
+    cfg = fsb.fsb_config_init(wl.n_fish, wl.seed, precision=fsb.FSB_FP32_KAHAN)
+    t = time_single(fsb, torch, cfg, wl.steps, 3, local, pg, {})
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    avg_s = (t["fused_ms"] / t["fused_n"]) / 1e3 if t["fused_n"] else None
+    roof = alu_roofline("resident", "resident_kernel", "FP32_KAHAN", wl.n_fish * wl.steps, avg_s,
+                        sms, t["clocks"])
+    roof["launches"] = t["fused_n"]
+    return {"workload": wl.name, "value": wl.n_fish * wl.steps / (t["ms"] / 1e3), "unit": UNIT,
+            "steps": wl.steps, "warmup": 3, "ms_per_step": t["ms"] / wl.steps,
+            "path": {1: "stream", 2: "resident"}.get(t["path"], str(t["path"])),
+            "tuning": t["tuning"], "roofline": roof, "gpu_launches": 1, "clocks": t["clocks"]}
+
+
+def static_record(fsb, torch, cfg, steps, warmup, local):
+    """fsb_step_static, the allocation-free entry point, on the main line's
+    school: `warmup` steps, then one call of `steps` steps on caller-owned
+    arrays timed with CUDA events (its scratch is the library's static
+    array; nothing is allocated)."""
+    stream = torch.cuda.current_stream()
+    school = fsb.School.create(cfg, stream=stream)   # its arrays, initialised
+    state = fsb.FsbStateDev(*(t.data_ptr() for t in school.tensors))
+    fsb.fsb_step_static(cfg, state, 0, warmup, None, stream.cuda_stream)
+    torch.cuda.synchronize()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        fsb.fsb_step_static(cfg, state, warmup, steps, None, stream.cuda_stream)
+        stop.record(stream)
+        torch.cuda.synchronize()
+    ms = start.elapsed_time(stop)
+    school.destroy()
+    del school, state
+    torch.cuda.empty_cache()
+    return {"value": cfg.n_fish * steps / (ms / 1e3), "unit": UNIT, "steps": steps,
+            "ms_per_step": ms / steps, "gpu_launches": steps + 1,
+            "what": "fsb_step_static(K) on caller-owned arrays, same school and steps",
+            "clocks": clk.summary()}
+
+
 def run_ours(args, world, rank, local, pg):
     import torch
 
@@ -639,40 +751,17 @@ def run_ours(args, world, rank, local, pg):
                               collective_mode=1 if coll else 0)
     stream = torch.cuda.current_stream()
 
-    def barrier():
-        torch.cuda.synchronize()
-        if pg is not None:
-            pg.barrier()
-        torch.cuda.synchronize()
-
     tuning = {"stream_kernel": args.stream_kernel, "stream_block": args.stream_block,
               "stream_stages": args.stream_stages}
 
     # ---- device-resident timing
-    school = fsb.School.create(cfg, stream=stream)
-    if any(tuning.values()):
-        fsb.fsb_set_tuning(school.handle, **tuning)
-    tuning = fsb.fsb_get_tuning(school.handle)
-    # the warm-up runs timed too, so the timed call reuses its timing events;
-    # enabling again clears the warm-up's times
-    fsb.fsb_set_kernel_timing(school.handle, True)
-    school.step(warmup)
-    fsb.fsb_set_kernel_timing(school.handle, True)
-    fsb.fsb_kernel_time(school.handle)
-    barrier()
-    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        start.record(stream)
-        fsb.fsb_step(school.handle, steps)
-        stop.record(stream)
-        torch.cuda.synchronize()
-    barrier()
-    ms = start.elapsed_time(stop)
-    fused_ms, fused_n = fsb.fsb_kernel_time(school.handle)
-    path = fsb.fsb_handle_path(school.handle)
-    school.destroy()
+    t = time_single(fsb, torch, cfg, steps, warmup, local, pg, tuning)
+    ms, fused_ms, fused_n, path, tuning = t["ms"], t["fused_ms"], t["fused_n"], t["path"], \
+        t["tuning"]
+    clocks = t["clocks"]
     ms_max = reduce_max(ms, pg)
     value = world * n * steps / (ms_max / 1e3)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
 
     # ---- roofline of the dominant kernel
     peak, peak_kind = measured_peaks()
@@ -684,44 +773,49 @@ def run_ours(args, world, rank, local, pg):
     if coll:
         # two passes per step, bound by instruction issue (grid terms, two
         # draws and three square roots per fish); HBM fraction kept beside
-        ipfs = alu_instr_per_fish_step("collective", args.precision)
-        rate = n / avg_fused_s if avg_fused_s else None
+        roof = alu_roofline("collective", "coll_kernel<eat> + coll_kernel<move> (one step)",
+                            args.precision, n, avg_fused_s, sms, clocks)
         hbm = bytes_per_fish_step * n / avg_fused_s / 1e9 if avg_fused_s else None
-        sms = torch.cuda.get_device_properties(local).multi_processor_count
-        roof = {"bound": "alu", "unit": "Glane-instr/s",
-                "kernel": "coll_kernel<eat> + coll_kernel<move> (one step)",
-                "launches": fused_n, "avg_launch_ms": avg_fused_s * 1e3 if avg_fused_s else None,
-                "fish_steps_per_launch": n, "lane_instr_per_fish_step": ipfs, "traffic": None,
-                "achieved": rate * ipfs / 1e9 if (rate and ipfs) else None,
-                "peak_source": "issue peak %d SMs x 128 lanes x measured median SM clock" % sms,
-                "_sms": sms, "hbm_achieved_gbs": hbm,
-                "hbm_frac_of_measured": hbm / peak if hbm else None,
-                "algorithmic_bytes_per_launch": bytes_per_fish_step * n}
+        roof.update({"launches": fused_n, "hbm_achieved_gbs": hbm,
+                     "hbm_frac_of_measured": hbm / peak if hbm else None,
+                     "algorithmic_bytes_per_launch": bytes_per_fish_step * n})
     elif path == fsb.FSB_PATH_RESIDENT:
         # one launch advances all `steps` steps with the state on chip: bound
         # by instruction issue, 152 SMs x 4 schedulers x 32 lanes per clock
-        ipfs = alu_instr_per_fish_step("resident", args.precision)
-        fish_steps_per_launch = n * steps
-        rate = fish_steps_per_launch / avg_fused_s if avg_fused_s else None
-        roof = {"bound": "alu", "unit": "Glane-instr/s", "kernel": "resident_kernel",
-                "launches": fused_n, "avg_launch_ms": avg_fused_s * 1e3 if avg_fused_s else None,
-                "fish_steps_per_launch": fish_steps_per_launch,
-                "lane_instr_per_fish_step": ipfs, "traffic": None}
-        sms = torch.cuda.get_device_properties(local).multi_processor_count
-        roof["peak_source"] = "issue peak %d SMs x 128 lanes x measured median SM clock" % sms
-        roof["_sms"] = sms
-        roof["achieved"] = rate * ipfs / 1e9 if (rate and ipfs) else None
+        roof = alu_roofline("resident", "resident_kernel", args.precision, n * steps,
+                            avg_fused_s, sms, clocks)
+        roof["launches"] = fused_n
     else:
         achieved = bytes_per_fish_step * n / avg_fused_s / 1e9 if avg_fused_s else None
         traffic = ncu_traffic(n, args.precision, tuning["stream_kernel"])
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
+                                  "fused launch, slope x N + intercept fitted over captured "
+                                  "school sizes (profiles/stream_fused_traffic.json)",
                 "peak_source": peak_kind + " hbm_gbs (STREAM copy)",
                 "kernel": {1: "stream_pass_kernel<fused>", 2: "stream_pass_tma_kernel<fused>",
                            3: "stream_pass_ws_kernel<fused>"}[tuning["stream_kernel"]],
                 "launches": fused_n,
                 "avg_launch_ms": avg_fused_s * 1e3 if avg_fused_s else None,
                 "algorithmic_bytes_per_launch": bytes_per_fish_step * n}
+
+    # ---- the metric's other configurations and the allocation-free entry
+    # point, measured in the same run (N = 1, default workload only)
+    subs = None
+    if world == 1 and args.workload == "stream" and not args.no_sub:
+        subs = {"no_alloc": static_record(fsb, torch, cfg, steps, warmup, local)}
+        subs["no_alloc"]["over_fsb_step"] = subs["no_alloc"]["value"] / value
+        subs["resident"] = resident_record(fsb, torch, local, pg)
+        bargs = argparse.Namespace(**{**vars(args), "steps": None, "warmup": 3,
+                                      "batch_schools": None, "batch_cluster": 0,
+                                      "no_per_school": False, "precision": "FP32_KAHAN"})
+        bl = measure_batch(bargs, world, rank, local, pg)
+        subs["batch"] = {k: bl[k] for k in ("value", "unit", "steps", "warmup", "ms_per_step",
+                                            "config", "roofline", "per_school",
+                                            "batched_over_per_school",
+                                            "batched_over_per_school_graph", "gpu_launches",
+                                            "clocks")}
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
@@ -743,7 +837,7 @@ def run_ours(args, world, rank, local, pg):
         # handle's first graph instantiation are warm-up, like the device
         # steps' warm-up
         for r_i in range(1 + args.e2e_runs):
-            barrier()
+            barrier(torch, pg)
             t0 = time.perf_counter()
             h = fsb.fsb_create(cfg, bufs, host, 0, stream.cuda_stream)
             if args.stream_kernel or args.stream_block or args.stream_stages:
@@ -792,11 +886,6 @@ def run_ours(args, world, rank, local, pg):
                              "sample": "%d fish x %d steps of the %s school, %.1f s"
                                        % (cn, osteps, wl.name, odt)}
 
-    clocks = clk.summary()
-    if roof.get("bound") == "alu":
-        sms = roof.pop("_sms")
-        roof["peak"] = issue_peak(sms, clocks)
-        roof["frac"] = roof["achieved"] / roof["peak"] if roof.get("achieved") else None
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": steps, "warmup": warmup, "ms_per_step": ms_max / steps,
@@ -811,8 +900,11 @@ def run_ours(args, world, rank, local, pg):
                                  else "state fits in L2 (reused across steps)",
                            "parallelism": "replicas x%d" % world, "tuning": tuning},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": steps + 1 if path != fsb.FSB_PATH_RESIDENT else 1,
+                "gpu_launches": (2 * steps + 1 if coll else steps + 1)
+                if path != fsb.FSB_PATH_RESIDENT else 1,
                 "clocks": clocks}
+        if subs is not None:
+            line["sub_records"] = subs
         print(json.dumps(line), flush=True)
 
 
