@@ -46,7 +46,11 @@ struct Part3 {
   Part w, x, y;
 };
 
-constexpr int kBatchThreads = 512;                // fish threads
+#ifndef FSB_BATCH_FISH_THREADS
+#define FSB_BATCH_FISH_THREADS 512
+#endif
+constexpr int kBatchThreads = FSB_BATCH_FISH_THREADS;  // fish threads
+static_assert(kBatchThreads % 32 == 0 && kBatchThreads <= 992, "fish threads: whole warps, <= 31");
 constexpr int kBatchWarps = kBatchThreads / 32;
 constexpr int kBlockThreads = kBatchThreads + 32;  // and one helper warp
 constexpr int kBlockFish = 8192;              // fish one block holds
@@ -71,17 +75,25 @@ struct BatchShared {
   Part3<Part> block_part[2][kMaxCluster];
 };
 
-// Fold of the warps' partials by one warp, a fixed xor tree over the
-// kBatchWarps partials (lanes beyond them repeat them); the result is valid
-// in every lane.
+// Fold of the warps' partials by one warp, a fixed xor tree; the result is
+// valid in every lane.  A power-of-two warp count folds over the kBatchWarps
+// partials (lanes beyond them repeat them); any other count over 32 lanes,
+// those beyond the warps holding zeros.
+constexpr int kFoldLanes = (kBatchWarps & (kBatchWarps - 1)) == 0 ? kBatchWarps : 32;
 template <typename Part>
 __device__ __forceinline__ Part3<Part> fold_warps(const Part3<Part>* wp) {
-  static_assert(kBatchWarps <= 32 && (kBatchWarps & (kBatchWarps - 1)) == 0,
-                "fold tree over a power-of-two warp count");
+  static_assert(kBatchWarps <= 31, "the helper warp makes the 32nd");
   const int lane = threadIdx.x & 31;
-  Part3<Part> r = wp[lane & (kBatchWarps - 1)];
+  Part3<Part> r;
+  if (kFoldLanes == kBatchWarps) {
+    r = wp[lane & (kBatchWarps - 1)];
+  } else if (lane < kBatchWarps) {
+    r = wp[lane];
+  } else {
+    r.w = r.x = r.y = part_zero<Part>();
+  }
 #pragma unroll
-  for (int off = kBatchWarps / 2; off > 0; off >>= 1) {
+  for (int off = kFoldLanes / 2; off > 0; off >>= 1) {
     r.w = merge(r.w, shfl_xor(r.w, off));
     r.x = merge(r.x, shfl_xor(r.x, off));
     r.y = merge(r.y, shfl_xor(r.y, off));
@@ -120,7 +132,7 @@ __device__ __forceinline__ void put_sums(fsb_step_stats* st, Part w, Part x, Par
 template <int ACC, bool VAR>
 __device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int rank, int nb,
                                            BatchShared<ACC>& S, const PairState& B) {
-  using Acc = SumAcc<ACC>;
+  using Acc = OnchipAcc<ACC>;
   using Part = typename Acc::Part;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const bool helper = warp == kBatchWarps;

@@ -53,25 +53,45 @@ template <>
 __device__ __forceinline__ double raw_to_sum<kAccF64>(double r) { return r; }
 
 // ----------------------------------------------- barycentre terms of a pair --
-// The two fish of one swim pair into the accumulator: plain binary32 and
-// binary64 add them one by one; compensated binary32 forms the pair's
-// binary32 sums (w0 + w1, w0 x0 + w1 x1, w0 y0 + w1 y1: one rounding each,
-// exact when one weight is zero) and adds each with one compensated step.
-__device__ __forceinline__ void acc_pair(SumAcc<kAccPlain32>& acc, float2 wv, float2 xv,
+// The accumulator of the on-chip passes.  Plain binary32 and binary64 add
+// the two fish of a swim pair one by one (SumAcc).  In compensated binary32
+// a thread holds at most eight pairs per step (a block's slice is at most
+// 16 fish per thread), so it keeps one plain binary32 sum per fish of its
+// pairs (the two lanes of a float2: w, w x, w y; one rounding per addition,
+// so an error below 7 * 2^-24 of the lane's sum of magnitudes) and hands the
+// warp the exact compensated pair TwoSum(lane 0, lane 1); compensation then
+// runs from the warp level up (warp_tree, merge).  This takes 7 instructions
+// per pair against 19 for a Kahan step per quantity.
+template <int ACC>
+struct OnchipAcc : SumAcc<ACC> {};
+
+template <>
+struct OnchipAcc<kAccKahan32> {
+  using Sum = double;
+  using Part = F2;
+  float2 w = make_float2(0.f, 0.f), x = make_float2(0.f, 0.f), y = make_float2(0.f, 0.f);
+  __device__ __forceinline__ Part pw() const { return two_sum(w.x, w.y); }
+  __device__ __forceinline__ Part px() const { return two_sum(x.x, x.y); }
+  __device__ __forceinline__ Part py() const { return two_sum(y.x, y.y); }
+};
+
+__device__ __forceinline__ float2 add_x2(float2 a, float2 b);
+
+__device__ __forceinline__ void acc_pair(OnchipAcc<kAccPlain32>& acc, float2 wv, float2 xv,
                                          float2 yv) {
   acc.add(wv.x, xv.x, yv.x);
   acc.add(wv.y, xv.y, yv.y);
 }
-__device__ __forceinline__ void acc_pair(SumAcc<kAccF64>& acc, float2 wv, float2 xv, float2 yv) {
+__device__ __forceinline__ void acc_pair(OnchipAcc<kAccF64>& acc, float2 wv, float2 xv,
+                                         float2 yv) {
   acc.add(wv.x, xv.x, yv.x);
   acc.add(wv.y, xv.y, yv.y);
 }
-__device__ __forceinline__ void acc_pair(SumAcc<kAccKahan32>& acc, float2 wv, float2 xv,
+__device__ __forceinline__ void acc_pair(OnchipAcc<kAccKahan32>& acc, float2 wv, float2 xv,
                                          float2 yv) {
-  using K = SumAcc<kAccKahan32>;
-  K::kadd(acc.sw, acc.cw, __fadd_rn(wv.x, wv.y));
-  K::kadd(acc.sx, acc.cx, __fadd_rn(__fmul_rn(wv.x, xv.x), __fmul_rn(wv.y, xv.y)));
-  K::kadd(acc.sy, acc.cy, __fadd_rn(__fmul_rn(wv.x, yv.x), __fmul_rn(wv.y, yv.y)));
+  acc.w = add_x2(acc.w, wv);
+  acc.x = add_x2(acc.x, make_float2(__fmul_rn(wv.x, xv.x), __fmul_rn(wv.y, xv.y)));
+  acc.y = add_x2(acc.y, make_float2(__fmul_rn(wv.x, yv.x), __fmul_rn(wv.y, yv.y)));
 }
 
 __device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
@@ -202,7 +222,7 @@ struct PassCtx {
 template <bool EAT, bool SWIM, bool LAST_SWIM, bool LAST_EAT, bool AHEAD, typename Acc>
 __device__ __forceinline__ void pair_pass(const PairState& B, uint32_t e, bool two,
                                           const PassCtx& c, const Physics<float>& ph, Acc& acc,
-                                          uint32_t& mb, uint32_t& ek) {
+                                          float& ihi, float& ilo) {
   float2 xv = B.Xs[e], yv = B.Ys[e], fv = B.F[e];
   float2 wv = (EAT || ph.swim_mode) ? B.W[e] : make_float2(0.f, 0.f);
   if (EAT) {
@@ -228,10 +248,11 @@ __device__ __forceinline__ void pair_pass(const PairState& B, uint32_t e, bool t
     fv = objective_pair(xv, yv);
     const float2 i = sub_x2(o, fv);  // prev - cur
     const float2 d = sub_x2(fv, o);  // delta
-    const uint32_t m0 = abs_bits(d.x), q0 = order_key(i.x);
-    const uint32_t m1 = two ? abs_bits(d.y) : 0u, q1 = two ? order_key(i.y) : 0u;
-    mb = max(mb, max(m0, m1));
-    ek = max(ek, max(q0, q1));
+    // the largest and smallest prev - cur (a half pair's absent fish
+    // repeats fish 0): max |delta| = max(ihi, -ilo), max(prev - cur) = ihi
+    const float i1 = two ? i.y : i.x;
+    ihi = fmaxf(ihi, fmaxf(i.x, i1));
+    ilo = fminf(ilo, fminf(i.x, i1));
     B.Xd[e] = xv;
     B.Yd[e] = yv;
     B.F[e] = fv;
@@ -242,19 +263,28 @@ __device__ __forceinline__ void pair_pass(const PairState& B, uint32_t e, bool t
 // All of this thread's pairs in one pass: elements threadIdx.x,
 // threadIdx.x + step, ... below np (nf fish), where step is the number of
 // threads that share the pass (threads 0 .. step - 1), two per iteration so
-// that two independent draws overlap.
+// that two independent draws overlap.  The thread's maxima of the pass's
+// swim go into mb (bits of max |delta|) and ek (order key of max(prev -
+// cur)): prev - cur is never -0 (x - x is +0), so the float extremes order
+// like the keys.
 template <bool EAT, bool SWIM, bool LAST_SWIM, bool LAST_EAT, bool AHEAD = false, typename Acc>
 __device__ __forceinline__ void block_pass(const PairState& B, uint32_t np, uint32_t nf,
                                            const PassCtx& c, const Physics<float>& ph, Acc& acc,
                                            uint32_t& mb, uint32_t& ek, uint32_t step) {
+  float ihi = -__int_as_float(0x7f800000), ilo = __int_as_float(0x7f800000);
   uint32_t e = threadIdx.x;
   for (; e + step < np; e += 2 * step) {
-    pair_pass<EAT, SWIM, LAST_SWIM, LAST_EAT, AHEAD>(B, e, true, c, ph, acc, mb, ek);
+    pair_pass<EAT, SWIM, LAST_SWIM, LAST_EAT, AHEAD>(B, e, true, c, ph, acc, ihi, ilo);
     const uint32_t e2 = e + step;
-    pair_pass<EAT, SWIM, LAST_SWIM, LAST_EAT, AHEAD>(B, e2, 2 * e2 + 1 < nf, c, ph, acc, mb, ek);
+    pair_pass<EAT, SWIM, LAST_SWIM, LAST_EAT, AHEAD>(B, e2, 2 * e2 + 1 < nf, c, ph, acc, ihi,
+                                                     ilo);
   }
   if (e < np)
-    pair_pass<EAT, SWIM, LAST_SWIM, LAST_EAT, AHEAD>(B, e, 2 * e + 1 < nf, c, ph, acc, mb, ek);
+    pair_pass<EAT, SWIM, LAST_SWIM, LAST_EAT, AHEAD>(B, e, 2 * e + 1 < nf, c, ph, acc, ihi, ilo);
+  if (SWIM && ihi >= ilo) {  // at least one fish swum
+    mb = max(mb, abs_bits(fmaxf(ihi, -ilo)));
+    ek = max(ek, order_key(ihi));
+  }
 }
 
 }  // namespace fsb

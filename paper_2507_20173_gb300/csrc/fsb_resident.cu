@@ -37,7 +37,12 @@
 namespace fsb {
 namespace {
 
-constexpr int kResThreads = 512;  // most fish threads per block (one more warp synchronises)
+#ifndef FSB_RESIDENT_FISH_THREADS
+#define FSB_RESIDENT_FISH_THREADS 512
+#endif
+// most fish threads per block (one more warp synchronises)
+constexpr int kResThreads = FSB_RESIDENT_FISH_THREADS;
+static_assert(kResThreads % 32 == 0 && kResThreads <= 992, "fish threads: whole warps, <= 31");
 // shared memory per fish: x and y (two buffers), feeding input (two
 // buffers), currentObjective and weight, binary32 each
 constexpr size_t kResSmemPerFish = 8 * sizeof(float);
@@ -109,7 +114,7 @@ constexpr int kBarMax = 3;  // ids 3, 4: "the block's maxima of step u are in s_
 // waits for the eat of step u, so it runs fused with it, after M_u.
 template <int ACC, bool WSWIM>
 __global__ void __launch_bounds__(kResThreads + 32, 1) resident_kernel(ResidentArgs a) {
-  using Acc = SumAcc<ACC>;
+  using Acc = OnchipAcc<ACC>;
   using Sum = typename Acc::Sum;
   using Part = typename Acc::Part;
   extern __shared__ float2 res_smem[];
