@@ -161,6 +161,7 @@ struct fsb_school {
   uint64_t fused_launches = 0;
   void* cur_stage = nullptr;       // two chunks of currentObjective for fsb_read_state
   uint64_t cur_chunk = 0;          // fish per chunk
+  BlockPartial* bpartials = nullptr;  // stream kernel 4: per-step partials of a pair
   bool collective = false;         // collective_mode 1: two passes per step
   fsb::CollLaunch coll{};
   uint32_t coll_cap = 0;           // steps the collective record ring holds
@@ -251,8 +252,34 @@ int enqueue_collective(fsb_school* h, uint32_t n, cudaStream_t s, bool timed) {
 }
 
 // Enqueue the pass sequence of one call on stream s (capturable).
+// Stream kernel 4: the pairs of blocked passes between the call's first
+// swim and its last eat, each advancing up to blocked_k steps (timed pairs
+// bracketed by events when `timed`).
+int enqueue_blocked(fsb_school* h, uint32_t n, cudaStream_t s, bool timed) {
+  int rc = launch_pass(h, fsb::kSwimOnly, s);
+  const uint32_t K = static_cast<uint32_t>(h->launch.blocked_k);
+  for (uint32_t j = 1; rc == FSB_OK && j < n; j += K) {
+    const uint32_t k = n - j < K ? n - j : K;
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (timed) {
+      a = take_event(h);
+      b = take_event(h);
+      if (!a || !b) return fail(FSB_ERR_CUDA, "cudaEventCreate failed");
+      FSB_CUDA(cudaEventRecord(a, s));
+    }
+    FSB_CUDA(fsb::launch_blocked_pair(h->launch, k, s));
+    if (timed) {
+      FSB_CUDA(cudaEventRecord(b, s));
+      h->ev_pending.emplace_back(a, b);
+    }
+  }
+  if (rc == FSB_OK) rc = launch_pass(h, fsb::kSettle, s);
+  return rc;
+}
+
 int enqueue_call(fsb_school* h, uint32_t n, cudaStream_t s) {
   if (h->collective) return enqueue_collective(h, n, s, false);
+  if (h->launch.blocked_k) return enqueue_blocked(h, n, s, false);
   int rc = launch_pass(h, fsb::kSwimOnly, s);
   for (uint32_t k = 1; rc == FSB_OK && k < n; ++k) rc = launch_pass(h, fsb::kFused, s);
   if (rc == FSB_OK) rc = launch_pass(h, fsb::kSettle, s);
@@ -337,6 +364,14 @@ int run_timed(fsb_school* h, uint32_t n) {
 int run_stream(fsb_school* h, uint32_t n) {
   if (h->collective) {
     if (h->timing || n > kGraphMaxSteps) return enqueue_collective(h, n, h->stream, h->timing);
+    cudaGraphExec_t exec = nullptr;
+    int rc = get_graph(h, n, &exec);
+    if (rc != FSB_OK) return rc;
+    FSB_CUDA(cudaGraphLaunch(exec, h->stream));
+    return FSB_OK;
+  }
+  if (h->launch.blocked_k) {
+    if (h->timing || n > kGraphMaxSteps) return enqueue_blocked(h, n, h->stream, h->timing);
     cudaGraphExec_t exec = nullptr;
     int rc = get_graph(h, n, &exec);
     if (rc != FSB_OK) return rc;
@@ -428,9 +463,45 @@ constexpr int kMaxPartialsPerSm = 8;
 constexpr uint64_t kCurChunk = 1ull << 22;
 
 // Streaming launch shape: kernel variant, block, grid.  Invalidates graphs.
-int configure_stream(fsb_school* h, int kernel, int block, int blocks_per_sm, int stages) {
+constexpr int kMaxBlockSteps = 8;
+
+int configure_stream(fsb_school* h, int kernel, int block, int blocks_per_sm, int stages,
+                     int block_steps) {
   StreamLaunch L = h->launch;
   const bool tma_ok = !L.real_is_double && L.vec == 4;
+  // stream kernel 4 runs the call's first swim and last eat on kernel 1 in
+  // its default shape, and the pairs of blocked passes in between
+  if (kernel == 4) {
+    if (!fsb::stream_blocked_supported(L) || h->collective)
+      return fail(FSB_ERR_INVALID_ARG,
+                  "stream kernel 4 needs binary32, 16-byte aligned state and the default swim");
+    if (block != 0 && block != 256)
+      return fail(FSB_ERR_INVALID_ARG, "stream kernel 4 runs 256-thread blocks");
+    const int k = block_steps ? block_steps : 4;
+    if (k != 2 && k != 4 && k != 8)
+      return fail(FSB_ERR_INVALID_ARG, "stream_block_steps must be 2, 4 or 8");
+    int rc = configure_stream(h, 1, 256, 4, 0, 0);
+    if (rc != FSB_OK) return rc;
+    L = h->launch;
+    L.blocked_k = k;
+    const int per_sm = fsb::stream_blocked_blocks_per_sm(L);
+    if (per_sm < 1) return fail(FSB_ERR_INVALID_ARG, "stream kernel 4 cannot be resident");
+    const uint64_t need = (h->cfg.n_fish / 4 + 255) / 256;
+    const uint64_t full = static_cast<uint64_t>(h->sms) * per_sm;
+    L.bgrid = static_cast<int>(need < 1 ? 1 : (need < full ? need : full));
+    if (!h->bpartials) {
+      BlockPartial* bp = nullptr;
+      FSB_CUDA(cudaMalloc(&bp, sizeof(BlockPartial) * kMaxBlockSteps * full));
+      h->bpartials = bp;
+    }
+    L.bpartials = h->bpartials;
+    h->launch = L;
+    h->tuning.stream_kernel = 4;
+    h->tuning.stream_block_steps = k;
+    return FSB_OK;
+  }
+  L.blocked_k = 0;
+  h->tuning.stream_block_steps = 0;
   // default measured on GB300 at N = 2^28: vector loads, 256 threads, 4
   // blocks per SM (0.96 of the copy peak, against 0.91 for the bulk-copy
   // ring and 0.90 for its warp-specialised form, timed back to back)
@@ -439,7 +510,7 @@ int configure_stream(fsb_school* h, int kernel, int block, int blocks_per_sm, in
   if (stages < 2 || stages > 4) return fail(FSB_ERR_INVALID_ARG, "stream stages must be 2..4");
   if ((kernel == 2 || kernel == 3) && !tma_ok)
     return fail(FSB_ERR_INVALID_ARG, "bulk-copy kernels need binary32, 16-byte aligned state");
-  if (kernel < 1 || kernel > 3) return fail(FSB_ERR_INVALID_ARG, "unknown stream kernel");
+  if (kernel < 1 || kernel > 4) return fail(FSB_ERR_INVALID_ARG, "unknown stream kernel");
   if (kernel == 3 && stages > 3)
     return fail(FSB_ERR_INVALID_ARG, "warp-specialised ring: stages must be 2 or 3");
   if (block == 0) block = kernel == 1 ? 256 : 512;
@@ -537,6 +608,7 @@ void release(fsb_school* h) {
   cudaFree(h->rctl);
   cudaFree(h->sums);
   cudaFree(h->partials);
+  cudaFree(h->bpartials);
   cudaFree(h->ring);
   cudaFree(h->cur_stage);
   cudaFree(h->coll.partials);
@@ -651,7 +723,7 @@ int fsb_create(const fsb_config* cfg, const fsb_state_dev* buffers, const fsb_st
     h->sms = sms;
     FSB_CUDA(cudaMalloc(&h->partials, sizeof(BlockPartial) * sms * kMaxPartialsPerSm));
     L.partials = h->partials;
-    int r0 = configure_stream(h, 0, 0, 0, 0);
+    int r0 = configure_stream(h, 0, 0, 0, 0, 0);
     if (r0 != FSB_OK) return r0;
 
     // collective movements: streaming only (two passes per step)
@@ -724,7 +796,22 @@ int fsb_create(const fsb_config* cfg, const fsb_state_dev* buffers, const fsb_st
     if (r != FSB_OK) return r;
     StreamLaunch& L2 = h->launch;
 
+    // pinned host arrays are copied in by the SMs (fsb_transfer.cu), others
+    // by the copy engines
+    // (no braced lists with commas here: this block is a macro argument)
+    const void* in_dev[4] = {};
+    bool direct = init != nullptr;
     if (init) {
+      in_dev[0] = fsb::host_view(init->x);
+      in_dev[1] = fsb::host_view(init->y);
+      in_dev[2] = fsb::host_view(init->w);
+      in_dev[3] = fsb::host_view(init->prev_objective);
+      for (int k = 0; k < 4; ++k)
+        if (!in_dev[k]) direct = false;
+    }
+    if (init && direct) {
+      FSB_CUDA(fsb::launch_copy_in(L2, in_dev, h->stream));
+    } else if (init) {
       FSB_CUDA(cudaMemcpyAsync(h->x, init->x, bytes, cudaMemcpyHostToDevice, h->stream));
       FSB_CUDA(cudaMemcpyAsync(h->y, init->y, bytes, cudaMemcpyHostToDevice, h->stream));
       FSB_CUDA(cudaMemcpyAsync(h->w, init->w, bytes, cudaMemcpyHostToDevice, h->stream));
@@ -773,6 +860,22 @@ int fsb_read_state(fsb_handle h, void* x, void* y, void* w, void* prev_objective
                    void* current_objective, uint64_t* step_out) {
   if (!h) return fail(FSB_ERR_INVALID_ARG, "handle is NULL");
   const size_t bytes = h->elem * h->cfg.n_fish;
+  // all requested arrays pinned: one kernel writes them (and computes
+  // currentObjective on the way, fsb_transfer.cu); else the copy engines
+  void* out[5] = {x, y, w, prev_objective, current_objective};
+  void* out_dev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  bool direct = false;
+  for (int k = 0; k < 5; ++k) {
+    if (!out[k]) continue;
+    out_dev[k] = fsb::host_view(out[k]);
+    direct = out_dev[k] != nullptr;
+    if (!direct) break;
+  }
+  if (direct) {
+    FSB_CUDA(fsb::launch_read_out(h->launch, out_dev, h->stream));
+    if (step_out) *step_out = h->step;
+    return check_status_word(h);
+  }
   if (x) FSB_CUDA(cudaMemcpyAsync(x, h->x, bytes, cudaMemcpyDeviceToHost, h->stream));
   if (y) FSB_CUDA(cudaMemcpyAsync(y, h->y, bytes, cudaMemcpyDeviceToHost, h->stream));
   if (w) FSB_CUDA(cudaMemcpyAsync(w, h->w, bytes, cudaMemcpyDeviceToHost, h->stream));
@@ -832,7 +935,7 @@ int fsb_set_tuning(fsb_handle h, const fsb_tuning* t) {
   const StreamLaunch saved = h->launch;
   const fsb_tuning saved_t = h->tuning;
   int rc = configure_stream(h, t->stream_kernel, t->stream_block, t->stream_blocks_per_sm,
-                            t->stream_stages);
+                            t->stream_stages, t->stream_block_steps);
   if (rc != FSB_OK) {
     h->launch = saved;
     h->tuning = saved_t;

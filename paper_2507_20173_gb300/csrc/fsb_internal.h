@@ -61,6 +61,9 @@ struct StreamLaunch {
   BlockPartial* partials;
   fsb_step_stats* ring;
   uint32_t ring_cap;
+  int blocked_k = 0;                   // stream kernel 4: steps per pair of passes (2, 4, 8)
+  int bgrid = 0;                       //   its grid
+  BlockPartial* bpartials = nullptr;   //   its per-step partials, blocked_k x bgrid
   unsigned long long timeout_ns = 0;  // bound of the copy rings' waits (0: 1 s)
   int inject_block = -1;               // test hook (copy-ring kernels): block that withholds
   uint32_t inject_pass = 0;            //   its first copy in this pass of a call; -1 = none
@@ -78,6 +81,12 @@ cudaError_t stream_ws_prepare(const StreamLaunch& L);
 int stream_ws_blocks_per_sm(const StreamLaunch& L);
 cudaError_t launch_stream_pass_ws(const StreamLaunch& L, int pass_kind, cudaStream_t s);
 cudaError_t launch_init(const StreamLaunch& L, int weight_mode, cudaStream_t s);
+// Stream kernel 4 (fsb_stream_blocked.cu): a pair of passes advancing k <=
+// L.blocked_k steps, the maxima pass and then the step pass (binary32,
+// 16-byte aligned state, default swim).
+bool stream_blocked_supported(const StreamLaunch& L);
+int stream_blocked_blocks_per_sm(const StreamLaunch& L);
+cudaError_t launch_blocked_pair(const StreamLaunch& L, uint32_t k, cudaStream_t s);
 
 // ---- collective movements (collective_mode 1, fsb_collective.cu)
 // A call of n steps runs pass 0 (kCSwim0), then for t = 1 .. n the passes
@@ -127,6 +136,15 @@ cudaError_t launch_coll_pass(const CollLaunch& L, int pass_kind, uint32_t n_step
 // currentObjective of fish [first, first + count) into cur[0, count).
 cudaError_t launch_objective(const StreamLaunch& L, uint64_t first, uint64_t count, void* cur,
                              cudaStream_t s);
+// State transfers done by the SMs (fsb_transfer.cu).  host_view: the
+// device-visible address of pinned (or registered) host memory, else null.
+// launch_read_out: the device state into host arrays out[0..4] (x, y, w,
+// prevObjective, currentObjective -- computed on the way; null ones
+// skipped), all device-visible.  launch_copy_in: host arrays in[0..3] (x, y,
+// w, prevObjective), all device-visible, into the device state.
+void* host_view(const void* p);
+cudaError_t launch_read_out(const StreamLaunch& L, void* const out[5], cudaStream_t s);
+cudaError_t launch_copy_in(const StreamLaunch& L, const void* const in[4], cudaStream_t s);
 // Launch description of the resident single-school kernel (binary32 state).
 struct ResidentLaunch {
   void* x;

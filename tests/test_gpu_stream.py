@@ -449,3 +449,43 @@ def test_fault_injection_needs_a_copy_ring_kernel():
     fsb.fsb_set_fault_injection(s.handle, -1, 0, 0)   # clearing is always fine
     s.step(2)
     s.destroy()
+
+
+@pytest.mark.parametrize("precision", [fsb.FSB_FP32_KAHAN, fsb.FSB_FP64_STATE])
+@pytest.mark.parametrize("offset", [0, 1])
+def test_pinned_host_transfers_match_the_copy_engine_path(precision, offset):
+    """Pinned host arrays are read and written by kernels (vector groups when
+    every array is 16-byte aligned, one fish per thread otherwise); pageable
+    ones by the copy engines.  Both routes give the same bits, and a school
+    resumed from a pinned checkpoint runs as one resumed from pageable
+    memory."""
+    n = 100_003
+    cfg = stream_cfg(n, 77, precision=precision, init_weight_mode=1)
+    dt = torch.float64 if precision == fsb.FSB_FP64_STATE else torch.float32
+    s = fsb.School.create(cfg)
+    s.step(5)
+    want = s.read()                                   # pageable: copy engines
+    pinned = [torch.empty(n + offset, dtype=dt).pin_memory()[offset:] for _ in range(5)]
+    views = [t.numpy() for t in pinned]
+    assert fsb.fsb_read_state(s.handle, *views) == 5  # pinned: kernels
+    for k, v in zip(("x", "y", "w", "prev", "cur"), views):
+        assert np.array_equal(v, want[k]), k
+    # only some fields, with currentObjective computed on the way out
+    for t in pinned:
+        t.zero_()
+    fsb.fsb_read_state(s.handle, None, views[1], None, None, views[4])
+    assert np.array_equal(views[1], want["y"]) and np.array_equal(views[4], want["cur"])
+    assert not views[0].any()
+    s.destroy()
+    # resume from the pinned arrays, and from pageable copies of them
+    out = []
+    for src in (views[:4], [np.array(v) for v in views[:4]]):
+        r = fsb.School.create(cfg, init=dict(zip(("x", "y", "w", "prev_objective"), src)),
+                              start_step=5)
+        st = r.step(3, stats=True)
+        out.append((r.read(), st))
+        r.destroy()
+    (a, sa), (b, sb) = out
+    for k in ("x", "y", "w", "prev", "cur"):
+        assert np.array_equal(a[k], b[k]), k
+    assert np.array_equal(sa["max_abs_delta"], sb["max_abs_delta"])
