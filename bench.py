@@ -65,9 +65,11 @@ def parse_args():
                     help="override the school size (profiling on a smaller case)")
     ap.add_argument("--stream-kernel", type=int, default=0,
                     help="0 library choice, 1 vector loads, 2 bulk-copy ring, "
-                         "3 warp-specialised bulk-copy ring")
+                         "3 warp-specialised bulk-copy ring, 4 steps blocked by recompute")
     ap.add_argument("--stream-block", type=int, default=0)
     ap.add_argument("--stream-stages", type=int, default=0)
+    ap.add_argument("--stream-block-steps", type=int, default=0,
+                    help="stream kernel 4: steps per pair of passes (2, 4, 8)")
     ap.add_argument("--reference-fish", type=int, default=1 << 22,
                     help="fish per bench step of the CPU reference arm")
     ap.add_argument("--no-e2e", action="store_true")
@@ -151,6 +153,8 @@ ALU_KERNEL_SOURCES = {
     "batch": ("fsb_batch.cu", "fsb_batch_wide.cu", "fsb_batch_kernel.cuh", "fsb_onchip.cuh",
               "fsb_check.cuh", "fsb_device.cuh", "fsb_reduce.cuh"),
     "collective": ("fsb_collective.cu", "fsb_device.cuh", "fsb_reduce.cuh"),
+    "blocked": ("fsb_stream_blocked.cu", "fsb_stream_common.cuh", "fsb_device.cuh",
+                "fsb_reduce.cuh"),
 }
 
 
@@ -752,7 +756,7 @@ def run_ours(args, world, rank, local, pg):
     stream = torch.cuda.current_stream()
 
     tuning = {"stream_kernel": args.stream_kernel, "stream_block": args.stream_block,
-              "stream_stages": args.stream_stages}
+              "stream_stages": args.stream_stages, "stream_block_steps": args.stream_block_steps}
 
     # ---- device-resident timing
     t = time_single(fsb, torch, cfg, steps, warmup, local, pg, tuning)
@@ -779,6 +783,20 @@ def run_ours(args, world, rank, local, pg):
         roof.update({"launches": fused_n, "hbm_achieved_gbs": hbm,
                      "hbm_frac_of_measured": hbm / peak if hbm else None,
                      "algorithmic_bytes_per_launch": bytes_per_fish_step * n})
+    elif tuning["stream_kernel"] == 4:
+        # steps blocked by recompute: each timed unit is a pair of passes
+        # (maxima, step) covering up to K steps; the pairs cover steps - 1
+        # steps of the call.  Bound by instruction issue; the HBM fraction of
+        # its algorithmic bytes (x, y read by the maxima pass; x, y, w, prev
+        # read and written by the step pass: 40 B per fish per pair) beside
+        pair_steps = steps - 1
+        per_step_s = (fused_ms / 1e3) / pair_steps if pair_steps and fused_n else None
+        roof = alu_roofline("blocked", "blocked_maxima_kernel + blocked_step_kernel (pairs)",
+                            args.precision, n, per_step_s, sms, clocks)
+        hbm = 40 * n * fused_n / (fused_ms / 1e3) / 1e9 if fused_n else None
+        roof.update({"launches": fused_n, "steps_per_pair": tuning["stream_block_steps"],
+                     "hbm_achieved_gbs": hbm, "hbm_frac_of_measured": hbm / peak if hbm else None,
+                     "what": "avg_launch_ms and achieved are per fish-step of the pairs"})
     elif path == fsb.FSB_PATH_RESIDENT:
         # one launch advances all `steps` steps with the state on chip: bound
         # by instruction issue, 152 SMs x 4 schedulers x 32 lanes per clock
@@ -843,7 +861,8 @@ def run_ours(args, world, rank, local, pg):
             if args.stream_kernel or args.stream_block or args.stream_stages:
                 fsb.fsb_set_tuning(h, stream_kernel=args.stream_kernel,
                                    stream_block=args.stream_block,
-                                   stream_stages=args.stream_stages)
+                                   stream_stages=args.stream_stages,
+                                   stream_block_steps=args.stream_block_steps)
             stream.synchronize()  # the state's host->device copies are in
             t1 = time.perf_counter()
             fsb.fsb_step(h, steps, stats)

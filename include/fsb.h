@@ -47,8 +47,11 @@ typedef enum {
 
 /* Arithmetic of the state and of the barycentre sums.
  *   FSB_FP32        binary32 state; plain binary32 sums (precision baseline)
- *   FSB_FP32_KAHAN  binary32 state; compensated binary32 per-thread sums,
- *                   combined in binary64 (default)
+ *   FSB_FP32_KAHAN  binary32 state; compensated binary32 sums, combined in
+ *                   binary64 (default).  The streaming kernels compensate
+ *                   each thread's running sums (Kahan); in the on-chip
+ *                   kernels a thread adds at most eight fish pairs per step
+ *                   in plain binary32 and compensation starts at the warp
  *   FSB_FP64_ACC    binary32 state; binary64 sums of exact products
  *   FSB_FP64_STATE  binary64 state and arithmetic; binary64 sums
  * In every binary32 mode the per-fish state is bit-identical; only the sums
@@ -351,7 +354,14 @@ int fsb_set_fault_injection(fsb_handle h, int block, uint32_t step, uint64_t tim
  *   stream_kernel        1: vector loads; 2: bulk asynchronous copies into a
  *                        shared-memory ring (binary32, 16-byte aligned state);
  *                        3: the same ring run by its own producer warp, stages
- *                        released per consumer warp (binary32, aligned state)
+ *                        released per consumer warp (binary32, aligned state);
+ *                        4: steps blocked by recompute -- positions do not
+ *                        depend on weights, so a maxima pass swims the next
+ *                        stream_block_steps steps from the state to find their
+ *                        max |delta| and eat() values, and a step pass then
+ *                        eats and swims them all with one read and write of
+ *                        the state (binary32, aligned state, swim_mode 0; the
+ *                        call's first swim and last eat take kernel 1)
  *   stream_block         threads per block of the streaming pass: 256 or 512
  *                        (kernel 3: consumer threads; the block has 32 more)
  *   stream_blocks_per_sm blocks per SM of the streaming grid (capped by
@@ -367,6 +377,8 @@ int fsb_set_fault_injection(fsb_handle h, int block, uint32_t step, uint64_t tim
  *                        with a fish pair for every thread
  *   stream_stages        bulk-copy kernels: shared-memory tiles in flight per
  *                        block, 2, 3 or 4 (kernel 3: 2 or 3)
+ *   stream_block_steps   kernel 4: steps per pair of passes, 2, 4 or 8
+ *                        (0: 4)
  * A combination that cannot run returns FSB_ERR_INVALID_ARG and leaves the
  * handle unchanged.  Synchronises the handle's stream. */
 typedef struct {
@@ -376,6 +388,7 @@ typedef struct {
     int32_t resident_fpt;
     int32_t resident_block;
     int32_t stream_stages;
+    int32_t stream_block_steps;
 } fsb_tuning;
 
 int fsb_set_tuning(fsb_handle h, const fsb_tuning* t);

@@ -87,7 +87,8 @@ class FsbStepStats(ctypes.Structure):
 class FsbTuning(ctypes.Structure):
     _fields_ = [("stream_kernel", ctypes.c_int32), ("stream_block", ctypes.c_int32),
                 ("stream_blocks_per_sm", ctypes.c_int32), ("resident_fpt", ctypes.c_int32),
-                ("resident_block", ctypes.c_int32), ("stream_stages", ctypes.c_int32)]
+                ("resident_block", ctypes.c_int32), ("stream_stages", ctypes.c_int32),
+                ("stream_block_steps", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -93,6 +93,16 @@ extern "C" int fsb_autotune(const fsb_config* cfg, uint32_t n_steps, int* best_p
           c.t.stream_stages = st;
           cands.push_back(c);
         }
+  if (!dbl && cfg->swim_mode == 0) {
+    const int ks[] = {4, 8};
+    for (int k : ks) {  // steps blocked by recompute
+      Candidate c{};
+      c.path = FSB_PATH_STREAM;
+      c.t.stream_kernel = 4;
+      c.t.stream_block_steps = k;
+      cands.push_back(c);
+    }
+  }
   if (!dbl) {
     const int fpts[] = {4, 8, 12, 16};
     for (int f : fpts) {
