@@ -176,8 +176,7 @@ __device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int r
         fv[h] = objective(xv[h], yv[h]);
       }
     }
-    B.Xd[e] = make_float2(xv[0], xv[1]);
-    B.Yd[e] = make_float2(yv[0], yv[1]);
+    B.XYd[e] = make_float4(xv[0], xv[1], yv[0], yv[1]);
     B.W[e] = make_float2(wv[0], wv[1]);
     B.F[e] = make_float2(fv[0], fv[1]);
   }
@@ -213,11 +212,7 @@ __device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int r
         }
       }
       if (do_eat) {
-        Part3<Part> wp;
-        wp.w = warp_tree(acc.pw());
-        wp.x = warp_tree(acc.px());
-        wp.y = warp_tree(acc.py());
-        if (lane == 0) S.warp_part[p & 1][warp] = wp;
+        warp_partials(&S.warp_part[p & 1][warp], acc.pw(), acc.px(), acc.py());
       }
     }
     if (nb > 1)
@@ -264,7 +259,8 @@ __device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int r
   if (nb > 1) cluster.sync();
 
   for (uint32_t e = tid; e < np; e += kBlockThreads) {
-    const float2 xv = B.Xs[e], yv = B.Ys[e], wv = B.W[e];
+    const float4 p = B.XYs[e];
+    const float2 xv = make_float2(p.x, p.y), yv = make_float2(p.z, p.w), wv = B.W[e];
     const float2 pv = T ? B.De[e] : B.F[e];
     const uint64_t g = s_lo + lo + 2 * e;
     a.x[g] = xv.x;
@@ -285,11 +281,10 @@ template <int CLUSTER, int ACC, bool VAR>
 __global__ void __launch_bounds__(kBlockThreads, 1) batch_kernel(BatchArgs a) {
   __shared__ BatchShared<ACC> S;
   __shared__ uint32_t s_pick;
-  extern __shared__ float2 state_smem[];
-  float2* const X = state_smem;
-  float2* const Y = state_smem + kBlockPairs;
+  extern __shared__ __align__(16) float2 state_smem[];
+  float4* const XY = reinterpret_cast<float4*>(state_smem);  // two float2 arrays' room
   float2* const D = state_smem + 4 * kBlockPairs;
-  const PairState B = pair_state(X, Y, D, X, Y, D, state_smem + 3 * kBlockPairs,
+  const PairState B = pair_state(XY, D, XY, D, state_smem + 3 * kBlockPairs,
                                  state_smem + 2 * kBlockPairs);
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = static_cast<int>(cluster.block_rank());

@@ -173,34 +173,84 @@ __device__ __forceinline__ float exact_scaled_width(float width) {
   return (a >= 0x1p-103f) ? __fmul_rn(width, 0x1p-23f) : 0.f;
 }
 
-// A block's fish.  The eat of a pass reads positions Xe, Ye and the
-// feeding input De; the swim reads positions Xs, Ys and writes Xd, Yd and
-// the next feeding input Dd.  An in-place pass uses one set of arrays for
-// all; the resident kernel's pipelined pass eats step u from one buffer
-// while the swim of step u + 2 reads the other (step u + 1's positions) and
+// A block's fish.  The positions of a swim pair are one float4 (x of fish
+// 0 and 1, then y of fish 0 and 1), so a pass moves them with one 16-byte
+// shared-memory access.  The eat of a pass reads positions XYe and the
+// feeding input De; the swim reads positions XYs and writes XYd and the next
+// feeding input Dd.  An in-place pass uses one set of arrays for all; the
+// resident kernel's pipelined pass eats step u from one buffer while the
+// swim of step u + 2 reads the other (step u + 1's positions) and
 // overwrites the first, pair by pair after its eat.  D holds a step's
 // feeding input (delta, or prev - cur when feeding follows the paper's
 // eat() value) -- except after the school's last swim, when it holds that
 // swim's starting objective (the state's prevObjective) and the final eat
 // forms the input from F and D.
 struct PairState {
-  const float2* Xe;
-  const float2* Ye;
+  const float4* XYe;
   const float2* De;
-  const float2* Xs;
-  const float2* Ys;
-  float2* Xd;
-  float2* Yd;
+  const float4* XYs;
+  float4* XYd;
   float2* Dd;
   float2* F;  // currentObjective
   float2* W;
 };
 
 // The same arrays for the eat and the swim (an in-place or one-buffer pass).
-__device__ __forceinline__ PairState pair_state(const float2* Xs, const float2* Ys,
-                                                const float2* Ds, float2* Xd, float2* Yd,
+__device__ __forceinline__ PairState pair_state(const float4* XYs, const float2* Ds, float4* XYd,
                                                 float2* Dd, float2* F, float2* W) {
-  return PairState{Xs, Ys, Ds, Xs, Ys, Xd, Yd, Dd, F, W};
+  return PairState{XYs, Ds, XYs, XYd, Dd, F, W};
+}
+
+// ------------------------------------------------ warp barycentre partials --
+// The warp's sums of eight binary32 values held by every lane, reduced and
+// scattered at once: each xor level hands half of the values a lane still
+// holds to its partner and adds the half it keeps, so after the levels 16,
+// 8 and 4 a lane holds one value, and levels 2 and 1 finish it.  Lane L ends
+// with the warp's sum of value (L >> 2) & 7 (32 terms, a fixed tree), in 32
+// instructions where six separate trees take 60.
+__device__ __forceinline__ float warp_scatter8(const float (&v)[8]) {
+  const int lane = threadIdx.x & 31;
+  const bool b16 = lane & 16, b8 = lane & 8, b4 = lane & 4;
+  float k[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float keep = b16 ? v[i + 4] : v[i];
+    const float give = b16 ? v[i] : v[i + 4];
+    k[i] = __fadd_rn(keep, __shfl_xor_sync(kFullMask, give, 16));
+  }
+  float h[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float keep = b8 ? k[i + 2] : k[i];
+    const float give = b8 ? k[i] : k[i + 2];
+    h[i] = __fadd_rn(keep, __shfl_xor_sync(kFullMask, give, 8));
+  }
+  float r = __fadd_rn(b4 ? h[1] : h[0], __shfl_xor_sync(kFullMask, b4 ? h[0] : h[1], 4));
+  r = __fadd_rn(r, __shfl_xor_sync(kFullMask, r, 2));
+  r = __fadd_rn(r, __shfl_xor_sync(kFullMask, r, 1));
+  return r;
+}
+
+// A warp's barycentre partials (w, w x, w y) of one step into *dst, a struct
+// of three Parts.  Compensated pairs: the hi and lo words are summed over the
+// warp as six binary32 values (as warp_tree does, one tree each) by
+// warp_scatter8, and lanes 0, 4, .., 20 write them; other types by warp_tree,
+// written by lane 0.
+template <typename P3, typename Part>
+__device__ __forceinline__ void warp_partials(P3* dst, Part w, Part x, Part y) {
+  P3 r;
+  r.w = warp_tree(w);
+  r.x = warp_tree(x);
+  r.y = warp_tree(y);
+  if ((threadIdx.x & 31) == 0) *dst = r;
+}
+template <typename P3>
+__device__ __forceinline__ void warp_partials(P3* dst, F2 w, F2 x, F2 y) {
+  static_assert(sizeof(P3) == 6 * sizeof(float), "three compensated pairs");
+  const float v[8] = {w.hi, w.lo, x.hi, x.lo, y.hi, y.lo, 0.f, 0.f};
+  const float s = warp_scatter8(v);
+  const int lane = threadIdx.x & 31;
+  if ((lane & 3) == 0 && lane < 24) reinterpret_cast<float*>(dst)[lane >> 2] = s;
 }
 
 // Per-pass context of one block.
@@ -223,11 +273,13 @@ template <bool EAT, bool SWIM, bool LAST_SWIM, bool LAST_EAT, bool AHEAD, typena
 __device__ __forceinline__ void pair_pass(const PairState& B, uint32_t e, bool two,
                                           const PassCtx& c, const Physics<float>& ph, Acc& acc,
                                           float& ihi, float& ilo) {
-  float2 xv = B.Xs[e], yv = B.Ys[e], fv = B.F[e];
+  const float4 ps = B.XYs[e];
+  float2 xv = make_float2(ps.x, ps.y), yv = make_float2(ps.z, ps.w), fv = B.F[e];
   float2 wv = (EAT || ph.swim_mode) ? B.W[e] : make_float2(0.f, 0.f);
   if (EAT) {
     const float2 dv = B.De[e];
-    const float2 xe = AHEAD ? B.Xe[e] : xv, ye = AHEAD ? B.Ye[e] : yv;
+    const float4 pe = AHEAD ? B.XYe[e] : ps;
+    const float2 xe = make_float2(pe.x, pe.y), ye = make_float2(pe.z, pe.w);
     float2 g = dv;
     if (LAST_EAT) g = ph.feed_mode ? sub_x2(dv, fv) : sub_x2(fv, dv);
     if (c.N > 0.f) {
@@ -253,8 +305,7 @@ __device__ __forceinline__ void pair_pass(const PairState& B, uint32_t e, bool t
     const float i1 = two ? i.y : i.x;
     ihi = fmaxf(ihi, fmaxf(i.x, i1));
     ilo = fminf(ilo, fminf(i.x, i1));
-    B.Xd[e] = xv;
-    B.Yd[e] = yv;
+    B.XYd[e] = make_float4(xv.x, xv.y, yv.x, yv.y);
     B.F[e] = fv;
     B.Dd[e] = LAST_SWIM ? o : (ph.feed_mode ? i : d);
   }

@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kResThreads + 32, 1) resident_kernel(ResidentA
   using Acc = OnchipAcc<ACC>;
   using Sum = typename Acc::Sum;
   using Part = typename Acc::Part;
-  extern __shared__ float2 res_smem[];
+  extern __shared__ __align__(16) float2 res_smem[];
   __shared__ uint32_t s_bmax[2], s_bkey[2];  // the block's maxima of a step, by parity
   __shared__ ResPart3<Part> s_wpart[2][32];  // the warps' barycentre partials, by parity
   __shared__ uint32_t s_M[2], s_E[2];        // M_u and E_u, by parity
@@ -141,10 +141,8 @@ __global__ void __launch_bounds__(kResThreads + 32, 1) resident_kernel(ResidentA
                               &a.ctl->status, &a.ctl->timeout_site, 0xB0u);
   const uint32_t nf = fits ? nf0 : (nf0 < 2 * cap ? nf0 : 2 * cap);
   const uint32_t np = (nf + 1) / 2;
-  float2* const X0 = res_smem;
-  float2* const X1 = res_smem + cap;
-  float2* const Y0 = res_smem + 2 * cap;
-  float2* const Y1 = res_smem + 3 * cap;
+  float4* const XY0 = reinterpret_cast<float4*>(res_smem);
+  float4* const XY1 = reinterpret_cast<float4*>(res_smem + 2 * cap);
   float2* const D0 = res_smem + 4 * cap;
   float2* const D1 = res_smem + 5 * cap;
   float2* const F = res_smem + 6 * cap;
@@ -152,16 +150,15 @@ __global__ void __launch_bounds__(kResThreads + 32, 1) resident_kernel(ResidentA
   // buffer k holds the positions after (and the feeding input of) the steps
   // of parity k
   auto state = [&](uint32_t from, uint32_t to) -> PairState {
-    return pair_state(from & 1u ? X1 : X0, from & 1u ? Y1 : Y0, from & 1u ? D1 : D0,
-                      to & 1u ? X1 : X0, to & 1u ? Y1 : Y0, to & 1u ? D1 : D0, F, W);
+    return pair_state(from & 1u ? XY1 : XY0, from & 1u ? D1 : D0, to & 1u ? XY1 : XY0,
+                      to & 1u ? D1 : D0, F, W);
   };
   // the pipelined pass of step u: eat step u from buffer u & 1 while the
   // swim of step u + 2 reads buffer (u + 1) & 1 and overwrites buffer u & 1
   auto ahead_state = [&](uint32_t u) -> PairState {
-    float2* const Xu = u & 1u ? X1 : X0;
-    float2* const Yu = u & 1u ? Y1 : Y0;
+    float4* const XYu = u & 1u ? XY1 : XY0;
     float2* const Du = u & 1u ? D1 : D0;
-    return PairState{Xu, Yu, Du, u & 1u ? X0 : X1, u & 1u ? Y0 : Y1, Xu, Yu, Du, F, W};
+    return PairState{XYu, Du, u & 1u ? XY0 : XY1, XYu, Du, F, W};
   };
   const Physics<float> ph = a.ph;
   const uint32_t T = a.n_steps;
@@ -179,8 +176,7 @@ __global__ void __launch_bounds__(kResThreads + 32, 1) resident_kernel(ResidentA
         fv[h] = objective(xv[h], yv[h]);
       }
     }
-    X0[e] = make_float2(xv[0], xv[1]);
-    Y0[e] = make_float2(yv[0], yv[1]);
+    XY0[e] = make_float4(xv[0], xv[1], yv[0], yv[1]);
     W[e] = make_float2(wv[0], wv[1]);
     F[e] = make_float2(fv[0], fv[1]);
   }
@@ -291,11 +287,7 @@ __global__ void __launch_bounds__(kResThreads + 32, 1) resident_kernel(ResidentA
       }
     };
     auto put_partial = [&](uint32_t u, const Acc& acc) {
-      ResPart3<Part> wp;
-      wp.w = warp_tree(acc.pw());
-      wp.x = warp_tree(acc.px());
-      wp.y = warp_tree(acc.py());
-      if (lane == 0) s_wpart[u & 1u][warp] = wp;
+      warp_partials(&s_wpart[u & 1u][warp], acc.pw(), acc.px(), acc.py());
     };
     {
       Acc unused;
@@ -371,7 +363,8 @@ __global__ void __launch_bounds__(kResThreads + 32, 1) resident_kernel(ResidentA
     }
   }
   for (uint32_t e = tid; e < np; e += nthreads) {
-    const float2 xv = (T & 1u ? X1 : X0)[e], yv = (T & 1u ? Y1 : Y0)[e], wv = W[e];
+    const float4 p = (T & 1u ? XY1 : XY0)[e];
+    const float2 xv = make_float2(p.x, p.y), yv = make_float2(p.z, p.w), wv = W[e];
     const float2 pv = T ? (T & 1u ? D1 : D0)[e] : F[e];
     const uint32_t i = lo + 2 * e;
     a.x[i] = xv.x;
