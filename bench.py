@@ -484,7 +484,12 @@ def run_precision(args, world, rank, local):
     over those schools, the error of the first school's barycentre sums at
     steps 1, 10, 100 and 1000 against the exact sums of its read-back state
     (normalised by sum |w x|), and the drift between the binary32 and the
-    binary64 trajectories (the same draws, different rounding)."""
+    binary64 trajectories (the same draws, different rounding).  Beside them,
+    the CPU oracle runs the first school's first 100 steps (its OpenMP step,
+    binary32 and binary64 state, sums compensated in binary64 over exact
+    products): every step's sums of each mode against it, its maxima, the
+    whole state at step 100 bit for bit, and the binary32 modes' drift from
+    the binary64 oracle's trajectory."""
     import torch
 
     import paper_2507_20173_gb300 as fsb
@@ -499,6 +504,18 @@ def run_precision(args, world, rank, local):
     stream = torch.cuda.current_stream()
     modes = {}
     finals = {}
+    # the oracle's trajectories of school 0 (seed 100) over the first steps
+    import oracle
+    ostep = min(100, total)
+    if ostep not in marks:
+        marks = sorted(set(marks) | {ostep})
+    ocfg = oracle.Config(n_fish=n, seed=100)
+    oref, ostats, otime = {}, {}, {}
+    for prec in ("f32", "f64"):
+        t0 = time.perf_counter()
+        oref[prec] = oracle.init(ocfg, prec)
+        ostats[prec] = oracle.run_omp(ocfg, oref[prec], 0, ostep)
+        otime[prec] = time.perf_counter() - t0
     for name in ("FP32", "FP32_KAHAN", "FP64_ACC", "FP64_STATE"):
         cfg = fsb.fsb_config_init(n, 100, precision=getattr(fsb, "FSB_" + name),
                                   path=fsb.FSB_PATH_STREAM)
@@ -506,6 +523,8 @@ def run_precision(args, world, rank, local):
         errs = {}
         done = 0
         elapsed = 0.0
+        gstats = []
+        at_ostep = None
         start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         for m in marks:
             k = m - done
@@ -516,7 +535,10 @@ def run_precision(args, world, rank, local):
             torch.cuda.synchronize()
             elapsed += start.elapsed_time(stop) / 1e3
             done = m
+            gstats.append(st)
             got = s.read()
+            if m == ostep:
+                at_ostep = got
             ex = exact_sums(got["w"], got["x"], got["y"])
             last = st[-1]
             errs[str(m)] = {
@@ -526,6 +548,29 @@ def run_precision(args, world, rank, local):
                 "bary_x_abs_err": abs(last["sum_wx"] / last["sum_w"] - ex["sum_wx"] / ex["sum_w"])}
         finals[name] = got
         s.destroy()
+        # against the oracle of the same state precision, steps 1 .. ostep
+        prec = "f64" if name == "FP64_STATE" else "f32"
+        g = np.concatenate(gstats)[:ostep]
+        o = ostats[prec]
+        r = oref[prec]
+        same = {k: bool(np.array_equal(at_ostep[k], r[f])) for k, f in
+                (("x", "x"), ("y", "y"), ("w", "weight"), ("prev", "prevObjective"),
+                 ("cur", "currentObjective"))}
+        vs_oracle = {
+            "steps": ostep, "oracle_state": prec,
+            "max_err_sum_w": float(np.max(np.abs(g["sum_w"] - o["sum_w"]) / np.abs(o["sum_w"]))),
+            "max_err_sum_wx": float(np.max(np.abs(g["sum_wx"] - o["sum_wx"]) / o["sum_abs_wx"])),
+            "max_err_sum_wy": float(np.max(np.abs(g["sum_wy"] - o["sum_wy"]) / o["sum_abs_wy"])),
+            "max_abs_delta_every_step_equal": bool(np.array_equal(g["max_abs_delta"],
+                                                                  o["max_abs_delta"])),
+            "eat_max_diff_every_step_equal": bool(np.array_equal(g["eat_max_diff"],
+                                                                 o["eat_max_diff"])),
+            "state_bitwise_equal_at_last_step": same}
+        if prec == "f32":
+            r64 = oref["f64"]
+            vs_oracle["drift_from_binary64_oracle"] = {
+                k: float(np.max(np.abs(at_ostep[k].astype(np.float64) - r64[f])))
+                for k, f in (("x", "x"), ("y", "y"), ("w", "weight"))}
         # the ensemble's other schools, timed over the whole call
         for k in range(1, max(1, args.precision_schools)):
             cfg_k = fsb.fsb_config_init(n, 100 + k, precision=getattr(fsb, "FSB_" + name),
@@ -540,7 +585,7 @@ def run_precision(args, world, rank, local):
             sk.destroy()
         schools = max(1, args.precision_schools)
         modes[name] = {"fish_steps_per_s": schools * n * total / elapsed, "errors": errs,
-                       "schools_timed": schools}
+                       "schools_timed": schools, "vs_oracle": vs_oracle}
     drift = {f: float(np.max(np.abs(finals["FP32_KAHAN"][f].astype(np.float64) -
                                     finals["FP64_STATE"][f])))
              for f in ("x", "y", "w")}
@@ -556,7 +601,9 @@ def run_precision(args, world, rank, local):
                                           total),
                            "note": "schools of the 64-school ensemble, timed per mode; errors "
                                    "of the first against exact host sums of its read-back "
-                                   "state"},
+                                   "state, and every step of its first %d against the CPU "
+                                   "oracle (OpenMP step; %.1f s binary32, %.1f s binary64)"
+                                   % (ostep, otime["f32"], otime["f64"])},
                 "modes": modes, "trajectory_drift_fp32_vs_fp64_state": drift}
         print(json.dumps(line), flush=True)
 
