@@ -54,6 +54,7 @@ static_assert(kBatchThreads % 32 == 0 && kBatchThreads <= 992, "fish threads: wh
 constexpr int kBatchWarps = kBatchThreads / 32;
 constexpr int kBlockThreads = kBatchThreads + 32;  // and one helper warp
 constexpr int kBlockFish = 8192;              // fish one block holds
+constexpr int kBatchPairsPerIter = 1;         // fish pairs per thread per iteration of a pass
 constexpr int kBlockPairs = kBlockFish / 2;
 constexpr int kMaxCluster = 8;
 // The block's fish in shared memory: five arrays of kBlockPairs float2
@@ -194,15 +195,15 @@ __device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int r
       uint32_t mb = 0, ek = 0;
       Acc acc;
       if (p == 0 && T > 1)
-        block_pass<false, true, false, false>(B, np, nf, c, ph, acc, mb, ek, kBatchThreads);
+        block_pass<false, true, false, false, false, kBatchPairsPerIter>(B, np, nf, c, ph, acc, mb, ek, kBatchThreads);
       else if (p == 0 && T == 1)
-        block_pass<false, true, true, false>(B, np, nf, c, ph, acc, mb, ek, kBatchThreads);
+        block_pass<false, true, true, false, false, kBatchPairsPerIter>(B, np, nf, c, ph, acc, mb, ek, kBatchThreads);
       else if (p + 1 < T)
-        block_pass<true, true, false, false>(B, np, nf, c, ph, acc, mb, ek, kBatchThreads);
+        block_pass<true, true, false, false, false, kBatchPairsPerIter>(B, np, nf, c, ph, acc, mb, ek, kBatchThreads);
       else if (p + 1 == T)
-        block_pass<true, true, true, false>(B, np, nf, c, ph, acc, mb, ek, kBatchThreads);
+        block_pass<true, true, true, false, false, kBatchPairsPerIter>(B, np, nf, c, ph, acc, mb, ek, kBatchThreads);
       else if (p == T)
-        block_pass<true, false, false, true>(B, np, nf, c, ph, acc, mb, ek, kBatchThreads);
+        block_pass<true, false, false, true, false, kBatchPairsPerIter>(B, np, nf, c, ph, acc, mb, ek, kBatchThreads);
       if (do_swim) {
         mb = warp_max(mb);
         ek = warp_max(ek);

@@ -313,24 +313,30 @@ __device__ __forceinline__ void pair_pass(const PairState& B, uint32_t e, bool t
 
 // All of this thread's pairs in one pass: elements threadIdx.x,
 // threadIdx.x + step, ... below np (nf fish), where step is the number of
-// threads that share the pass (threads 0 .. step - 1), two per iteration so
-// that two independent draws overlap.  The thread's maxima of the pass's
-// swim go into mb (bits of max |delta|) and ek (order key of max(prev -
-// cur)): prev - cur is never -0 (x - x is +0), so the float extremes order
-// like the keys.
-template <bool EAT, bool SWIM, bool LAST_SWIM, bool LAST_EAT, bool AHEAD = false, typename Acc>
+// threads that share the pass (threads 0 .. step - 1), ITER per iteration
+// so that independent draws overlap (measured on GB300 over 1 to 4: the
+// resident kernel runs fastest at 2, 3 within 1%; the batch kernel at 1).
+// The thread's maxima of the pass's swim go into mb (bits of max |delta|)
+// and ek (order key of max(prev - cur)): prev - cur is never -0 (x - x is
+// +0), so the float extremes order like the keys.
+template <bool EAT, bool SWIM, bool LAST_SWIM, bool LAST_EAT, bool AHEAD = false, int ITER = 2,
+          typename Acc>
 __device__ __forceinline__ void block_pass(const PairState& B, uint32_t np, uint32_t nf,
                                            const PassCtx& c, const Physics<float>& ph, Acc& acc,
                                            uint32_t& mb, uint32_t& ek, uint32_t step) {
   float ihi = -__int_as_float(0x7f800000), ilo = __int_as_float(0x7f800000);
+  static_assert(ITER >= 1 && ITER <= 4, "1 to 4 pairs per iteration");
+  constexpr uint32_t kIter = ITER;
   uint32_t e = threadIdx.x;
-  for (; e + step < np; e += 2 * step) {
-    pair_pass<EAT, SWIM, LAST_SWIM, LAST_EAT, AHEAD>(B, e, true, c, ph, acc, ihi, ilo);
-    const uint32_t e2 = e + step;
-    pair_pass<EAT, SWIM, LAST_SWIM, LAST_EAT, AHEAD>(B, e2, 2 * e2 + 1 < nf, c, ph, acc, ihi,
-                                                     ilo);
+  for (; e + (kIter - 1) * step < np; e += kIter * step) {
+#pragma unroll
+    for (uint32_t k = 0; k < kIter; ++k) {
+      const uint32_t ek2 = e + k * step;  // only the group's last pair can be the half pair
+      pair_pass<EAT, SWIM, LAST_SWIM, LAST_EAT, AHEAD>(B, ek2, k + 1 < kIter || 2 * ek2 + 1 < nf,
+                                                       c, ph, acc, ihi, ilo);
+    }
   }
-  if (e < np)
+  for (; e < np; e += step)
     pair_pass<EAT, SWIM, LAST_SWIM, LAST_EAT, AHEAD>(B, e, 2 * e + 1 < nf, c, ph, acc, ihi, ilo);
   if (SWIM && ihi >= ilo) {  // at least one fish swum
     mb = max(mb, abs_bits(fmaxf(ihi, -ilo)));
