@@ -54,7 +54,11 @@ static_assert(kBatchThreads % 32 == 0 && kBatchThreads <= 992, "fish threads: wh
 constexpr int kBatchWarps = kBatchThreads / 32;
 constexpr int kBlockThreads = kBatchThreads + 32;  // and one helper warp
 constexpr int kBlockFish = 8192;              // fish one block holds
-constexpr int kBatchPairsPerIter = 1;         // fish pairs per thread per iteration of a pass
+#ifndef FSB_BATCH_PAIRS_PER_ITER
+#define FSB_BATCH_PAIRS_PER_ITER 1
+#endif
+// fish pairs per thread per iteration of a pass (a build-time constant)
+constexpr int kBatchPairsPerIter = FSB_BATCH_PAIRS_PER_ITER;
 constexpr int kBlockPairs = kBlockFish / 2;
 constexpr int kMaxCluster = 8;
 // The block's fish in shared memory: five arrays of kBlockPairs float2
