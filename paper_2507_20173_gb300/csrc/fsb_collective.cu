@@ -49,7 +49,6 @@ struct CollArgs {
   Real s_vol;
   Real g_p, g_g, g_w;  // grid scales 2^kp, 2^kg, 2^kw (exact)
   int kp, kg;
-  int wide;            // terms may exceed 2^43 (schools below 2^19 fish)
   Ctl* ctl;
   CollPartial* partials;
   fsb_step_stats* ring;
@@ -157,8 +156,8 @@ __device__ __forceinline__ long long round_shifted(uint64_t sig, int s, bool neg
 //    lands in [2^23, 2^24), where the spacing is 1, so the sum is rounded to
 //    an integer, ties to even, and its bits minus M's bits are that integer.
 // x_hi is a multiple of 2^22 (even), so round(x) = x_hi + round(x_lo).
-// Smaller schools (`wide`, uniform over the launch) can have terms up to
-// 2^62.  A binary32 value of magnitude 2^23 or more is already an integer:
+// Smaller schools (`wide`: the kernel copy compiled for them) can have
+// terms up to 2^62.  A binary32 value of magnitude 2^23 or more is already an integer:
 // its 24-bit significand shifted left by (biased exponent - 150), at most 39
 // places.  Below 2^23 the FMA-pipe rounding above applies.
 __device__ __forceinline__ long long grid_term(float v, float scale, bool wide) {
@@ -224,7 +223,7 @@ __device__ __forceinline__ bool coll_prologue(Ctl* ctl, uint32_t n_steps, uint32
 
 // Swim of one fish at step t with draw words (r0, r1): the maxima keys, and
 // (when it improved) its instinctive terms dx g, dy g and g on the grid.
-template <typename Real, typename B>
+template <bool WIDE, typename Real, typename B>
 __device__ __forceinline__ void swim_fish(Real& x, Real& y, Real& cur, Real w, uint32_t r0,
                                           uint32_t r1, const CollArgs<Real>& a, B& maxb,
                                           B& ekey, long long (&q)[4]) {
@@ -239,14 +238,16 @@ __device__ __forceinline__ void swim_fish(Real& x, Real& y, Real& cur, Real w, u
   maxb = mb > maxb ? mb : maxb;
   ekey = ek > ekey ? ek : ekey;
   if (g > Real(0)) {
-    q[0] += grid_term(A::mul(A::sub(x, x0), g), a.g_p, a.wide);
-    q[1] += grid_term(A::mul(A::sub(y, y0), g), a.g_p, a.wide);
-    q[2] += grid_term(g, a.g_g, a.wide);
+    q[0] += grid_term(A::mul(A::sub(x, x0), g), a.g_p, WIDE);
+    q[1] += grid_term(A::mul(A::sub(y, y0), g), a.g_p, WIDE);
+    q[2] += grid_term(g, a.g_g, WIDE);
   }
   cur = ncur;
 }
 
-template <typename Real, int PASS, int ACC>
+// WIDE: terms may exceed 2^43 (schools below 2^19 fish; see grid_term),
+// a separate copy so that larger schools carry no test for it.
+template <typename Real, int PASS, int ACC, bool WIDE>
 __global__ void __launch_bounds__(kCollBlock, 4) coll_kernel(CollArgs<Real> a) {
   using A = Arith<Real>;
   using Bt = typename Bits<Real>::type;
@@ -300,10 +301,10 @@ __global__ void __launch_bounds__(kCollBlock, 4) coll_kernel(CollArgs<Real> a) {
 #pragma unroll
       for (int f = 0; f < 2; ++f) {
         if (f < nf) {
-          q[3] += grid_term(w[f], a.g_w, a.wide);  // the school's weight before the first eat
+          q[3] += grid_term(w[f], a.g_w, WIDE);  // the school's weight before the first eat
           Real cur = objective(x[f], y[f]);
           pv[f] = cur;                     // prevObjective after this swim
-          swim_fish(x[f], y[f], cur, w[f], r.v[2 * f], r.v[2 * f + 1], a, maxb, ekey, q);
+          swim_fish<WIDE>(x[f], y[f], cur, w[f], r.v[2 * f], r.v[2 * f + 1], a, maxb, ekey, q);
         }
       }
     } else if (PASS == kCEat) {
@@ -316,9 +317,9 @@ __global__ void __launch_bounds__(kCollBlock, 4) coll_kernel(CollArgs<Real> a) {
           acc.add(w[f], x[f], y[f]);
           x[f] = A::clamp(A::add(x[f], ix), -a.ph.pond_half, a.ph.pond_half);
           y[f] = A::clamp(A::add(y[f], iy), -a.ph.pond_half, a.ph.pond_half);
-          q[0] += grid_term(w[f], a.g_w, a.wide);
-          q[1] += grid_term(A::mul(w[f], x[f]), a.g_w, a.wide);
-          q[2] += grid_term(A::mul(w[f], y[f]), a.g_w, a.wide);
+          q[0] += grid_term(w[f], a.g_w, WIDE);
+          q[1] += grid_term(A::mul(w[f], x[f]), a.g_w, WIDE);
+          q[2] += grid_term(A::mul(w[f], y[f]), a.g_w, WIDE);
         }
       }
     } else {
@@ -349,7 +350,7 @@ __global__ void __launch_bounds__(kCollBlock, 4) coll_kernel(CollArgs<Real> a) {
           if (f < nf) {
             Real cur = objective(x[f], y[f]);
             pv[f] = cur;  // prevObjective after this swim
-            swim_fish(x[f], y[f], cur, w[f], r.v[2 * f], r.v[2 * f + 1], a, maxb, ekey, q);
+            swim_fish<WIDE>(x[f], y[f], cur, w[f], r.v[2 * f], r.v[2 * f + 1], a, maxb, ekey, q);
           }
         }
       }
@@ -546,24 +547,32 @@ __global__ void __launch_bounds__(kCollBlock, 4) coll_kernel(CollArgs<Real> a) {
   __threadfence();
 }
 
-template <typename Real, int PASS>
+template <typename Real, int PASS, bool WIDE>
 const void* pick_acc(int acc) {
-  if (sizeof(Real) == 8) return reinterpret_cast<const void*>(&coll_kernel<Real, PASS, kAccF64>);
+  if (sizeof(Real) == 8)
+    return reinterpret_cast<const void*>(&coll_kernel<Real, PASS, kAccF64, false>);
   switch (acc) {
-    case kAccPlain32: return reinterpret_cast<const void*>(&coll_kernel<Real, PASS, kAccPlain32>);
-    case kAccKahan32: return reinterpret_cast<const void*>(&coll_kernel<Real, PASS, kAccKahan32>);
-    case kAccF64: return reinterpret_cast<const void*>(&coll_kernel<Real, PASS, kAccF64>);
+    case kAccPlain32:
+      return reinterpret_cast<const void*>(&coll_kernel<Real, PASS, kAccPlain32, WIDE>);
+    case kAccKahan32:
+      return reinterpret_cast<const void*>(&coll_kernel<Real, PASS, kAccKahan32, WIDE>);
+    case kAccF64: return reinterpret_cast<const void*>(&coll_kernel<Real, PASS, kAccF64, WIDE>);
     default: return nullptr;
   }
 }
 
+template <typename Real, int PASS>
+const void* pick_wide(int acc, bool wide) {
+  return wide ? pick_acc<Real, PASS, true>(acc) : pick_acc<Real, PASS, false>(acc);
+}
+
 template <typename Real>
-const void* pick_pass(int pass, int acc) {
+const void* pick_pass(int pass, int acc, bool wide) {
   switch (pass) {
-    case kCSwim0: return pick_acc<Real, kCSwim0>(acc);
-    case kCEat: return pick_acc<Real, kCEat>(acc);
-    case kCMove: return pick_acc<Real, kCMove>(acc);
-    case kCMoveLast: return pick_acc<Real, kCMoveLast>(acc);
+    case kCSwim0: return pick_wide<Real, kCSwim0>(acc, wide);
+    case kCEat: return pick_wide<Real, kCEat>(acc, wide);
+    case kCMove: return pick_wide<Real, kCMove>(acc, wide);
+    case kCMoveLast: return pick_wide<Real, kCMoveLast>(acc, wide);
     default: return nullptr;
   }
 }
@@ -592,9 +601,6 @@ CollArgs<Real> make_args(const CollLaunch& L, uint32_t n_steps) {
   a.g_w = static_cast<Real>(ldexp(1.0, L.kw));
   a.kp = L.kp;
   a.kg = L.kg;
-  // every sum of N terms is within 2^62, so a term exceeds 2^43 only when
-  // N < 2^19
-  a.wide = L.n < (1ull << 19) ? 1 : 0;
   a.ctl = L.ctl;
   a.partials = L.partials;
   a.ring = L.ring;
@@ -619,8 +625,11 @@ int coll_grid(const CollLaunch& L, int sms) {
 
 cudaError_t launch_coll_pass(const CollLaunch& L, int pass_kind, uint32_t n_steps,
                              cudaStream_t s) {
-  const void* fn = L.real_is_double ? pick_pass<double>(pass_kind, L.acc)
-                                    : pick_pass<float>(pass_kind, L.acc);
+  // every sum of N terms is within 2^62, so a term exceeds 2^43 only when
+  // N < 2^19
+  const bool wide = L.n < (1ull << 19);
+  const void* fn = L.real_is_double ? pick_pass<double>(pass_kind, L.acc, wide)
+                                    : pick_pass<float>(pass_kind, L.acc, wide);
   if (!fn || L.grid <= 0) return cudaErrorInvalidValue;
   if (L.real_is_double) {
     CollArgs<double> a = make_args<double>(L, n_steps);
