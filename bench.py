@@ -355,10 +355,11 @@ def measure_batch(args, world, rank, local, pg):
         fsb.fsb_batch_set_cluster(b, args.batch_cluster)
     fsb.fsb_batch_step(b, warmup)
     fsb.fsb_batch_step(b, steps)          # captures the timed call's graph
-    fsb.fsb_batch_set_timing(b, True)
-    barrier()
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
+        fsb.fsb_batch_step(b, warmup)     # warm again after the sampler's start-up pause
+        fsb.fsb_batch_set_timing(b, True)
+        barrier()
         start.record(stream)
         fsb.fsb_batch_step(b, steps)
         stop.record(stream)
@@ -701,11 +702,14 @@ def time_single(fsb, torch, cfg, steps, warmup, local, pg, tuning):
     # enabling again clears the warm-up's times
     fsb.fsb_set_kernel_timing(school.handle, True)
     school.step(warmup)
-    fsb.fsb_set_kernel_timing(school.handle, True)
-    fsb.fsb_kernel_time(school.handle)
-    barrier(torch, pg)
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
+        # warm again after the sampler's start-up pause (an idle GPU timed
+        # short calls slow), then clear the warm-up's kernel times
+        school.step(warmup)
+        fsb.fsb_set_kernel_timing(school.handle, True)
+        fsb.fsb_kernel_time(school.handle)
+        barrier(torch, pg)
         start.record(stream)
         fsb.fsb_step(school.handle, steps)
         stop.record(stream)
@@ -763,10 +767,10 @@ def static_record(fsb, torch, cfg, steps, warmup, local):
     stream = torch.cuda.current_stream()
     school = fsb.School.create(cfg, stream=stream)   # its arrays, initialised
     state = fsb.FsbStateDev(*(t.data_ptr() for t in school.tensors))
-    fsb.fsb_step_static(cfg, state, 0, warmup, None, stream.cuda_stream)
-    torch.cuda.synchronize()
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
+        fsb.fsb_step_static(cfg, state, 0, warmup, None, stream.cuda_stream)
+        torch.cuda.synchronize()
         start.record(stream)
         fsb.fsb_step_static(cfg, state, warmup, steps, None, stream.cuda_stream)
         stop.record(stream)
