@@ -82,3 +82,32 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(fsb, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(ImportError):
         fsb.lib()
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes structures of the binding have the size and field offsets
+    of the C structures in include/fsb.h (a small C program prints them)."""
+    structs = {"fsb_config": fsb.FsbConfig, "fsb_state_dev": fsb.FsbStateDev,
+               "fsb_state_host": fsb.FsbStateHost, "fsb_step_stats": fsb.FsbStepStats,
+               "fsb_tuning": fsb.FsbTuning}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "fsb.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append('  printf("%s sizeof %%zu\\n", sizeof(%s));' % (cname, cname))
+        for fname, _ in py._fields_:
+            lines.append('  printf("%s %s %%zu\\n", offsetof(%s, %s));'
+                         % (cname, fname, cname, fname))
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                               check=True).stdout.splitlines():
+        cname, field, value = line.split()
+        got[(cname, field)] = int(value)
+    for cname, py in structs.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
