@@ -244,8 +244,9 @@ int fsb_destroy(fsb_handle h);
  *   n_schools   >= 1
  *   offsets     host array of n_schools + 1 increasing fish offsets,
  *               offsets[0] = 0; school k is fish [offsets[k], offsets[k+1])
- *               and holds >= 1 fish and at most 65536 (a cluster of eight
- *               blocks; larger schools -> FSB_ERR_UNSUPPORTED, use fsb_create)
+ *               and holds >= 1 fish and at most 8 * block_fish = 90112 (a
+ *               cluster of eight blocks, fsb_batch_limits; larger schools
+ *               -> FSB_ERR_UNSUPPORTED, use fsb_create)
  *   seeds       host array of n_schools keys; school k uses key seeds[k] and
  *               school id k, so it reproduces a single-school run created
  *               with that seed and school_id = k
@@ -264,19 +265,29 @@ int fsb_batch_create(const fsb_config* tmpl, uint32_t n_schools, const uint64_t*
                      const uint64_t* seeds, const fsb_state_dev* state, int init,
                      uint64_t start_step, void* cuda_stream, fsb_batch_handle* out);
 
+/* Capacities of the batched kernel (any pointer may be NULL): *block_fish
+ * fish one block holds on chip (11264; a school on a cluster of c blocks,
+ * c <= *max_cluster = 8, holds up to c times that), and *team_fish fish
+ * one warp of a packed team holds (704: schools of at most 8, 4, 2 and 1
+ * times that run on teams of 8, 4, 2 and 1 warps, several to a block; 0
+ * if the library was built without packing).  Needs no GPU. */
+int fsb_batch_limits(uint64_t* block_fish, uint64_t* team_fish, int* max_cluster);
+
 /* Advance every school of the batch by n_steps.  Asynchronous on the
  * batch's stream unless stats is given (then synchronises and fills it). */
 int fsb_batch_step(fsb_batch_handle b, uint32_t n_steps, fsb_step_stats* stats);
 
 /* Cluster size of the batch's schools.
  *   0 (default): each school runs on the smallest cluster (1 to 8 blocks of
- *     8192 fish) that holds it.  One persistent launch per cluster size in
+ *     block_fish fish) that holds it, a school of at most half a block on
+ *     the smallest packed team that holds it.  One persistent launch per cluster size in
  *     use runs concurrently with the others, each on a share of the SMs
  *     proportional to its schools' fish times a measured cost per fish of
  *     that width; single-block schools take the SMs left over, and every launch helps with the schools of smaller clusters
  *     once its own are done.
  *   1 to 8: every school larger than one block runs on clusters of this
- *     size (one launch on every SM it can hold, single blocks beside it).
+ *     size (one launch on every SM it can hold, single blocks beside it);
+ *     1 also runs every school on a block of its own (no packing).
  * Too small for the largest school -> FSB_ERR_UNSUPPORTED; another value ->
  * FSB_ERR_INVALID_ARG.  Synchronises. */
 int fsb_batch_set_cluster(fsb_batch_handle b, int cluster);
@@ -291,9 +302,12 @@ int fsb_batch_info(fsb_batch_handle b, int* cluster, int* n_clusters, int* fille
 /* The batch's launch plan (any pointer may be NULL): n_launches (1 to 8)
  * concurrent persistent launches, launch i running clusters of cluster[i]
  * blocks on a grid of blocks[i] blocks (arrays of 8; entries past
- * n_launches are 0), and queue_schools[t] (array of 8) schools in the work
- * queue of clusters of 8 - t blocks (t = 0 .. 6) and of single blocks
- * (t = 7). */
+ * n_launches are 0), and queue_schools[t] (array of 12) schools in the
+ * work queue of clusters of 8 - t blocks (t = 0 .. 6), of single blocks
+ * (t = 7), and of schools packed several to a block on teams of 8, 4, 2
+ * and 1 warps (t = 8 .. 11: at most 8, 4, 2 and 1 times team_fish fish;
+ * every school of at most half a block is packed unless the cluster size
+ * is forced to 1). */
 int fsb_batch_plan(fsb_batch_handle b, int* n_launches, int* cluster, int* blocks,
                    uint32_t* queue_schools);
 

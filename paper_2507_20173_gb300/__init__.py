@@ -48,7 +48,8 @@ EXPORTED = ("fsb_config_init", "fsb_create", "fsb_step", "fsb_read_state",
             "fsb_set_tuning", "fsb_get_tuning", "fsb_batch_create", "fsb_batch_step",
             "fsb_batch_set_cluster", "fsb_batch_info", "fsb_batch_set_timing",
             "fsb_batch_kernel_time", "fsb_batch_destroy", "fsb_autotune",
-            "fsb_autotune_batch", "fsb_eat_max", "fsb_batch_plan", "fsb_batch_set_plan")
+            "fsb_autotune_batch", "fsb_eat_max", "fsb_batch_plan", "fsb_batch_set_plan",
+            "fsb_batch_limits")
 
 
 class FsbError(RuntimeError):
@@ -134,6 +135,7 @@ def lib() -> ctypes.CDLL:
         "fsb_batch_plan": [P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
                            ctypes.POINTER(u32)],
         "fsb_batch_set_plan": [P, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)],
+        "fsb_batch_limits": [ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(i32)],
         "fsb_batch_set_timing": [P, i32],
         "fsb_batch_kernel_time": [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u64)],
         "fsb_batch_destroy": [P],
@@ -294,16 +296,28 @@ def fsb_batch_info(handle: int) -> dict:
             "n_big": nb.value, "step": st.value}
 
 
+def fsb_batch_limits() -> dict:
+    """Fish one block of the batched kernel holds, fish one warp of a packed
+    team holds (0: no packing), and the widest cluster."""
+    bf, tf, mc = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_int()
+    _check(lib().fsb_batch_limits(ctypes.byref(bf), ctypes.byref(tf), ctypes.byref(mc)),
+           "fsb_batch_limits")
+    return {"block_fish": bf.value, "team_fish": tf.value, "max_cluster": mc.value}
+
+
 def fsb_batch_plan(handle: int) -> dict:
-    """The batch's concurrent launches (cluster size, grid) and the schools
-    in each work queue, keyed by the queue's cluster size (8 down to 1)."""
+    """The batch's concurrent launches (cluster size, grid), the schools in
+    each work queue keyed by the queue's cluster size (8 down to 1), and the
+    schools packed several to a block, keyed by the team's warps (8 down to
+    1)."""
     n = ctypes.c_int()
     c, b = (ctypes.c_int * 8)(), (ctypes.c_int * 8)()
-    q = (ctypes.c_uint32 * 8)()
+    q = (ctypes.c_uint32 * 12)()
     _check(lib().fsb_batch_plan(ctypes.c_void_p(handle), ctypes.byref(n), c, b, q),
            "fsb_batch_plan")
     return {"launches": [{"cluster": c[i], "blocks": b[i]} for i in range(n.value)],
-            "queue_schools": {8 - t: q[t] for t in range(7)} | {1: q[7]}}
+            "queue_schools": {8 - t: q[t] for t in range(7)} | {1: q[7]},
+            "packed_schools": {8 >> t: q[8 + t] for t in range(4)}}
 
 
 def fsb_batch_set_plan(handle: int, launches) -> None:

@@ -4,12 +4,12 @@
 // Thread-block clusters of C blocks pop schools from work queues sorted by
 // size, largest first (longest-processing-time order), through atomic
 // counters over a ragged offset table, and run all n_steps of a school on
-// chip: each block keeps up to 8192 fish (x, y, weight, currentObjective and
+// chip: each block keeps up to 11264 fish (x, y, weight, currentObjective and
 // the feeding input) in shared memory and runs one compact pass over them
 // per step -- the eat of step p fused with the swim of step p + 1, as in the
 // streaming kernel -- so the step's code stays small and a school of a few
 // hundred fish costs little more than its own pairs.  A school goes to the
-// queue of the narrowest cluster that holds it (ceil(n / 8192) blocks, 1 to
+// queue of the narrowest cluster that holds it (ceil(n / 11264) blocks, 1 to
 // 8, so every block is at least half full):
 //   - a cluster first takes schools from the queue of its own size, then
 //     from the queues of smaller multi-block clusters; the warps of its C
@@ -18,7 +18,14 @@
 //     and the barycentre partials follow one and two barriers behind, folded
 //     in a fixed order;
 //   - when those run out, every block pops single-block schools on its own
-//     and synchronises with __syncthreads only.
+//     and synchronises with __syncthreads only;
+//   - then schools of at most half a block are packed: the block's fish
+//     warps split into teams (8, then 4, 2 and 1 warps), each with its own
+//     share of the shared memory and its own named barrier (a single warp
+//     needs none), popping schools that fill at least half of it.  A small
+//     school thus runs beside others instead of leaving most of a block's
+//     warps idle at every step's barrier (on one block, a school of 256
+//     fish runs at a sixth of the rate per fish of a full one).
 // The per-step order within a school is the paper's (Sec. 2.1.2 swim,
 // Sec. 2.1.1 objective, delta, the Sec. 2.3.2 max, feeding, barycentre).
 // School k uses key seeds[k] and school id k, so it reproduces the
@@ -82,6 +89,7 @@ cudaError_t launch_bump_step(unsigned long long* base_step, uint32_t n, cudaStre
 }
 
 uint64_t batch_block_capacity() { return kBlockFish; }
+uint64_t batch_team_fish() { return kTeamFish; }
 
 void batch_finish_stats(fsb_step_stats* st, size_t count, int acc) {
   if (acc == kAccF64) return;

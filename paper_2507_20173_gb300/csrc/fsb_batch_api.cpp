@@ -76,9 +76,12 @@ struct fsb_batch {
 
 namespace {
 
-// Work queues and launches of a batch.  A school one block holds goes to
-// the single-block queue; a larger one to the queue of the smallest cluster
-// that holds it (or, with a forced cluster size, to that size's queue).
+// Work queues and launches of a batch.  A school of at most half a block
+// goes to the packed queue of the smallest team of warps that holds it
+// (with a forced cluster size of 1: to the single-block queue), another
+// school one block holds to the single-block queue, a larger one to the
+// queue of the smallest cluster that holds it (or, with a forced cluster
+// size, to that size's queue).
 // Each queue is largest first (longest-processing-time order).  One
 // persistent launch per multi-block cluster size in use gets a share of the
 // SMs in proportion to its queue's fish (with a forced size: every SM it
@@ -102,12 +105,20 @@ int plan_batch(fsb_batch* b, int forced) {
   }
   std::vector<uint32_t> queue[fsb::kBatchQueues];
   uint64_t fish[fsb::kBatchQueues] = {};
+  // schools of at most half a block are packed on teams of warps, unless
+  // every school is to run on a block of its own (forced cluster size 1)
+  const uint64_t team = forced == 1 ? 0 : fsb::batch_team_fish();
   for (uint32_t k : b->sizes_sorted) {
     const uint64_t n = b->offsets[k + 1] - b->offsets[k];
     const int need = static_cast<int>((n + cap - 1) / cap);  // blocks that hold it
     const int c = need <= 1 ? 1 : (forced ? forced : width_for[need]);
     if (c < 1) return bfail(FSB_ERR_UNSUPPORTED, "no resident cluster holds %d blocks", need);
-    const int t = fsb::batch_queue_of(c);
+    int t = fsb::batch_queue_of(c);
+    if (c == 1 && team > 0 && 2 * n <= cap) {
+      int warps = 1;  // the smallest team that holds it
+      while (static_cast<uint64_t>(warps) * team < n) warps *= 2;
+      t = fsb::batch_pack_queue_of(warps);
+    }
     queue[t].push_back(k);
     fish[t] += n;
   }
@@ -130,7 +141,8 @@ int plan_batch(fsb_batch* b, int forced) {
   const double cost[fsb::kMaxBatchCluster + 1] = {0.0, 0.8, 1.0, 1.1, 1.1, 1.1, 1.0, 0.9, 1.0};
   double work[fsb::kBatchQueues], total = 0.0;
   for (int t = 0; t < fsb::kBatchQueues; ++t) {
-    const int c = t == fsb::kBatchQueues - 1 ? 1 : fsb::kMaxBatchCluster - t;
+    // packed schools count as single-block ones
+    const int c = t >= fsb::kBatchSingleQueue ? 1 : fsb::kMaxBatchCluster - t;
     work[t] = cost[c] * static_cast<double>(fish[t]);
     total += work[t];
   }
@@ -397,6 +409,13 @@ int fsb_batch_step(fsb_batch_handle b, uint32_t n_steps, fsb_step_stats* host_st
   return FSB_OK;
 }
 
+int fsb_batch_limits(uint64_t* block_fish, uint64_t* team_fish, int* max_cluster) {
+  if (block_fish) *block_fish = fsb::batch_block_capacity();
+  if (team_fish) *team_fish = fsb::batch_team_fish();
+  if (max_cluster) *max_cluster = fsb::kMaxBatchCluster;
+  return FSB_OK;
+}
+
 int fsb_batch_set_cluster(fsb_batch_handle b, int cluster) {
   if (!b) return bfail(FSB_ERR_INVALID_ARG, "batch handle is NULL");
   BCUDA(cudaStreamSynchronize(b->stream));
@@ -415,7 +434,7 @@ int fsb_batch_info(fsb_batch_handle b, int* cluster, int* n_clusters, int* fille
   if (n_clusters) *n_clusters = L.blocks[0] / L.cluster[0];
   if (filler_blocks)
     *filler_blocks = !single_only && L.cluster[L.n_launches - 1] == 1 ? L.blocks[L.n_launches - 1] : 0;
-  if (n_big) *n_big = L.queue_lo[fsb::kBatchQueues - 1];
+  if (n_big) *n_big = L.queue_lo[fsb::kBatchSingleQueue];
   if (step) *step = b->step;
   return FSB_OK;
 }
@@ -441,7 +460,7 @@ int fsb_batch_set_plan(fsb_batch_handle b, int n_launches, const int* cluster,
   }
   // every multi-block queue needs a launch of at least its cluster size (a
   // launch serves its own queue, then the smaller ones)
-  for (int t = 0; t < fsb::kBatchQueues - 1; ++t)
+  for (int t = 0; t < fsb::kBatchSingleQueue; ++t)
     if (L.queue_lo[t + 1] > L.queue_lo[t] && cluster[0] < fsb::kMaxBatchCluster - t)
       return bfail(FSB_ERR_INVALID_ARG, "schools need clusters of %d blocks; the widest launch "
                    "has %d", fsb::kMaxBatchCluster - t, cluster[0]);

@@ -182,10 +182,16 @@ int resident_blocks_per_sm(int fpt, int acc, int block, int swim_mode);
 size_t resident_smem_bytes(uint64_t slice);
 
 // Work queues of a batch: queue t (t = 0 .. 6) holds the schools run on
-// whole clusters of 8 - t blocks, queue 7 the schools one block runs; each
-// queue largest first.  One counter per queue, zeroed before every call.
+// whole clusters of 8 - t blocks, queue 7 the schools one block runs, and
+// queues 8 .. 11 the schools packed several to a block, each on a team of
+// 8, 4, 2 or 1 fish warps (up to 8, 4, 2 or 1 times batch_team_fish());
+// each queue largest first.  One counter per queue, zeroed before every
+// call.
 constexpr int kMaxBatchCluster = 8;  // widest cluster of a batch (portable limit)
-constexpr int kBatchQueues = kMaxBatchCluster;
+constexpr int kBatchSingleQueue = kMaxBatchCluster - 1;
+constexpr int kBatchPackQueue0 = kMaxBatchCluster;  // teams of 8 warps; then 4, 2, 1
+constexpr int kBatchPackLevels = 4;
+constexpr int kBatchQueues = kMaxBatchCluster + kBatchPackLevels;
 constexpr int kBatchMaxLaunches = kMaxBatchCluster;
 struct alignas(16) BatchCtl {
   unsigned next[kBatchQueues];
@@ -195,6 +201,10 @@ struct alignas(16) BatchCtl {
 
 // Queue of the schools that need clusters of c blocks (c = 1 .. 8).
 inline int batch_queue_of(int c) { return c >= 8 ? 0 : (c <= 1 ? 7 : 8 - c); }
+// Queue of the schools packed on teams of `warps` (8, 4, 2, 1) fish warps.
+inline int batch_pack_queue_of(int warps) {
+  return kBatchPackQueue0 + (warps >= 8 ? 0 : warps >= 4 ? 1 : warps >= 2 ? 2 : 3);
+}
 
 // Launch description of the batched (many schools) kernel, binary32 state.
 struct BatchLaunch {
@@ -204,7 +214,7 @@ struct BatchLaunch {
   void* pv;
   const unsigned long long* offsets;  // device, n_schools + 1
   const unsigned long long* seeds;    // device, n_schools
-  const uint32_t* order;              // device, queues 0..7 back to back
+  const uint32_t* order;              // device, queues 0..11 back to back
   uint32_t queue_lo[kBatchQueues + 1];  // queue t is order[queue_lo[t] .. queue_lo[t + 1])
   uint32_t n_schools;
   double pond_half, step, w0, w_min, w_max;
@@ -219,8 +229,9 @@ struct BatchLaunch {
   // Concurrent persistent launches, largest cluster first.  Launch i runs
   // clusters of cluster[i] blocks on a grid of blocks[i]: it takes whole-
   // cluster schools from queue batch_queue_of(cluster[i]) and then from the
-  // queues of smaller clusters, and finally single-block schools one block
-  // at a time (queue 3).
+  // queues of smaller clusters, then single-block schools one block at a
+  // time (queue 7), and finally packed schools, each team of warps on its
+  // own (queues 8 .. 11).
   int n_launches;
   int cluster[kBatchMaxLaunches];
   int blocks[kBatchMaxLaunches];
@@ -235,6 +246,9 @@ cudaError_t launch_batch(const BatchLaunch& L, cudaStream_t s, const cudaStream_
 const void* batch_kernel_wide(int cluster, int acc, bool var);
 int batch_max_clusters(int cluster, int acc);
 uint64_t batch_block_capacity();
+// Fish one fish warp holds when schools are packed on teams of warps (0:
+// the batch kernel was built without packing).
+uint64_t batch_team_fish();
 // Host side: completes the barycentre sums of `count` records copied out of
 // the batch kernel's statistics (raw partials of accumulation mode acc).
 void batch_finish_stats(fsb_step_stats* st, size_t count, int acc);

@@ -55,10 +55,10 @@ __device__ __forceinline__ double raw_to_sum<kAccF64>(double r) { return r; }
 // ----------------------------------------------- barycentre terms of a pair --
 // The accumulator of the on-chip passes.  Plain binary32 and binary64 add
 // the two fish of a swim pair one by one (SumAcc).  In compensated binary32
-// a thread holds at most eight pairs per step (a block's slice is at most
-// 16 fish per thread), so it keeps one plain binary32 sum per fish of its
+// a thread holds at most eleven pairs per step (a block's slice is at most
+// 22 fish per thread), so it keeps one plain binary32 sum per fish of its
 // pairs (the two lanes of a float2: w, w x, w y; one rounding per addition,
-// so an error below 7 * 2^-24 of the lane's sum of magnitudes) and hands the
+// so an error below 10 * 2^-24 of the lane's sum of magnitudes) and hands the
 // warp the exact compensated pair TwoSum(lane 0, lane 1); compensation then
 // runs from the warp level up (warp_tree, merge).  This takes 7 instructions
 // per pair against 19 for a Kahan step per quantity.
@@ -311,9 +311,9 @@ __device__ __forceinline__ void pair_pass(const PairState& B, uint32_t e, bool t
   }
 }
 
-// All of this thread's pairs in one pass: elements threadIdx.x,
-// threadIdx.x + step, ... below np (nf fish), where step is the number of
-// threads that share the pass (threads 0 .. step - 1), ITER per iteration
+// All of this thread's pairs in one pass: elements first, first + step,
+// ... below np (nf fish), where step is the number of threads that share
+// the pass and first this thread's rank among them, ITER per iteration
 // so that independent draws overlap (measured on GB300 over 1 to 4: the
 // resident kernel runs fastest at 2, 3 within 1%; the batch kernel at 1).
 // The thread's maxima of the pass's swim go into mb (bits of max |delta|)
@@ -321,13 +321,14 @@ __device__ __forceinline__ void pair_pass(const PairState& B, uint32_t e, bool t
 // +0), so the float extremes order like the keys.
 template <bool EAT, bool SWIM, bool LAST_SWIM, bool LAST_EAT, bool AHEAD = false, int ITER = 2,
           typename Acc>
-__device__ __forceinline__ void block_pass(const PairState& B, uint32_t np, uint32_t nf,
-                                           const PassCtx& c, const Physics<float>& ph, Acc& acc,
-                                           uint32_t& mb, uint32_t& ek, uint32_t step) {
+__device__ __forceinline__ void block_pass_from(const PairState& B, uint32_t np, uint32_t nf,
+                                                const PassCtx& c, const Physics<float>& ph,
+                                                Acc& acc, uint32_t& mb, uint32_t& ek,
+                                                uint32_t first, uint32_t step) {
   float ihi = -__int_as_float(0x7f800000), ilo = __int_as_float(0x7f800000);
   static_assert(ITER >= 1 && ITER <= 4, "1 to 4 pairs per iteration");
   constexpr uint32_t kIter = ITER;
-  uint32_t e = threadIdx.x;
+  uint32_t e = first;
   for (; e + (kIter - 1) * step < np; e += kIter * step) {
 #pragma unroll
     for (uint32_t k = 0; k < kIter; ++k) {
@@ -342,6 +343,16 @@ __device__ __forceinline__ void block_pass(const PairState& B, uint32_t np, uint
     mb = max(mb, abs_bits(fmaxf(ihi, -ilo)));
     ek = max(ek, order_key(ihi));
   }
+}
+
+// The same pass shared by threads 0 .. step - 1 of the block.
+template <bool EAT, bool SWIM, bool LAST_SWIM, bool LAST_EAT, bool AHEAD = false, int ITER = 2,
+          typename Acc>
+__device__ __forceinline__ void block_pass(const PairState& B, uint32_t np, uint32_t nf,
+                                           const PassCtx& c, const Physics<float>& ph, Acc& acc,
+                                           uint32_t& mb, uint32_t& ek, uint32_t step) {
+  block_pass_from<EAT, SWIM, LAST_SWIM, LAST_EAT, AHEAD, ITER>(B, np, nf, c, ph, acc, mb, ek,
+                                                               threadIdx.x, step);
 }
 
 }  // namespace fsb

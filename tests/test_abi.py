@@ -53,6 +53,11 @@ def test_binding_loads_and_names_statuses(libpath):
     assert fsb.fsb_strerror(0) == "FSB_OK"
 
 
+def test_batch_limits_need_no_gpu(libpath):
+    # 11 pairs per fish thread of a 512-thread block; 16 warps share a block
+    assert fsb.fsb_batch_limits() == {"block_fish": 11264, "team_fish": 704, "max_cluster": 8}
+
+
 def test_config_defaults_and_host_validation(libpath):
     cfg = fsb.fsb_config_init(10, 3)
     assert (cfg.pond_half, cfg.step, cfg.w0, cfg.w_min, cfg.w_max) == (100.0, 0.1, 1.0, 0.0, 2.0)

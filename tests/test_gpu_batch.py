@@ -11,7 +11,14 @@ from paper_2507_20173_gb300 import workloads
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-EDGE_SIZES = [1, 2, 31, 257, 512, 4097, 8191, 8192, 8193, 12000, 20000, 40000, 65536, 3, 700]
+# fish one block holds and fish one warp of a packed team holds (library
+# constants, read once the library is loaded)
+BF = TF = 0
+
+
+def edge_sizes():
+    return [1, 2, 31, 257, 512, 4097, BF // 2, BF // 2 + 1, BF - 1, BF, BF + 1, 12000, 20000,
+            40000, 65536, 8 * BF, 3, 700]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -21,6 +28,22 @@ def _lib():
     from paper_2507_20173_gb300 import build
     build.build()
     fsb.lib()
+    global BF, TF
+    limits = fsb.fsb_batch_limits()
+    BF, TF = limits["block_fish"], limits["team_fish"]
+    assert BF > 0 and TF > 0 and limits["max_cluster"] == 8
+
+
+def team_warps(n):
+    """Warps of the packed team a school of n fish runs on (TF fish per
+    warp; 0: not packed, more than half a block)."""
+    n = int(n)
+    if n > 8 * TF:
+        return 0
+    w = 1
+    while w * TF < n:
+        w *= 2
+    return w
 
 
 def make_state(total):
@@ -62,11 +85,13 @@ def check_batch(tmpl, offsets, seeds, got, stats, steps, precision):
                                "school %d" % k)
 
 
-@pytest.mark.parametrize("cluster", [2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("cluster", [1, 2, 3, 4, 5, 6, 7, 8])
 def test_edge_size_batch_every_cluster_size(cluster):
-    sizes = np.array(EDGE_SIZES, dtype=np.uint64)
-    if cluster * 8192 < sizes.max():
-        sizes = np.minimum(sizes, cluster * 8192)
+    """Every school on clusters of `cluster` blocks (1: every school on a
+    block of its own, none packed)."""
+    sizes = np.array(edge_sizes(), dtype=np.uint64)
+    if cluster * BF < sizes.max():
+        sizes = np.minimum(sizes, cluster * BF)
     offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
     seeds = (1000 + np.arange(sizes.size)).astype(np.uint64)
     tmpl = fsb.fsb_config_init(1, 0, step=2.0, init_weight_mode=1)
@@ -153,9 +178,10 @@ def test_ragged_ensemble_sample(precision):
 
 def test_batch_argument_errors():
     tmpl = fsb.fsb_config_init(1, 0)
-    ts, state = make_state(70000)
+    big = 8 * BF + 1                             # more than a cluster of 8 holds
+    ts, state = make_state(big)
     with pytest.raises(fsb.FsbError) as e:
-        fsb.fsb_batch_create(tmpl, np.array([0, 70000], np.uint64), np.array([1], np.uint64),
+        fsb.fsb_batch_create(tmpl, np.array([0, big], np.uint64), np.array([1], np.uint64),
                              state, init=True)
     assert e.value.status == fsb.FSB_ERR_UNSUPPORTED
     with pytest.raises(fsb.FsbError) as e:
@@ -167,10 +193,10 @@ def test_batch_argument_errors():
         fsb.fsb_batch_create(t64, np.array([0, 10], np.uint64), np.array([1], np.uint64),
                              state, init=True)
     assert e.value.status == fsb.FSB_ERR_UNSUPPORTED
-    b = fsb.fsb_batch_create(tmpl, np.array([0, 10000], np.uint64), np.array([1], np.uint64),
+    b = fsb.fsb_batch_create(tmpl, np.array([0, BF + 1], np.uint64), np.array([1], np.uint64),
                              state, init=True)
     with pytest.raises(fsb.FsbError) as e:
-        fsb.fsb_batch_set_cluster(b, 1)          # 10000 fish do not fit one block
+        fsb.fsb_batch_set_cluster(b, 1)          # BF + 1 fish do not fit one block
     assert e.value.status == fsb.FSB_ERR_UNSUPPORTED
     with pytest.raises(fsb.FsbError) as e:
         fsb.fsb_batch_set_cluster(b, 9)          # beyond the widest cluster
@@ -181,7 +207,8 @@ def test_batch_argument_errors():
 
 def test_default_plan_runs_each_school_on_the_cluster_that_holds_it():
     """With no forced cluster size every school goes to the queue of the
-    smallest cluster (1, 2, 4 or 8 blocks of 8192 fish) that holds it, one
+    smallest cluster (1 to 8 blocks of BF fish) that holds it (one of at
+    most half a block to the smallest packed team of warps), one
     concurrent launch per size, largest first, single blocks on the SMs left
     over; the result is still every school's single-school trajectory."""
     sizes = np.array([65536, 40000, 33000, 32768, 20000, 16385, 16384, 9000, 8193, 8192, 5000,
@@ -192,15 +219,20 @@ def test_default_plan_runs_each_school_on_the_cluster_that_holds_it():
     ts, state = make_state(offsets[-1])
     b = fsb.fsb_batch_create(tmpl, offsets, seeds, state, init=True)
     plan = fsb.fsb_batch_plan(b)
-    need = [max(1, -(-int(n) // 8192)) for n in sizes]   # blocks of 8192 fish that hold it
-    assert plan["queue_schools"] == {c: need.count(c) for c in range(8, 0, -1)}
+    need = [max(1, -(-int(n) // BF)) for n in sizes]   # blocks of BF fish that hold it
+    packed = [team_warps(n) for n in sizes]
+    assert plan["queue_schools"] == {c: sum(1 for k, m in enumerate(need)
+                                            if m == c and not packed[k])
+                                     for c in range(8, 0, -1)}
+    assert plan["packed_schools"] == {w: packed.count(w) for w in (8, 4, 2, 1)}
     clusters = [l["cluster"] for l in plan["launches"]]
     assert clusters[0] == max(need) and clusters == sorted(clusters, reverse=True)
+    assert max(need) > 2
     assert all(need.count(c) > 0 for c in clusters if c > 1)
     for l in plan["launches"]:
         assert l["blocks"] >= l["cluster"] and l["blocks"] % l["cluster"] == 0
     info = fsb.fsb_batch_info(b)
-    assert info["cluster"] == 8 and info["n_big"] == sum(c > 1 for c in need)
+    assert info["cluster"] == max(need) and info["n_big"] == sum(c > 1 for c in need)
     steps = 5
     stats = np.zeros(sizes.size * steps, fsb.STATS_DTYPE)
     fsb.fsb_batch_step(b, steps, stats)
@@ -209,23 +241,25 @@ def test_default_plan_runs_each_school_on_the_cluster_that_holds_it():
 
 
 def test_forced_cluster_size_and_back_to_the_default_plan():
-    sizes = np.array([20000, 9000, 100, 30000], dtype=np.uint64)
+    # on 2, 1 (a whole block), 1 (a packed warp) and 3 blocks
+    sizes = np.array([2 * BF - 500, BF - 100, 100, 3 * BF - 1000], dtype=np.uint64)
     offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
     seeds = (40 + np.arange(sizes.size)).astype(np.uint64)
     tmpl = fsb.fsb_config_init(1, 0)
     ts, state = make_state(offsets[-1])
     b = fsb.fsb_batch_create(tmpl, offsets, seeds, state, init=True)
-    assert [l["cluster"] for l in fsb.fsb_batch_plan(b)["launches"]][:3] == [4, 3, 2]
+    assert [l["cluster"] for l in fsb.fsb_batch_plan(b)["launches"]] == [3, 2, 1]
     fsb.fsb_batch_set_cluster(b, 8)
     plan = fsb.fsb_batch_plan(b)
-    assert plan["launches"][0]["cluster"] == 8 and plan["queue_schools"][8] == 3
+    assert plan["launches"][0]["cluster"] == 8 and plan["queue_schools"][8] == 2
     with pytest.raises(fsb.FsbError) as e:
-        fsb.fsb_batch_set_cluster(b, 2)          # 30000 fish do not fit 2 blocks
+        fsb.fsb_batch_set_cluster(b, 2)          # 3 BF - 1000 fish do not fit 2 blocks
     assert e.value.status == fsb.FSB_ERR_UNSUPPORTED
     assert fsb.fsb_batch_plan(b)["launches"][0]["cluster"] == 8   # unchanged
     fsb.fsb_batch_set_cluster(b, 0)
-    assert fsb.fsb_batch_plan(b)["queue_schools"] == {8: 0, 7: 0, 6: 0, 5: 0, 4: 1, 3: 1,
-                                                      2: 1, 1: 1}
+    plan = fsb.fsb_batch_plan(b)
+    assert plan["queue_schools"] == {8: 0, 7: 0, 6: 0, 5: 0, 4: 0, 3: 1, 2: 1, 1: 1}
+    assert plan["packed_schools"] == {8: 0, 4: 0, 2: 0, 1: 1}     # 100 fish on one warp
     stats = np.zeros(sizes.size * 4, fsb.STATS_DTYPE)
     fsb.fsb_batch_step(b, 4, stats)
     fsb.fsb_batch_destroy(b)
@@ -264,3 +298,56 @@ def test_explicit_plans_give_the_same_trajectories():
             what = "plan %s school %d (N=%d)" % (plan, k, hi - lo)
             assert_state_equal(sub, ref, what)
             assert_stats_match(stats[k * steps:(k + 1) * steps], ref_stats, tmpl.precision, what)
+
+
+def pack_edges():
+    return [1, 2, 3, 31, 32, 33, 255, 256, TF - 1, TF, TF + 1, 2 * TF - 1, 2 * TF, 2 * TF + 1,
+            4 * TF - 1, 4 * TF, 4 * TF + 1, 8 * TF - 1, 8 * TF, 8 * TF + 1, BF]
+
+
+@pytest.mark.parametrize("plan", [None, [(1, 1)], [(1, 3)], [(2, 2), (1, 1)]])
+@pytest.mark.parametrize("steps", [1, 2, 7])
+def test_packed_teams_every_size_class(plan, steps):
+    """Schools at the edges of every team size (1, 2, 4, 8 times TF fish on
+    teams of 1, 2, 4, 8 warps), three of each, beside whole-block
+    schools.  On one block (plan (1, 1)) every team runs several schools in
+    turn and the teams split level by level while others still run; every
+    school must keep its single-school trajectory, maxima exact."""
+    edges = pack_edges()
+    sizes = np.array(edges * 3, dtype=np.uint64)
+    offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    seeds = (700 + np.arange(sizes.size)).astype(np.uint64)
+    tmpl = fsb.fsb_config_init(1, 0, step=1.25, init_weight_mode=1)
+    ts, state = make_state(offsets[-1])
+    b = fsb.fsb_batch_create(tmpl, offsets, seeds, state, init=True)
+    got_plan = fsb.fsb_batch_plan(b)
+    assert got_plan["packed_schools"] == {w: 3 * [team_warps(n) for n in edges].count(w)
+                                          for w in (8, 4, 2, 1)}
+    if plan is not None:
+        fsb.fsb_batch_set_plan(b, plan)
+    stats = np.zeros(sizes.size * steps, fsb.STATS_DTYPE)
+    fsb.fsb_batch_step(b, steps, stats)
+    fsb.fsb_batch_destroy(b)
+    check_batch(tmpl, offsets, seeds, read_state(ts), stats, steps, tmpl.precision)
+
+
+@pytest.mark.parametrize("precision", [fsb.FSB_FP32, fsb.FSB_FP32_KAHAN, fsb.FSB_FP64_ACC])
+def test_many_small_schools_more_than_the_warps(precision):
+    """3000 schools of 1 to 600 fish (more than the GPU's fish warps), two
+    calls: the teams of one warp run several schools each, and the second
+    call loads the state the first one stored."""
+    rng = np.random.default_rng(11)
+    sizes = rng.integers(1, 601, 3000).astype(np.uint64)
+    offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    seeds = (20_000 + np.arange(sizes.size)).astype(np.uint64)
+    tmpl = fsb.fsb_config_init(1, 0, precision=precision)
+    ts, state = make_state(offsets[-1])
+    b = fsb.fsb_batch_create(tmpl, offsets, seeds, state, init=True)
+    s1 = np.zeros(sizes.size * 3, fsb.STATS_DTYPE)
+    s2 = np.zeros(sizes.size * 2, fsb.STATS_DTYPE)
+    fsb.fsb_batch_step(b, 3, s1)
+    fsb.fsb_batch_step(b, 2, s2)
+    fsb.fsb_batch_destroy(b)
+    stats = np.concatenate([np.concatenate([s1[k * 3:(k + 1) * 3], s2[k * 2:(k + 1) * 2]])
+                            for k in range(sizes.size)])
+    check_batch(tmpl, offsets, seeds, read_state(ts), stats, 5, precision)
