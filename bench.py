@@ -65,11 +65,12 @@ def parse_args():
                     help="override the school size (profiling on a smaller case)")
     ap.add_argument("--stream-kernel", type=int, default=0,
                     help="0 library choice, 1 vector loads, 2 bulk-copy ring, "
-                         "3 warp-specialised bulk-copy ring, 4 steps blocked by recompute")
+                         "3 warp-specialised bulk-copy ring, 4 steps blocked by recompute, "
+                         "5 the same keeping the positions of the blocked steps")
     ap.add_argument("--stream-block", type=int, default=0)
     ap.add_argument("--stream-stages", type=int, default=0)
     ap.add_argument("--stream-block-steps", type=int, default=0,
-                    help="stream kernel 4: steps per pair of passes (2, 4, 8)")
+                    help="stream kernels 4, 5: steps per pair of passes (2, 4, 8)")
     ap.add_argument("--reference-fish", type=int, default=1 << 22,
                     help="fish per bench step of the CPU reference arm")
     ap.add_argument("--no-e2e", action="store_true")
@@ -155,17 +156,35 @@ ALU_KERNEL_SOURCES = {
     "collective": ("fsb_collective.cu", "fsb_device.cuh", "fsb_reduce.cuh"),
     "blocked": ("fsb_stream_blocked.cu", "fsb_stream_common.cuh", "fsb_device.cuh",
                 "fsb_reduce.cuh"),
+    "blocked5": ("fsb_stream_blocked.cu", "fsb_stream_common.cuh", "fsb_device.cuh",
+                 "fsb_reduce.cuh"),
 }
+
+
+def launches_per_call(steps, coll, resident, tuning):
+    """Kernel launches of one fsb_step(steps) call: the resident kernel once;
+    the collective movements two passes per step and a first swim; streaming
+    kernels 4 and 5 a first swim, a pair of passes per k steps after it and
+    a last eat; the other streaming kernels one pass per step and a last
+    eat."""
+    if resident:
+        return 1
+    if coll:
+        return 2 * steps + 1
+    if tuning.get("stream_kernel") in (4, 5):
+        k = tuning["stream_block_steps"]
+        return 2 + 2 * ((steps - 1 + k - 1) // k)
+    return steps + 1
 
 
 def alu_source_hash(kernel):
     return _sources_hash(ALU_KERNEL_SOURCES[kernel])
 
 
-def alu_instr_per_fish_step(kernel, precision):
-    """Lane instructions per fish-step of the resident or batch kernel from
-    the committed ncu summary (profiles/<kernel>_instr.json); None if the
-    kernel changed since or the precision differs."""
+def alu_record(kernel, precision, steps_per_pair=None):
+    """The committed ncu summary of an issue-bound kernel
+    (profiles/<kernel>_instr.json); None if the kernel changed since, or the
+    precision or the steps per pair of passes differ."""
     p = os.path.join(ROOT, "profiles", "%s_instr.json" % kernel)
     if not os.path.exists(p):
         return None
@@ -173,7 +192,15 @@ def alu_instr_per_fish_step(kernel, precision):
         d = json.load(f)
     if d.get("kernel_source_hash") != alu_source_hash(kernel) or d.get("precision") != precision:
         return None
-    return float(d["lane_instr_per_fish_step"])
+    if steps_per_pair is not None and d.get("steps_per_pair") != steps_per_pair:
+        return None
+    return d
+
+
+def alu_instr_per_fish_step(kernel, precision, steps_per_pair=None):
+    """Lane instructions per fish-step from the kernel's ncu summary."""
+    d = alu_record(kernel, precision, steps_per_pair)
+    return float(d["lane_instr_per_fish_step"]) if d else None
 
 
 def issue_peak(sms, clocks):
@@ -723,17 +750,22 @@ def time_single(fsb, torch, cfg, steps, warmup, local, pg, tuning):
             "clocks": clk.summary()}
 
 
-def alu_roofline(kernel, name, precision, fish_steps_per_launch, avg_s, sms, clocks):
-    """Instruction-issue roofline of an on-chip kernel: fish-steps per launch
-    / the launch's event time x the lane-instructions per fish-step ncu
+def alu_roofline(kernel, name, precision, fish_steps_per_launch, avg_s, sms, clocks,
+                 steps_per_pair=None):
+    """Instruction-issue roofline of an issue-bound kernel: fish-steps per
+    launch / the launch's event time x the lane-instructions per fish-step ncu
     counted (profiles/<kernel>_instr.json), against the issue peak at the
-    median SM clock sampled during the timed region."""
-    ipfs = alu_instr_per_fish_step(kernel, precision)
+    median SM clock sampled during the timed region.  traffic: the DRAM bytes
+    per fish-step of that summary (when it has them) x fish-steps per launch."""
+    rec = alu_record(kernel, precision, steps_per_pair)
+    ipfs = float(rec["lane_instr_per_fish_step"]) if rec else None
+    bpfs = rec.get("dram_bytes_per_fish_step") if rec else None
     rate = fish_steps_per_launch / avg_s if avg_s else None
     roof = {"bound": "alu", "unit": "Glane-instr/s", "kernel": name,
             "avg_launch_ms": avg_s * 1e3 if avg_s else None,
             "fish_steps_per_launch": fish_steps_per_launch, "lane_instr_per_fish_step": ipfs,
-            "traffic": None, "achieved": rate * ipfs / 1e9 if (rate and ipfs) else None,
+            "traffic": bpfs * fish_steps_per_launch if bpfs else None,
+            "achieved": rate * ipfs / 1e9 if (rate and ipfs) else None,
             "peak": issue_peak(sms, clocks),
             "peak_source": "issue peak %d SMs x 128 lanes x measured median SM clock" % sms}
     roof["frac"] = roof["achieved"] / roof["peak"] if roof["achieved"] else None
@@ -836,17 +868,23 @@ def run_ours(args, world, rank, local, pg):
         roof.update({"launches": fused_n, "hbm_achieved_gbs": hbm,
                      "hbm_frac_of_measured": hbm / peak if hbm else None,
                      "algorithmic_bytes_per_launch": bytes_per_fish_step * n})
-    elif tuning["stream_kernel"] == 4:
+    elif tuning["stream_kernel"] in (4, 5):
         # steps blocked by recompute: each timed unit is a pair of passes
         # (maxima, step) covering up to K steps; the pairs cover steps - 1
         # steps of the call.  Bound by instruction issue; the HBM fraction of
-        # its algorithmic bytes (x, y read by the maxima pass; x, y, w, prev
-        # read and written by the step pass: 40 B per fish per pair) beside
+        # its algorithmic bytes beside (x, y read by the maxima pass; x, y, w,
+        # prev read and written by the step pass: 40 B per fish per pair;
+        # kernel 5 also writes and reads the positions of the K steps, 16 K B)
         pair_steps = steps - 1
         per_step_s = (fused_ms / 1e3) / pair_steps if pair_steps and fused_n else None
-        roof = alu_roofline("blocked", "blocked_maxima_kernel + blocked_step_kernel (pairs)",
-                            args.precision, n, per_step_s, sms, clocks)
-        hbm = 40 * n * fused_n / (fused_ms / 1e3) / 1e9 if fused_n else None
+        five = tuning["stream_kernel"] == 5
+        roof = alu_roofline("blocked5" if five else "blocked",
+                            "blocked_maxima_kernel + blocked_step_kernel (pairs%s)"
+                            % (", positions kept" if five else ""),
+                            args.precision, n, per_step_s, sms, clocks,
+                            steps_per_pair=tuning["stream_block_steps"])
+        pair_bytes = 40 * n * fused_n + (16 * n * pair_steps if five else 0)
+        hbm = pair_bytes / (fused_ms / 1e3) / 1e9 if fused_n else None
         roof.update({"launches": fused_n, "steps_per_pair": tuning["stream_block_steps"],
                      "hbm_achieved_gbs": hbm, "hbm_frac_of_measured": hbm / peak if hbm else None,
                      "what": "avg_launch_ms and achieved are per fish-step of the pairs"})
@@ -972,8 +1010,8 @@ def run_ours(args, world, rank, local, pg):
                                  else "state fits in L2 (reused across steps)",
                            "parallelism": "replicas x%d" % world, "tuning": tuning},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": (2 * steps + 1 if coll else steps + 1)
-                if path != fsb.FSB_PATH_RESIDENT else 1,
+                "gpu_launches": launches_per_call(steps, coll, path == fsb.FSB_PATH_RESIDENT,
+                                                  tuning),
                 "clocks": clocks}
         if subs is not None:
             line["sub_records"] = subs

@@ -375,7 +375,17 @@ int fsb_set_fault_injection(fsb_handle h, int block, uint32_t step, uint64_t tim
  *                        max |delta| and eat() values, and a step pass then
  *                        eats and swims them all with one read and write of
  *                        the state (binary32, aligned state, swim_mode 0; the
- *                        call's first swim and last eat take kernel 1)
+ *                        call's first swim and last eat take kernel 1);
+ *                        5: the same pair of passes, the maxima pass also
+ *                        storing the positions of the k steps (8 k B per fish
+ *                        in slots the handle allocates), which the step pass
+ *                        loads instead of drawing and swimming again.
+ *                        The library's choice (0) is kernel 5 with 8 steps
+ *                        per pair for a streaming school of at least 2^22
+ *                        fish that allows it, when its 64 B per fish of
+ *                        slots take at most half of the free device memory;
+ *                        kernel 1 otherwise.  A slot allocation that fails
+ *                        returns FSB_ERR_OOM
  *   stream_block         threads per block of the streaming pass: 256 or 512
  *                        (kernel 3: consumer threads; the block has 32 more)
  *   stream_blocks_per_sm blocks per SM of the streaming grid (capped by
@@ -391,8 +401,8 @@ int fsb_set_fault_injection(fsb_handle h, int block, uint32_t step, uint64_t tim
  *                        with a fish pair for every thread
  *   stream_stages        bulk-copy kernels: shared-memory tiles in flight per
  *                        block, 2, 3 or 4 (kernel 3: 2 or 3)
- *   stream_block_steps   kernel 4: steps per pair of passes, 2, 4 or 8
- *                        (0: 4)
+ *   stream_block_steps   kernels 4 and 5: steps per pair of passes, 2, 4 or
+ *                        8 (0: 4 for kernel 4, 8 for kernel 5)
  * A combination that cannot run returns FSB_ERR_INVALID_ARG and leaves the
  * handle unchanged.  Synchronises the handle's stream. */
 typedef struct {
@@ -458,8 +468,10 @@ int fsb_handle_path(fsb_handle h, int* path_out);
  * hosts that own all device memory through their own arena and forbid later
  * cudaMalloc, and latency-bound pipelines in which cudaMalloc / cudaFree
  * (which can synchronise the whole device) would stall their other streams.
- * It runs the same streaming kernels, in the same launch shape, as fsb_step;
- * their scratch (control word, per-block reduction partials, per-step
+ * It runs stream kernel 1 (vector loads) in fsb_step's launch shape for that
+ * kernel -- not kernel 5, which fsb_step chooses for large schools and whose
+ * position slots (64 B per fish) would need an allocation; the kernels'
+ * scratch (control word, per-block reduction partials, per-step
  * statistics ring) lives in one fixed file-scope __device__ array of about
  * 210 KB that every GPU loading the library holds until the process exits.
  *   cfg         as for fsb_create (path is ignored: always streaming;

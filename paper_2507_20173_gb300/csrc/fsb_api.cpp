@@ -161,7 +161,9 @@ struct fsb_school {
   uint64_t fused_launches = 0;
   void* cur_stage = nullptr;       // two chunks of currentObjective for fsb_read_state
   uint64_t cur_chunk = 0;          // fish per chunk
-  BlockPartial* bpartials = nullptr;  // stream kernel 4: per-step partials of a pair
+  BlockPartial* bpartials = nullptr;  // stream kernels 4, 5: per-step partials of a pair
+  float* slots = nullptr;          // stream kernel 5: positions of a pair's steps
+  size_t slot_bytes = 0;
   bool collective = false;         // collective_mode 1: two passes per step
   fsb::CollLaunch coll{};
   uint32_t coll_cap = 0;           // steps the collective record ring holds
@@ -464,26 +466,64 @@ constexpr uint64_t kCurChunk = 1ull << 22;
 
 // Streaming launch shape: kernel variant, block, grid.  Invalidates graphs.
 constexpr int kMaxBlockSteps = 8;
+// The library's streaming kernel for a school of at least this many fish
+// (binary32, aligned state, default swim): kernel 5 with 8 steps per pair.
+// Measured on GB300 against kernel 1: 2^20 fish (in L2) 2.50e11 against
+// 2.51e11 fish-steps/s, 2^22 1.45e11 against 1.24e11, 2^24 2.13e11 against
+// 1.76e11, 2^26 2.39e11 against 1.98e11, 2^28 2.46e11 against 2.01e11.
+constexpr uint64_t kBlockedMinFish = 1ull << 22;
 
 int configure_stream(fsb_school* h, int kernel, int block, int blocks_per_sm, int stages,
                      int block_steps) {
   StreamLaunch L = h->launch;
   const bool tma_ok = !L.real_is_double && L.vec == 4;
-  // stream kernel 4 runs the call's first swim and last eat on kernel 1 in
-  // its default shape, and the pairs of blocked passes in between
-  if (kernel == 4) {
+  // the library's choice: kernel 5 (k = 8) for a large streaming school
+  // whose position slots (64 B per fish) take at most half of the free
+  // device memory, else kernel 1
+  if (kernel == 0 && block == 0 && blocks_per_sm == 0 && stages == 0 && block_steps == 0 &&
+      h->path == FSB_PATH_STREAM && !h->collective && h->cfg.n_fish >= kBlockedMinFish &&
+      fsb::stream_blocked_supported(L)) {
+    size_t free_b = 0, total_b = 0;
+    const size_t slots = 64 * static_cast<size_t>(h->cfg.n_fish);
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && slots <= free_b / 2 &&
+        configure_stream(h, 5, 0, 0, 0, 8) == FSB_OK)
+      return FSB_OK;
+    cudaGetLastError();
+  }
+  // stream kernels 4 and 5 run the call's first swim and last eat on kernel
+  // 1 in its default shape, and the pairs of blocked passes in between;
+  // kernel 5 keeps 2 k position arrays of the school's size (8 k B per fish)
+  if (kernel == 4 || kernel == 5) {
     if (!fsb::stream_blocked_supported(L) || h->collective)
-      return fail(FSB_ERR_INVALID_ARG,
-                  "stream kernel 4 needs binary32, 16-byte aligned state and the default swim");
+      return fail(FSB_ERR_INVALID_ARG, "stream kernels 4 and 5 need binary32, 16-byte aligned "
+                  "state and the default swim");
     if (block != 0 && block != 256)
-      return fail(FSB_ERR_INVALID_ARG, "stream kernel 4 runs 256-thread blocks");
-    const int k = block_steps ? block_steps : 4;
+      return fail(FSB_ERR_INVALID_ARG, "stream kernels 4 and 5 run 256-thread blocks");
+    const int k = block_steps ? block_steps : (kernel == 5 ? 8 : 4);
     if (k != 2 && k != 4 && k != 8)
       return fail(FSB_ERR_INVALID_ARG, "stream_block_steps must be 2, 4 or 8");
+    const uint64_t ss = (h->cfg.n_fish + 3) / 4 * 4;
+    const size_t need_slots = kernel == 5 ? sizeof(float) * 2 * static_cast<size_t>(k) * ss : 0;
+    if (need_slots > h->slot_bytes) {
+      // before the handle changes, so that a failure leaves it as it was
+      float* p = nullptr;
+      const cudaError_t e = cudaMalloc(&p, need_slots);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? FSB_ERR_OOM : FSB_ERR_CUDA,
+                    "stream kernel 5: %zu bytes of position slots: %s", need_slots,
+                    cudaGetErrorString(e));
+      }
+      cudaFree(h->slots);
+      h->slots = p;
+      h->slot_bytes = need_slots;
+    }
     int rc = configure_stream(h, 1, 256, 4, 0, 0);
     if (rc != FSB_OK) return rc;
     L = h->launch;
     L.blocked_k = k;
+    L.slots = kernel == 5 ? h->slots : nullptr;
+    L.slot_stride = kernel == 5 ? ss : 0;
     const int per_sm = fsb::stream_blocked_blocks_per_sm(L);
     if (per_sm < 1) return fail(FSB_ERR_INVALID_ARG, "stream kernel 4 cannot be resident");
     const uint64_t need = (h->cfg.n_fish / 4 + 255) / 256;
@@ -496,11 +536,13 @@ int configure_stream(fsb_school* h, int kernel, int block, int blocks_per_sm, in
     }
     L.bpartials = h->bpartials;
     h->launch = L;
-    h->tuning.stream_kernel = 4;
+    h->tuning.stream_kernel = kernel;
     h->tuning.stream_block_steps = k;
     return FSB_OK;
   }
   L.blocked_k = 0;
+  L.slots = nullptr;
+  L.slot_stride = 0;
   h->tuning.stream_block_steps = 0;
   // default measured on GB300 at N = 2^28: vector loads, 256 threads, 4
   // blocks per SM (0.96 of the copy peak, against 0.91 for the bulk-copy
@@ -510,7 +552,7 @@ int configure_stream(fsb_school* h, int kernel, int block, int blocks_per_sm, in
   if (stages < 2 || stages > 4) return fail(FSB_ERR_INVALID_ARG, "stream stages must be 2..4");
   if ((kernel == 2 || kernel == 3) && !tma_ok)
     return fail(FSB_ERR_INVALID_ARG, "bulk-copy kernels need binary32, 16-byte aligned state");
-  if (kernel < 1 || kernel > 4) return fail(FSB_ERR_INVALID_ARG, "unknown stream kernel");
+  if (kernel < 1 || kernel > 5) return fail(FSB_ERR_INVALID_ARG, "unknown stream kernel");
   if (kernel == 3 && stages > 3)
     return fail(FSB_ERR_INVALID_ARG, "warp-specialised ring: stages must be 2 or 3");
   if (block == 0) block = kernel == 1 ? 256 : 512;
@@ -609,6 +651,7 @@ void release(fsb_school* h) {
   cudaFree(h->sums);
   cudaFree(h->partials);
   cudaFree(h->bpartials);
+  cudaFree(h->slots);
   cudaFree(h->ring);
   cudaFree(h->cur_stage);
   cudaFree(h->coll.partials);
@@ -723,7 +766,8 @@ int fsb_create(const fsb_config* cfg, const fsb_state_dev* buffers, const fsb_st
     h->sms = sms;
     FSB_CUDA(cudaMalloc(&h->partials, sizeof(BlockPartial) * sms * kMaxPartialsPerSm));
     L.partials = h->partials;
-    int r0 = configure_stream(h, 0, 0, 0, 0, 0);
+    // kernel 1 until the path is known (the library's choice below)
+    int r0 = configure_stream(h, 1, 0, 0, 0, 0);
     if (r0 != FSB_OK) return r0;
 
     // collective movements: streaming only (two passes per step)
@@ -788,6 +832,10 @@ int fsb_create(const fsb_config* cfg, const fsb_state_dev* buffers, const fsb_st
       R.inject_step = 0;
       FSB_CUDA(cudaMalloc(&h->rctl, sizeof(fsb::ResCtl)));
       R.rctl = h->rctl;
+    }
+    if (h->path == FSB_PATH_STREAM && !h->collective) {
+      const int rk = configure_stream(h, 0, 0, 0, 0, 0);
+      if (rk != FSB_OK) return rk;
     }
     // per-call scratch for calls of up to 1024 steps, so that such a call
     // allocates nothing (a longer one grows it, synchronising once)

@@ -37,6 +37,7 @@ int time_candidate(const fsb_config* base, const Candidate& c, uint32_t n_steps,
   int rc = fsb_create(&cfg, nullptr, nullptr, 0, s, &h);
   if (rc != FSB_OK) return rc;
   rc = fsb_set_tuning(h, &c.t);
+  if (rc == FSB_ERR_OOM) rc = FSB_ERR_UNSUPPORTED;  // this shape's scratch does not fit: skip it
   if (rc == FSB_OK) rc = fsb_step(h, n_steps < 8 ? n_steps : 8, nullptr);  // warm-up
   cudaEvent_t a = nullptr, b = nullptr;
   if (rc == FSB_OK && (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess))
@@ -95,13 +96,14 @@ extern "C" int fsb_autotune(const fsb_config* cfg, uint32_t n_steps, int* best_p
         }
   if (!dbl && cfg->swim_mode == 0) {
     const int ks[] = {4, 8};
-    for (int k : ks) {  // steps blocked by recompute
-      Candidate c{};
-      c.path = FSB_PATH_STREAM;
-      c.t.stream_kernel = 4;
-      c.t.stream_block_steps = k;
-      cands.push_back(c);
-    }
+    for (int kernel : {4, 5})  // steps blocked by recompute; 5: positions kept
+      for (int k : ks) {
+        Candidate c{};
+        c.path = FSB_PATH_STREAM;
+        c.t.stream_kernel = kernel;
+        c.t.stream_block_steps = k;
+        cands.push_back(c);
+      }
   }
   if (!dbl) {
     const int fpts[] = {4, 8, 12, 16};

@@ -61,9 +61,11 @@ struct StreamLaunch {
   BlockPartial* partials;
   fsb_step_stats* ring;
   uint32_t ring_cap;
-  int blocked_k = 0;                   // stream kernel 4: steps per pair of passes (2, 4, 8)
-  int bgrid = 0;                       //   its grid
-  BlockPartial* bpartials = nullptr;   //   its per-step partials, blocked_k x bgrid
+  int blocked_k = 0;                   // stream kernels 4, 5: steps per pair of passes (2, 4, 8)
+  int bgrid = 0;                       //   their grid
+  BlockPartial* bpartials = nullptr;   //   their per-step partials, blocked_k x bgrid
+  float* slots = nullptr;              // stream kernel 5: positions of the pair's steps,
+  uint64_t slot_stride = 0;            //   x and y of step t at slots + (2t, 2t + 1) * stride
   unsigned long long timeout_ns = 0;  // bound of the copy rings' waits (0: 1 s)
   int inject_block = -1;               // test hook (copy-ring kernels): block that withholds
   uint32_t inject_pass = 0;            //   its first copy in this pass of a call; -1 = none
@@ -81,9 +83,10 @@ cudaError_t stream_ws_prepare(const StreamLaunch& L);
 int stream_ws_blocks_per_sm(const StreamLaunch& L);
 cudaError_t launch_stream_pass_ws(const StreamLaunch& L, int pass_kind, cudaStream_t s);
 cudaError_t launch_init(const StreamLaunch& L, int weight_mode, cudaStream_t s);
-// Stream kernel 4 (fsb_stream_blocked.cu): a pair of passes advancing k <=
-// L.blocked_k steps, the maxima pass and then the step pass (binary32,
-// 16-byte aligned state, default swim).
+// Stream kernels 4 and 5 (fsb_stream_blocked.cu): a pair of passes
+// advancing k <= L.blocked_k steps, the maxima pass and then the step pass
+// (binary32, 16-byte aligned state, default swim); kernel 5 (L.slots set)
+// keeps the maxima pass's positions for the step pass.
 bool stream_blocked_supported(const StreamLaunch& L);
 int stream_blocked_blocks_per_sm(const StreamLaunch& L);
 cudaError_t launch_blocked_pair(const StreamLaunch& L, uint32_t k, cudaStream_t s);

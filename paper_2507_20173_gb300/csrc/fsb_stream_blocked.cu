@@ -18,6 +18,11 @@
 //                barycentre terms and swims the next step; writes the state
 //                "swum j + k, not eaten" and the k steps' barycentre sums.
 //
+// Stream kernel 5 trades memory for instructions: its maxima pass also
+// stores the positions of steps j + 1 .. j + k (8 B per fish and step, in
+// slots beside the state), and its step pass loads them instead of drawing
+// and swimming again, so each fish-step's draw and swim run once.
+//
 // Per fish the arithmetic is fsb_stream.cu's, operation for operation, so
 // the state is bit-identical to the one-pass-per-step kernels'; only the
 // rounding order of the barycentre sums differs.  The pass sequence of a
@@ -28,6 +33,7 @@
 // arrays and the default swim only (the host enforces it).
 #include <cstdint>
 
+#include "fsb_bulk_copy.cuh"
 #include "fsb_stream_common.cuh"
 
 namespace fsb {
@@ -35,6 +41,28 @@ namespace {
 
 constexpr int kBlkThreads = 256;
 constexpr int kBlkWarps = kBlkThreads / 32;
+// Kernel 5's step pass: each thread's positions of the next kLead steps are
+// in flight through its own ring of kLead + 1 shared-memory entries, filled
+// by asynchronous 16-byte copies (no registers held for them).  Measured at
+// N = 2^28, k = 8: a lead of 2 steps 2.46e11 fish-steps/s, 3: 2.45e11, 4:
+// 2.43e11, 6: 2.41e11; one step held in registers instead: 2.07e11.  The
+// paired (f32x2) arithmetic of the on-chip passes measured slower in both
+// passes here (2.43e11; kernel 4 at k = 8: 1.97e11 against 2.04e11).
+constexpr int kLead = 2;
+constexpr int kRing = kLead + 1;
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+// Waits until at most N of this thread's copy groups are still pending.
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 // Pass index j of the pair and its step count k; false (status latched) if
 // they do not fit the call: the maxima pass writes records j .. j + k - 1,
@@ -80,9 +108,18 @@ __device__ __forceinline__ void swim_extremes(float& x, float& y, float& cur, ui
 }
 
 // ------------------------------------------------------- maxima pass --
-template <int K>
+// Slot t (the positions after the swim of step j + 1 + t): x, then y.
+__device__ __forceinline__ float* slot_x(float* slots, uint64_t ss, int t) {
+  return slots + static_cast<uint64_t>(2 * t) * ss;
+}
+__device__ __forceinline__ float* slot_y(float* slots, uint64_t ss, int t) {
+  return slots + static_cast<uint64_t>(2 * t + 1) * ss;
+}
+
+template <int K, bool STORE>
 __global__ void __launch_bounds__(kBlkThreads, 2)
-    blocked_maxima_kernel(StreamArgs<float> a, uint32_t k, BlockPartial* bp) {
+    blocked_maxima_kernel(StreamArgs<float> a, uint32_t k, BlockPartial* bp, float* slots,
+                          uint64_t ss) {
   uint32_t j;
   uint64_t base;
   if (!blocked_prologue<K>(a.ctl, a.ring_cap, k, j, base)) return;
@@ -122,6 +159,10 @@ __global__ void __launch_bounds__(kBlkThreads, 2)
         swim_extremes(x[1], y[1], cur[1], r0.v[2], r0.v[3], ph, hi[t], lo[t]);
         swim_extremes(x[2], y[2], cur[2], r1.v[0], r1.v[1], ph, hi[t], lo[t]);
         swim_extremes(x[3], y[3], cur[3], r1.v[2], r1.v[3], ph, hi[t], lo[t]);
+        if (STORE) {
+          reinterpret_cast<float4*>(slot_x(slots, ss, t))[g] = make_float4(x[0], x[1], x[2], x[3]);
+          reinterpret_cast<float4*>(slot_y(slots, ss, t))[g] = make_float4(y[0], y[1], y[2], y[3]);
+        }
       }
     }
   }
@@ -135,6 +176,10 @@ __global__ void __launch_bounds__(kBlkThreads, 2)
         if (static_cast<uint32_t>(t) < k) {
           const Words2 r = fish_swim_words(a.key, a.school, i, t1 + t);
           swim_extremes(x, y, cur, r.r0, r.r1, ph, hi[t], lo[t]);
+          if (STORE) {
+            slot_x(slots, ss, t)[i] = x;
+            slot_y(slots, ss, t)[i] = y;
+          }
         }
       }
     }
@@ -216,13 +261,14 @@ __global__ void __launch_bounds__(kBlkThreads, 2)
 
 // --------------------------------------------------------- step pass --
 // One fish through the k steps of a pair: eat of step j + t (normaliser
-// N[t]), its barycentre terms, then the swim of step j + t + 1.  `cur` is the
-// objective of the position in hand, `pv` the one before its swim.
-template <int K, typename Acc>
+// N[t]), its barycentre terms, then the swim of step j + t + 1 (STORE: its
+// positions from slot t).  `cur` is the objective of the position in hand,
+// `pv` the one before its swim; the last swim's objective is not needed.
+template <int K, bool STORE, typename Acc>
 __device__ __forceinline__ void fish_steps(float& x, float& y, float& w, float& pv, uint64_t i,
                                            const float (&N)[K], uint32_t k, uint32_t t1, Key key,
                                            uint32_t school, const Physics<float>& ph,
-                                           Acc (&acc)[K]) {
+                                           Acc (&acc)[K], float* slots, uint64_t ss) {
   float cur = objective(x, y);
 #pragma unroll
   for (int t = 0; t < K; ++t) {
@@ -230,17 +276,23 @@ __device__ __forceinline__ void fish_steps(float& x, float& y, float& w, float& 
       if (N[t] > 0.f)
         w = eat(w, ph.feed_mode ? __fsub_rn(pv, cur) : __fsub_rn(cur, pv), N[t], ph);
       acc[t].add(w, x, y);
-      const Words2 r = fish_swim_words(key, school, i, t1 + t);
-      swim(x, y, r.r0, r.r1, ph.step, ph);
+      if (STORE) {
+        x = slot_x(slots, ss, t)[i];
+        y = slot_y(slots, ss, t)[i];
+      } else {
+        const Words2 r = fish_swim_words(key, school, i, t1 + t);
+        swim(x, y, r.r0, r.r1, ph.step, ph);
+      }
       pv = cur;
-      cur = objective(x, y);
+      if (static_cast<uint32_t>(t) + 1 < k) cur = objective(x, y);
     }
   }
 }
 
-template <int K, int ACC, bool VAR>
+template <int K, int ACC, bool VAR, bool STORE>
 __global__ void __launch_bounds__(kBlkThreads, 2)
-    blocked_step_kernel(StreamArgs<float> a, uint32_t k, BlockPartial* bp) {
+    blocked_step_kernel(StreamArgs<float> a, uint32_t k, BlockPartial* bp, float* slots,
+                        uint64_t ss) {
   using Acc = SumAcc<ACC>;
   using Sum = typename Acc::Sum;
   uint32_t j;
@@ -260,6 +312,29 @@ __global__ void __launch_bounds__(kBlkThreads, 2)
   const uint64_t ngroups = a.n / 4;
   const uint64_t stride = static_cast<uint64_t>(gridDim.x) * kBlkThreads;
   const uint64_t tid = static_cast<uint64_t>(blockIdx.x) * kBlkThreads + threadIdx.x;
+  // kernel 5: the copy cursor runs kLead steps (of this thread's groups in
+  // order, k steps each) ahead of the consumer; a step past the thread's
+  // last group commits an empty copy group, so that every step commits one
+  __shared__ __align__(16) float4 ring[STORE ? kRing : 1][2][kBlkThreads];
+  uint64_t pg = tid;
+  uint32_t pt = 0, pw = 0, rc = 0;
+  auto issue = [&]() {
+    if (pg < ngroups) {
+      cp_async16(&ring[pw][0][threadIdx.x], slot_x(slots, ss, static_cast<int>(pt)) + 4 * pg);
+      cp_async16(&ring[pw][1][threadIdx.x], slot_y(slots, ss, static_cast<int>(pt)) + 4 * pg);
+      if (++pt == k) {
+        pt = 0;
+        pg += stride;
+      }
+    }
+    cp_async_commit();
+    pw = pw + 1 == kRing ? 0u : pw + 1;
+  };
+  if (STORE) {
+#pragma unroll
+    for (int d = 0; d < kLead; ++d) issue();
+  }
+  // the next group's state is loaded while this one computes
   float4 xn = make_float4(0.f, 0.f, 0.f, 0.f), yn = xn, wn = xn, pn = xn;
   if (tid < ngroups) {
     xn = X[tid];
@@ -289,14 +364,28 @@ __global__ void __launch_bounds__(kBlkThreads, 2)
                        N[t], ph);
         }
         acc[t].add4(w, x, y);
-        const Words4 r0 = pair_draw(a.key, a.school, 2 * g, t1 + t);
-        const Words4 r1 = pair_draw(a.key, a.school, 2 * g + 1, t1 + t);
+        if (STORE) {
+          cp_async_wait<kLead - 1>();  // this step's copies have landed
+          const float4 sx = ring[rc][0][threadIdx.x], sy = ring[rc][1][threadIdx.x];
+          rc = rc + 1 == kRing ? 0u : rc + 1;
+          x[0] = sx.x; x[1] = sx.y; x[2] = sx.z; x[3] = sx.w;
+          y[0] = sy.x; y[1] = sy.y; y[2] = sy.z; y[3] = sy.w;
+          issue();  // into the entry read one step before this one
+        } else {
+          const Words4 r0 = pair_draw(a.key, a.school, 2 * g, t1 + t);
+          const Words4 r1 = pair_draw(a.key, a.school, 2 * g + 1, t1 + t);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const Words4& r = q < 2 ? r0 : r1;
+            swim(x[q], y[q], r.v[2 * (q & 1)], r.v[2 * (q & 1) + 1], ph.step, ph);
+          }
+        }
+        // the objective of the last swim's position is not needed
+        const bool more = static_cast<uint32_t>(t) + 1 < k;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const Words4& r = q < 2 ? r0 : r1;
-          swim(x[q], y[q], r.v[2 * (q & 1)], r.v[2 * (q & 1) + 1], ph.step, ph);
           pv[q] = cur[q];
-          cur[q] = objective(x[q], y[q]);
+          if (more) cur[q] = objective(x[q], y[q]);
         }
       }
     }
@@ -305,11 +394,12 @@ __global__ void __launch_bounds__(kBlkThreads, 2)
     W[g] = make_float4(w[0], w[1], w[2], w[3]);
     PV[g] = make_float4(pv[0], pv[1], pv[2], pv[3]);
   }
+  if (STORE) cp_async_wait<0>();  // (every copy issued was consumed)
   {  // ragged tail: the last n % 4 fish, one per thread
     const uint64_t i = ngroups * 4 + tid;
     if (i < a.n) {
       float x = a.x[i], y = a.y[i], w = a.w[i], pv = a.pv[i];
-      fish_steps<K>(x, y, w, pv, i, N, k, t1, a.key, a.school, ph, acc);
+      fish_steps<K, STORE>(x, y, w, pv, i, N, k, t1, a.key, a.school, ph, acc, slots, ss);
       a.x[i] = x;
       a.y[i] = y;
       a.w[i] = w;
@@ -392,38 +482,40 @@ __global__ void __launch_bounds__(kBlkThreads, 2)
   }
 }
 
-template <int K>
+template <int K, int ACC, bool STORE>
+const void* step_ptr(bool var) {
+  return var ? reinterpret_cast<const void*>(&blocked_step_kernel<K, ACC, true, STORE>)
+             : reinterpret_cast<const void*>(&blocked_step_kernel<K, ACC, false, STORE>);
+}
+
+template <int K, bool STORE>
 const void* pick_step(int acc, bool var) {
   switch (acc) {
-    case kAccPlain32:
-      return var ? reinterpret_cast<const void*>(&blocked_step_kernel<K, kAccPlain32, true>)
-                 : reinterpret_cast<const void*>(&blocked_step_kernel<K, kAccPlain32, false>);
-    case kAccKahan32:
-      return var ? reinterpret_cast<const void*>(&blocked_step_kernel<K, kAccKahan32, true>)
-                 : reinterpret_cast<const void*>(&blocked_step_kernel<K, kAccKahan32, false>);
-    case kAccF64:
-      return var ? reinterpret_cast<const void*>(&blocked_step_kernel<K, kAccF64, true>)
-                 : reinterpret_cast<const void*>(&blocked_step_kernel<K, kAccF64, false>);
+    case kAccPlain32: return step_ptr<K, kAccPlain32, STORE>(var);
+    case kAccKahan32: return step_ptr<K, kAccKahan32, STORE>(var);
+    case kAccF64: return step_ptr<K, kAccF64, STORE>(var);
     default: return nullptr;
   }
 }
 
-// The kernels of a pair of k_max steps: the maxima pass and the step pass.
+template <int K, bool STORE>
+void pick_k(int acc, bool var, const void** maxima, const void** step) {
+  *maxima = reinterpret_cast<const void*>(&blocked_maxima_kernel<K, STORE>);
+  *step = pick_step<K, STORE>(acc, var);
+}
+
+// The kernels of a pair of k_max steps: the maxima pass and the step pass
+// (kernel 5 when the slots are set).
 bool pick_pair(const StreamLaunch& L, const void** maxima, const void** step) {
   const bool var = L.feed_mode != 0;
+  const bool store = L.slots != nullptr;
   switch (L.blocked_k) {
-    case 2:
-      *maxima = reinterpret_cast<const void*>(&blocked_maxima_kernel<2>);
-      *step = pick_step<2>(L.acc, var);
-      break;
-    case 4:
-      *maxima = reinterpret_cast<const void*>(&blocked_maxima_kernel<4>);
-      *step = pick_step<4>(L.acc, var);
-      break;
-    case 8:
-      *maxima = reinterpret_cast<const void*>(&blocked_maxima_kernel<8>);
-      *step = pick_step<8>(L.acc, var);
-      break;
+    case 2: store ? pick_k<2, true>(L.acc, var, maxima, step)
+                  : pick_k<2, false>(L.acc, var, maxima, step); break;
+    case 4: store ? pick_k<4, true>(L.acc, var, maxima, step)
+                  : pick_k<4, false>(L.acc, var, maxima, step); break;
+    case 8: store ? pick_k<8, true>(L.acc, var, maxima, step)
+                  : pick_k<8, false>(L.acc, var, maxima, step); break;
     default: return false;
   }
   return *step != nullptr;
@@ -452,9 +544,12 @@ cudaError_t launch_blocked_pair(const StreamLaunch& L, uint32_t k, cudaStream_t 
   if (!pick_pair(L, &fa, &fb) || L.bgrid <= 0 || !L.bpartials || k == 0 ||
       k > static_cast<uint32_t>(L.blocked_k))
     return cudaErrorInvalidValue;
+  if (L.slots && L.slot_stride % 4 != 0) return cudaErrorInvalidValue;
   StreamArgs<float> a = make_stream_args<float>(L);
   BlockPartial* bp = L.bpartials;
-  void* args[] = {&a, &k, &bp};
+  float* slots = L.slots;
+  uint64_t ss = L.slot_stride;
+  void* args[] = {&a, &k, &bp, &slots, &ss};
   cudaError_t e = cudaLaunchKernel(fa, dim3(L.bgrid), dim3(kBlkThreads), args, 0, s);
   if (e != cudaSuccess) return e;
   return cudaLaunchKernel(fb, dim3(L.bgrid), dim3(kBlkThreads), args, 0, s);
