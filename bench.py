@@ -69,6 +69,8 @@ def parse_args():
                          "5 the same keeping the positions of the blocked steps")
     ap.add_argument("--stream-block", type=int, default=0)
     ap.add_argument("--stream-stages", type=int, default=0)
+    ap.add_argument("--stream-blocks-per-sm", type=int, default=0,
+                    help="blocks per SM of the streaming pass (kernels 1-3)")
     ap.add_argument("--stream-block-steps", type=int, default=0,
                     help="stream kernels 4, 5: steps per pair of passes (2, 4, 8)")
     ap.add_argument("--reference-fish", type=int, default=1 << 22,
@@ -841,7 +843,9 @@ def run_ours(args, world, rank, local, pg):
     stream = torch.cuda.current_stream()
 
     tuning = {"stream_kernel": args.stream_kernel, "stream_block": args.stream_block,
-              "stream_stages": args.stream_stages, "stream_block_steps": args.stream_block_steps}
+              "stream_stages": args.stream_stages, "stream_block_steps": args.stream_block_steps,
+              "stream_blocks_per_sm": args.stream_blocks_per_sm}
+    tuning_args = dict(tuning)  # as asked (tuning below becomes the handle's)
 
     # ---- device-resident timing
     t = time_single(fsb, torch, cfg, steps, warmup, local, pg, tuning)
@@ -949,11 +953,8 @@ def run_ours(args, world, rank, local, pg):
             barrier(torch, pg)
             t0 = time.perf_counter()
             h = fsb.fsb_create(cfg, bufs, host, 0, stream.cuda_stream)
-            if args.stream_kernel or args.stream_block or args.stream_stages:
-                fsb.fsb_set_tuning(h, stream_kernel=args.stream_kernel,
-                                   stream_block=args.stream_block,
-                                   stream_stages=args.stream_stages,
-                                   stream_block_steps=args.stream_block_steps)
+            if any(tuning_args.values()):
+                fsb.fsb_set_tuning(h, **tuning_args)
             stream.synchronize()  # the state's host->device copies are in
             t1 = time.perf_counter()
             fsb.fsb_step(h, steps, stats)
