@@ -374,8 +374,9 @@ int fsb_set_fault_injection(fsb_handle h, int block, uint32_t step, uint64_t tim
  *                        stream_block_steps steps from the state to find their
  *                        max |delta| and eat() values, and a step pass then
  *                        eats and swims them all with one read and write of
- *                        the state (binary32, aligned state, swim_mode 0; the
- *                        call's first swim and last eat take kernel 1);
+ *                        the state (binary32, aligned state, swim_mode 0, a
+ *                        swim step of 0 or at least 2^-103; the call's first
+ *                        swim and last eat take kernel 1);
  *                        5: the same pair of passes, the maxima pass also
  *                        storing the positions of the k steps (8 k B per fish
  *                        in slots the handle allocates), which the step pass

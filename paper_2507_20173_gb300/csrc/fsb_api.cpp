@@ -496,7 +496,7 @@ int configure_stream(fsb_school* h, int kernel, int block, int blocks_per_sm, in
   if (kernel == 4 || kernel == 5) {
     if (!fsb::stream_blocked_supported(L) || h->collective)
       return fail(FSB_ERR_INVALID_ARG, "stream kernels 4 and 5 need binary32, 16-byte aligned "
-                  "state and the default swim");
+                  "state, the default swim and a swim step of 0 or at least 2^-103");
     if (block != 0 && block != 256)
       return fail(FSB_ERR_INVALID_ARG, "stream kernels 4 and 5 run 256-thread blocks");
     const int k = block_steps ? block_steps : (kernel == 5 ? 8 : 4);

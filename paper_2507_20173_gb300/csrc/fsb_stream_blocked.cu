@@ -95,11 +95,28 @@ __device__ __forceinline__ bool arrive_last(Ctl* ctl) {
   return s_last;
 }
 
+// The swim's move (2u - 1) * width (Sec. 2.1.2) as v * (width * 2^-23) with
+// the integer v = (r >> 8) - 2^23: one rounding of the same real product as
+// swim()'s (v * 2^-23) * width, since width * 2^-23 is exact (the host runs
+// these kernels only for width 0 or |width| >= 2^-103), so bit-identical, with one
+// product less per coordinate (measured: 1.2% faster; the same with a
+// fallback branch to swim() per fish, 4% slower).
+__device__ __forceinline__ float scaled_width(float width) {
+  return __fmul_rn(width, 0x1p-23f);
+}
+__device__ __forceinline__ void swim_scaled(float& x, float& y, uint32_t r0, uint32_t r1,
+                                            float scaled, const Physics<float>& ph) {
+  const float vx = __int2float_rn(static_cast<int>(r0 >> 8) - (1 << 23));
+  const float vy = __int2float_rn(static_cast<int>(r1 >> 8) - (1 << 23));
+  x = fminf(fmaxf(__fadd_rn(x, __fmul_rn(vx, scaled)), -ph.pond_half), ph.pond_half);
+  y = fminf(fmaxf(__fadd_rn(y, __fmul_rn(vy, scaled)), -ph.pond_half), ph.pond_half);
+}
+
 // One fish's swim of one step and its prev - cur into the extremes.
 __device__ __forceinline__ void swim_extremes(float& x, float& y, float& cur, uint32_t r0,
-                                              uint32_t r1, const Physics<float>& ph, float& hi,
-                                              float& lo) {
-  swim(x, y, r0, r1, ph.step, ph);
+                                              uint32_t r1, float scaled,
+                                              const Physics<float>& ph, float& hi, float& lo) {
+  swim_scaled(x, y, r0, r1, scaled, ph);
   const float n = objective(x, y);
   const float i = __fsub_rn(cur, n);
   hi = fmaxf(hi, i);
@@ -124,6 +141,7 @@ __global__ void __launch_bounds__(kBlkThreads, 2)
   uint64_t base;
   if (!blocked_prologue<K>(a.ctl, a.ring_cap, k, j, base)) return;
   const Physics<float> ph = a.ph;
+  const float scaled = scaled_width(ph.step);
   const uint32_t t1 = static_cast<uint32_t>(base + j + 1);  // first step swum here
   float hi[K], lo[K];
 #pragma unroll
@@ -155,10 +173,10 @@ __global__ void __launch_bounds__(kBlkThreads, 2)
       if (static_cast<uint32_t>(t) < k) {
         const Words4 r0 = pair_draw(a.key, a.school, 2 * g, t1 + t);
         const Words4 r1 = pair_draw(a.key, a.school, 2 * g + 1, t1 + t);
-        swim_extremes(x[0], y[0], cur[0], r0.v[0], r0.v[1], ph, hi[t], lo[t]);
-        swim_extremes(x[1], y[1], cur[1], r0.v[2], r0.v[3], ph, hi[t], lo[t]);
-        swim_extremes(x[2], y[2], cur[2], r1.v[0], r1.v[1], ph, hi[t], lo[t]);
-        swim_extremes(x[3], y[3], cur[3], r1.v[2], r1.v[3], ph, hi[t], lo[t]);
+        swim_extremes(x[0], y[0], cur[0], r0.v[0], r0.v[1], scaled, ph, hi[t], lo[t]);
+        swim_extremes(x[1], y[1], cur[1], r0.v[2], r0.v[3], scaled, ph, hi[t], lo[t]);
+        swim_extremes(x[2], y[2], cur[2], r1.v[0], r1.v[1], scaled, ph, hi[t], lo[t]);
+        swim_extremes(x[3], y[3], cur[3], r1.v[2], r1.v[3], scaled, ph, hi[t], lo[t]);
         if (STORE) {
           reinterpret_cast<float4*>(slot_x(slots, ss, t))[g] = make_float4(x[0], x[1], x[2], x[3]);
           reinterpret_cast<float4*>(slot_y(slots, ss, t))[g] = make_float4(y[0], y[1], y[2], y[3]);
@@ -175,7 +193,7 @@ __global__ void __launch_bounds__(kBlkThreads, 2)
       for (int t = 0; t < K; ++t) {
         if (static_cast<uint32_t>(t) < k) {
           const Words2 r = fish_swim_words(a.key, a.school, i, t1 + t);
-          swim_extremes(x, y, cur, r.r0, r.r1, ph, hi[t], lo[t]);
+          swim_extremes(x, y, cur, r.r0, r.r1, scaled, ph, hi[t], lo[t]);
           if (STORE) {
             slot_x(slots, ss, t)[i] = x;
             slot_y(slots, ss, t)[i] = y;
@@ -281,7 +299,7 @@ __device__ __forceinline__ void fish_steps(float& x, float& y, float& w, float& 
         y = slot_y(slots, ss, t)[i];
       } else {
         const Words2 r = fish_swim_words(key, school, i, t1 + t);
-        swim(x, y, r.r0, r.r1, ph.step, ph);
+        swim_scaled(x, y, r.r0, r.r1, scaled_width(ph.step), ph);
       }
       pv = cur;
       if (static_cast<uint32_t>(t) + 1 < k) cur = objective(x, y);
@@ -299,6 +317,7 @@ __global__ void __launch_bounds__(kBlkThreads, 2)
   uint64_t base;
   if (!blocked_prologue<K>(a.ctl, a.ring_cap, k, j, base)) return;
   const Physics<float> ph = kernel_physics<VAR>(a.ph);
+  const float scaled = scaled_width(ph.step);
   const uint32_t t1 = static_cast<uint32_t>(base + j + 1);
   float N[K];
 #pragma unroll
@@ -377,7 +396,7 @@ __global__ void __launch_bounds__(kBlkThreads, 2)
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             const Words4& r = q < 2 ? r0 : r1;
-            swim(x[q], y[q], r.v[2 * (q & 1)], r.v[2 * (q & 1) + 1], ph.step, ph);
+            swim_scaled(x[q], y[q], r.v[2 * (q & 1)], r.v[2 * (q & 1) + 1], scaled, ph);
           }
         }
         // the objective of the last swim's position is not needed
@@ -524,7 +543,10 @@ bool pick_pair(const StreamLaunch& L, const void** maxima, const void** step) {
 }  // namespace
 
 bool stream_blocked_supported(const StreamLaunch& L) {
-  return !L.real_is_double && L.vec == 4 && L.swim_mode == 0;
+  // step 0 or |step| >= 2^-103: its product with 2^-23 is exact
+  const float step = static_cast<float>(L.step);
+  return !L.real_is_double && L.vec == 4 && L.swim_mode == 0 &&
+         (step == 0.f || fabsf(step) >= 0x1p-103f);
 }
 
 int stream_blocked_blocks_per_sm(const StreamLaunch& L) {

@@ -131,6 +131,22 @@ def test_blocked_refused_where_positions_or_state_do_not_allow_it(fields, kernel
 
 
 @pytest.mark.parametrize("kernel", [4, 5])
+def test_blocked_swim_steps_the_scaled_move_allows(kernel):
+    """The blocked passes form the move as v * (step * 2^-23), exact only for
+    a step of 0 or of at least 2^-103: a still school (step 0) runs them and
+    matches the oracle; a step between is refused (kernel 1 runs it)."""
+    cfg = fsb.fsb_config_init(4099, 3, path=fsb.FSB_PATH_STREAM, step=0.0)
+    got, stats, ref, ref_stats = run_pair(cfg, 4, [6], kernel)
+    assert_state_equal(got, ref, "blocked, step 0")
+    assert_stats_match(stats, ref_stats, cfg.precision, "blocked, step 0")
+    tiny = fsb.School.create(fsb.fsb_config_init(4096, 1, path=fsb.FSB_PATH_STREAM, step=1e-35))
+    with pytest.raises(fsb.FsbError) as e:
+        fsb.fsb_set_tuning(tiny.handle, stream_kernel=kernel)
+    assert e.value.status == fsb.FSB_ERR_INVALID_ARG
+    tiny.destroy()
+
+
+@pytest.mark.parametrize("kernel", [4, 5])
 def test_blocked_needs_aligned_state_and_a_valid_block(kernel):
     n = 1000
     ts = [torch.zeros(n + 1, dtype=torch.float32, device="cuda")[1:] for _ in range(4)]
