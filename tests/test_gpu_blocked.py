@@ -227,3 +227,37 @@ def test_full_size_blocked_agrees_bitwise_with_one_pass_per_step(kernel, k):
     assert np.all(np.abs(sa["sum_w"] - sb["sum_w"]) <= 2e-5 * sb["sum_w"])
     for key in ("sum_wx", "sum_wy"):
         assert np.all(np.abs(sa[key] - sb[key]) <= 2e-5 * 100.0 * sb["sum_w"]), key
+
+
+def test_library_choice_is_kernel5_for_large_streaming_schools():
+    """The library's streaming kernel: 5 with 8 steps per pair for a school
+    of at least 2^22 fish that allows it (binary32, default swim) when its
+    slots (64 B per fish) take at most half of the free device memory;
+    kernel 1 otherwise."""
+    def chosen(n, **fields):
+        s = fsb.School.create(fsb.fsb_config_init(n, 1, path=fsb.FSB_PATH_STREAM, **fields))
+        t = fsb.fsb_get_tuning(s.handle)
+        s.destroy()
+        return t["stream_kernel"], t["stream_block_steps"]
+    torch.cuda.empty_cache()
+    assert chosen(1 << 22) == (5, 8)
+    assert chosen((1 << 22) - 1)[0] == 1
+    assert chosen(1 << 22, precision=fsb.FSB_FP64_STATE)[0] == 1
+    assert chosen(1 << 22, swim_mode=1)[0] == 1
+    assert chosen(1 << 22, step=1e-35)[0] == 1
+    # set_tuning with every field 0 is the library's choice again
+    s = fsb.School.create(fsb.fsb_config_init(1 << 22, 1, path=fsb.FSB_PATH_STREAM))
+    fsb.fsb_set_tuning(s.handle, stream_kernel=1)
+    fsb.fsb_set_tuning(s.handle)
+    assert fsb.fsb_get_tuning(s.handle)["stream_kernel"] == 5
+    s.destroy()
+    # not enough free memory for the slots: kernel 1
+    free, _ = torch.cuda.mem_get_info()
+    if free < 8 * (1 << 30):
+        pytest.skip("needs 8 GB of free device memory")
+    hog = torch.empty(free - 6 * (1 << 30), dtype=torch.uint8, device="cuda")
+    try:
+        assert chosen(1 << 26)[0] == 1       # 1 GB of state, 4 GB of slots: > half of what is left
+    finally:
+        del hog
+        torch.cuda.empty_cache()
