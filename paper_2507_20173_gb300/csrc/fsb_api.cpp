@@ -406,8 +406,8 @@ int run_stream(fsb_school* h, uint32_t n) {
 // Pick (fish per thread, block, grid) so a school of n fish sits in
 // registers across at most one block per SM.  Returns false if it does not
 // fit on chip.
-bool resident_config(int sms, int acc, int swim_mode, uint64_t n, fsb::ResidentLaunch* R,
-                     int want_fpt = 0, int want_block = 0) {
+bool resident_config(int sms, int acc, int swim_mode, double step, uint64_t n,
+                     fsb::ResidentLaunch* R, int want_fpt = 0, int want_block = 0) {
   const int fpts[] = {4, 8, 12, 16};
   for (int fpt : fpts) {
     if (want_fpt && fpt != want_fpt) continue;
@@ -450,7 +450,7 @@ bool resident_config(int sms, int acc, int swim_mode, uint64_t n, fsb::ResidentL
                       : small_block ? small_block
                                     : static_cast<int>(pairs32 < static_cast<uint64_t>(maxb) ? pairs32 : maxb);
     if (slice > fsb::resident_max_slice(fpt, block)) continue;
-    if (fsb::resident_blocks_per_sm(fpt, acc, block, swim_mode) < 1) continue;
+    if (fsb::resident_blocks_per_sm(fpt, acc, block, swim_mode, step) < 1) continue;
     R->fpt = fpt;
     R->block = block;
     R->grid = static_cast<int>((n + slice - 1) / slice);
@@ -802,7 +802,8 @@ int fsb_create(const fsb_config* cfg, const fsb_state_dev* buffers, const fsb_st
     // resident path: binary32 state that fits in registers across the SMs
     fsb::ResidentLaunch& R = h->res;
     const bool fits = !dbl && !h->collective &&
-                      resident_config(sms, h->launch.acc, cfg->swim_mode, cfg->n_fish, &R);
+                      resident_config(sms, h->launch.acc, cfg->swim_mode, cfg->step, cfg->n_fish,
+                                      &R);
     if (cfg->path == FSB_PATH_RESIDENT && !fits)
       return fail(FSB_ERR_UNSUPPORTED,
                   "resident path: school of %llu fish does not fit on chip (binary32 only)",
@@ -991,7 +992,8 @@ int fsb_set_tuning(fsb_handle h, const fsb_tuning* t) {
   }
   if (h->path == FSB_PATH_RESIDENT && (t->resident_fpt || t->resident_block)) {
     fsb::ResidentLaunch R = h->res;
-    if (!resident_config(h->sms, R.acc, R.swim_mode, h->cfg.n_fish, &R, t->resident_fpt,
+    if (!resident_config(h->sms, R.acc, R.swim_mode, h->cfg.step, h->cfg.n_fish, &R,
+                         t->resident_fpt,
                          t->resident_block)) {
       h->launch = saved;
       h->tuning = saved_t;

@@ -136,7 +136,11 @@ int batch_max_clusters(int cluster, int acc) {
 
 cudaError_t launch_batch(const BatchLaunch& L, cudaStream_t s, const cudaStream_t* side,
                          cudaEvent_t fork, const cudaEvent_t* join) {
-  const bool var = L.swim_mode != 0 || L.feed_mode != 0;
+  // the variant copy also serves a default swim whose width's scaled form is
+  // not exact (a step below 2^-103 but not 0): the default copy takes that
+  // form without checking
+  const bool var = L.swim_mode != 0 || L.feed_mode != 0 ||
+                   !swim_scale_exact(static_cast<float>(L.step));
   if (L.n_launches < 1 || L.n_launches > kBatchMaxLaunches) return cudaErrorInvalidValue;
   if (L.n_launches > 1 && (!side || !fork || !join)) return cudaErrorInvalidValue;
   const void* fn[kBatchMaxLaunches];

@@ -269,19 +269,19 @@ __device__ __forceinline__ void run_school(const BatchArgs& a, uint32_t k, int r
       uint32_t mb = 0, ek = 0;
       Acc acc;
       if (p == 0 && T > 1)
-        block_pass_from<false, true, false, false, false, kBatchPairsPerIter>(
+        block_pass_from<false, true, false, false, false, kBatchPairsPerIter, !VAR>(
             B, np, nf, c, ph, acc, mb, ek, first, fish_threads);
       else if (p == 0 && T == 1)
-        block_pass_from<false, true, true, false, false, kBatchPairsPerIter>(
+        block_pass_from<false, true, true, false, false, kBatchPairsPerIter, !VAR>(
             B, np, nf, c, ph, acc, mb, ek, first, fish_threads);
       else if (p + 1 < T)
-        block_pass_from<true, true, false, false, false, kBatchPairsPerIter>(
+        block_pass_from<true, true, false, false, false, kBatchPairsPerIter, !VAR>(
             B, np, nf, c, ph, acc, mb, ek, first, fish_threads);
       else if (p + 1 == T)
-        block_pass_from<true, true, true, false, false, kBatchPairsPerIter>(
+        block_pass_from<true, true, true, false, false, kBatchPairsPerIter, !VAR>(
             B, np, nf, c, ph, acc, mb, ek, first, fish_threads);
       else if (p == T)
-        block_pass_from<true, false, false, true, false, kBatchPairsPerIter>(
+        block_pass_from<true, false, false, true, false, kBatchPairsPerIter, !VAR>(
             B, np, nf, c, ph, acc, mb, ek, first, fish_threads);
       if (do_swim) {
         mb = warp_max(mb);

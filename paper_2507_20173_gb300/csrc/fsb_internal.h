@@ -181,7 +181,7 @@ struct ResidentLaunch {
 cudaError_t launch_resident(const ResidentLaunch& L, cudaStream_t s);
 int resident_max_block(int fpt);
 uint64_t resident_max_slice(int fpt, int block);
-int resident_blocks_per_sm(int fpt, int acc, int block, int swim_mode);
+int resident_blocks_per_sm(int fpt, int acc, int block, int swim_mode, double step);
 size_t resident_smem_bytes(uint64_t slice);
 
 // Work queues of a batch: queue t (t = 0 .. 6) holds the schools run on

@@ -158,6 +158,27 @@ __device__ __forceinline__ void swim_pair(float2& xv, float2& yv, const Words4& 
   yv = clamp_x2(add_x2(yv, dy), -P, P);
 }
 
+// The default swim of a pair with the width folded into the exact scale
+// `scaled` (nonzero, or the width 0): swim_pair's first form without its
+// run-time choice, which measured several per cent in the per-pair loop.
+__device__ __forceinline__ void swim_pair_scaled(float2& xv, float2& yv, const Words4& r,
+                                                 float scaled, float P) {
+  const float vx0 = __int2float_rn(static_cast<int>(r.v[0] >> 8) - (1 << 23));
+  const float vy0 = __int2float_rn(static_cast<int>(r.v[1] >> 8) - (1 << 23));
+  const float vx1 = __int2float_rn(static_cast<int>(r.v[2] >> 8) - (1 << 23));
+  const float vy1 = __int2float_rn(static_cast<int>(r.v[3] >> 8) - (1 << 23));
+  const float2 dx = make_float2(__fmul_rn(vx0, scaled), __fmul_rn(vx1, scaled));
+  const float2 dy = make_float2(__fmul_rn(vy0, scaled), __fmul_rn(vy1, scaled));
+  xv = clamp_x2(add_x2(xv, dx), -P, P);
+  yv = clamp_x2(add_x2(yv, dy), -P, P);
+}
+
+// width * 2^-23 is exact (and nonzero unless width is 0) for width 0 or
+// |width| >= 2^-103: then the scaled form of the default swim applies.
+__host__ __device__ __forceinline__ bool swim_scale_exact(float width) {
+  return width == 0.f || fabsf(width) >= 0x1p-103f;
+}
+
 // Objective (Sec. 2.1.1) of both fish of a pair: sqrt((x * x) + (y * y)).
 __device__ __forceinline__ float2 objective_pair(float2 xv, float2 yv) {
   const float2 xx = make_float2(__fmul_rn(xv.x, xv.x), __fmul_rn(xv.y, xv.y));
@@ -265,17 +286,20 @@ struct PassCtx {
 
 // One fish pair of a pass: the eat of step p and its barycentre terms (EAT),
 // then the swim of step p + 1 with its objective and maxima (SWIM).
+// SCALED: the default swim with c.scaled exact (the kernel's host checks it),
+// no run-time choice of the swim's form.
 // LAST_SWIM: D keeps the swim's starting objectives; LAST_EAT: the feeding
 // input comes from F and D.  `two`: the pair's second fish is in the school
 // (a half pair's second fish is computed but neither summed nor maximised).
 // AHEAD: the eat reads its own positions (Xe, Ye), else the swim's.
-template <bool EAT, bool SWIM, bool LAST_SWIM, bool LAST_EAT, bool AHEAD, typename Acc>
+template <bool EAT, bool SWIM, bool LAST_SWIM, bool LAST_EAT, bool AHEAD, bool SCALED = false,
+          typename Acc>
 __device__ __forceinline__ void pair_pass(const PairState& B, uint32_t e, bool two,
                                           const PassCtx& c, const Physics<float>& ph, Acc& acc,
                                           float& ihi, float& ilo) {
   const float4 ps = B.XYs[e];
   float2 xv = make_float2(ps.x, ps.y), yv = make_float2(ps.z, ps.w), fv = B.F[e];
-  float2 wv = (EAT || ph.swim_mode) ? B.W[e] : make_float2(0.f, 0.f);
+  float2 wv = (EAT || (!SCALED && ph.swim_mode)) ? B.W[e] : make_float2(0.f, 0.f);
   if (EAT) {
     const float2 dv = B.De[e];
     const float4 pe = AHEAD ? B.XYe[e] : ps;
@@ -294,9 +318,14 @@ __device__ __forceinline__ void pair_pass(const PairState& B, uint32_t e, bool t
   if (SWIM) {
     const Words4 r = pair_draw(c.key, c.school, c.pair0 + e, c.t);
     const float2 o = fv;
-    const float2 width = ph.swim_mode ? make_float2(swim_width(ph, wv.x), swim_width(ph, wv.y))
-                                      : make_float2(ph.step, ph.step);
-    swim_pair(xv, yv, r, ph.swim_mode ? 0.f : c.scaled, width, ph.pond_half);
+    if (SCALED) {
+      swim_pair_scaled(xv, yv, r, c.scaled, ph.pond_half);
+    } else {
+      const float2 width = ph.swim_mode
+                               ? make_float2(swim_width(ph, wv.x), swim_width(ph, wv.y))
+                               : make_float2(ph.step, ph.step);
+      swim_pair(xv, yv, r, ph.swim_mode ? 0.f : c.scaled, width, ph.pond_half);
+    }
     fv = objective_pair(xv, yv);
     const float2 i = sub_x2(o, fv);  // prev - cur
     const float2 d = sub_x2(fv, o);  // delta
@@ -320,7 +349,7 @@ __device__ __forceinline__ void pair_pass(const PairState& B, uint32_t e, bool t
 // and ek (order key of max(prev - cur)): prev - cur is never -0 (x - x is
 // +0), so the float extremes order like the keys.
 template <bool EAT, bool SWIM, bool LAST_SWIM, bool LAST_EAT, bool AHEAD = false, int ITER = 2,
-          typename Acc>
+          bool SCALED = false, typename Acc>
 __device__ __forceinline__ void block_pass_from(const PairState& B, uint32_t np, uint32_t nf,
                                                 const PassCtx& c, const Physics<float>& ph,
                                                 Acc& acc, uint32_t& mb, uint32_t& ek,
@@ -333,12 +362,13 @@ __device__ __forceinline__ void block_pass_from(const PairState& B, uint32_t np,
 #pragma unroll
     for (uint32_t k = 0; k < kIter; ++k) {
       const uint32_t ek2 = e + k * step;  // only the group's last pair can be the half pair
-      pair_pass<EAT, SWIM, LAST_SWIM, LAST_EAT, AHEAD>(B, ek2, k + 1 < kIter || 2 * ek2 + 1 < nf,
-                                                       c, ph, acc, ihi, ilo);
+      pair_pass<EAT, SWIM, LAST_SWIM, LAST_EAT, AHEAD, SCALED>(
+          B, ek2, k + 1 < kIter || 2 * ek2 + 1 < nf, c, ph, acc, ihi, ilo);
     }
   }
   for (; e < np; e += step)
-    pair_pass<EAT, SWIM, LAST_SWIM, LAST_EAT, AHEAD>(B, e, 2 * e + 1 < nf, c, ph, acc, ihi, ilo);
+    pair_pass<EAT, SWIM, LAST_SWIM, LAST_EAT, AHEAD, SCALED>(B, e, 2 * e + 1 < nf, c, ph, acc,
+                                                             ihi, ilo);
   if (SWIM && ihi >= ilo) {  // at least one fish swum
     mb = max(mb, abs_bits(fmaxf(ihi, -ilo)));
     ek = max(ek, order_key(ihi));
@@ -347,12 +377,12 @@ __device__ __forceinline__ void block_pass_from(const PairState& B, uint32_t np,
 
 // The same pass shared by threads 0 .. step - 1 of the block.
 template <bool EAT, bool SWIM, bool LAST_SWIM, bool LAST_EAT, bool AHEAD = false, int ITER = 2,
-          typename Acc>
+          bool SCALED = false, typename Acc>
 __device__ __forceinline__ void block_pass(const PairState& B, uint32_t np, uint32_t nf,
                                            const PassCtx& c, const Physics<float>& ph, Acc& acc,
                                            uint32_t& mb, uint32_t& ek, uint32_t step) {
-  block_pass_from<EAT, SWIM, LAST_SWIM, LAST_EAT, AHEAD, ITER>(B, np, nf, c, ph, acc, mb, ek,
-                                                               threadIdx.x, step);
+  block_pass_from<EAT, SWIM, LAST_SWIM, LAST_EAT, AHEAD, ITER, SCALED>(B, np, nf, c, ph, acc, mb,
+                                                                       ek, threadIdx.x, step);
 }
 
 }  // namespace fsb

@@ -270,14 +270,18 @@ __global__ void __launch_bounds__(kResThreads + 32, 1) resident_kernel(ResidentA
       const PairState B = state(u - 1, u);
       if (!eat_too) {
         if (u == T)
-          block_pass<false, true, true, false>(B, np, nf, c, ph, acc, mb, ek, fish_threads);
+          block_pass<false, true, true, false, false, 2, !WSWIM>(B, np, nf, c, ph, acc, mb, ek,
+                                                               fish_threads);
         else
-          block_pass<false, true, false, false>(B, np, nf, c, ph, acc, mb, ek, fish_threads);
+          block_pass<false, true, false, false, false, 2, !WSWIM>(B, np, nf, c, ph, acc, mb, ek,
+                                                                fish_threads);
       } else {
         if (u == T)
-          block_pass<true, true, true, false>(B, np, nf, c, ph, acc, mb, ek, fish_threads);
+          block_pass<true, true, true, false, false, 2, !WSWIM>(B, np, nf, c, ph, acc, mb, ek,
+                                                              fish_threads);
         else
-          block_pass<true, true, false, false>(B, np, nf, c, ph, acc, mb, ek, fish_threads);
+          block_pass<true, true, false, false, false, 2, !WSWIM>(B, np, nf, c, ph, acc, mb, ek,
+                                                               fish_threads);
       }
       mb = warp_max(mb);
       ek = warp_max(ek);
@@ -318,9 +322,11 @@ __global__ void __launch_bounds__(kResThreads + 32, 1) resident_kernel(ResidentA
         c.t = static_cast<uint32_t>(a.base_step + u + 2);
         const PairState B = ahead_state(u);
         if (u + 2 == T)
-          block_pass<true, true, true, false, true>(B, np, nf, c, ph, acc, mb, ek, fish_threads);
+          block_pass<true, true, true, false, true, 2, !WSWIM>(B, np, nf, c, ph, acc, mb, ek,
+                                                             fish_threads);
         else
-          block_pass<true, true, false, false, true>(B, np, nf, c, ph, acc, mb, ek, fish_threads);
+          block_pass<true, true, false, false, true, 2, !WSWIM>(B, np, nf, c, ph, acc, mb, ek,
+                                                              fish_threads);
         mb = warp_max(mb);
         ek = warp_max(ek);
         if (lane == 0) {
@@ -457,8 +463,15 @@ uint64_t resident_max_slice(int fpt, int block) {
 
 size_t resident_smem_bytes(uint64_t slice) { return kResSmemPerFish * slice; }
 
-int resident_blocks_per_sm(int fpt, int acc, int block, int swim_mode) {
-  const void* fn = pick(acc, swim_mode != 0);
+// The kernel copy for a launch: the weight-scaled swim's copy also serves
+// the default swim when its width's scaled form is not exact (a step below
+// 2^-103 but not 0), for the default copy takes that form without checking.
+static bool wswim_copy(int swim_mode, double step) {
+  return swim_mode != 0 || !swim_scale_exact(static_cast<float>(step));
+}
+
+int resident_blocks_per_sm(int fpt, int acc, int block, int swim_mode, double step) {
+  const void* fn = pick(acc, wswim_copy(swim_mode, step));
   if (!fn || block < 32 || block > resident_max_block(fpt)) return 0;
   // the attribute is per kernel, shared by every handle: always the largest
   // slice, so no handle lowers it under another
@@ -477,7 +490,7 @@ int resident_blocks_per_sm(int fpt, int acc, int block, int swim_mode) {
 }
 
 cudaError_t launch_resident(const ResidentLaunch& L, cudaStream_t s) {
-  const void* fn = pick(L.acc, L.swim_mode != 0);
+  const void* fn = pick(L.acc, wswim_copy(L.swim_mode, L.step));
   if (!fn || L.grid < 1 || L.block < 32 || L.block % 32 || L.block > resident_max_block(L.fpt) ||
       L.slice < 2 || L.slice % 2 || L.slice > resident_max_slice(L.fpt, L.block) ||
       static_cast<uint64_t>(L.grid) * L.slice < L.n)

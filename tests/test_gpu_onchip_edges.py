@@ -1,8 +1,9 @@
 """Edge cases of the on-chip (resident and batched) per-pair passes against
 the CPU oracle: swim steps on either side of the threshold below which the
 paired swim keeps the two-rounding form of (2u - 1) * s (s * 2^-23 must be
-exact to fold it), tiny ponds whose objectives underflow, subnormal
-positions, and both model variants, bit for bit."""
+exact to fold it; such a step runs the kernels' variant copies, which
+choose the form per pair), tiny ponds whose objectives underflow,
+subnormal positions, and both model variants, bit for bit."""
 import numpy as np
 import pytest
 
