@@ -306,10 +306,15 @@ __device__ __forceinline__ void pair_pass(const PairState& B, uint32_t e, bool t
     const float2 xe = make_float2(pe.x, pe.y), ye = make_float2(pe.z, pe.w);
     float2 g = dv;
     if (LAST_EAT) g = ph.feed_mode ? sub_x2(dv, fv) : sub_x2(fv, dv);
-    if (c.N > 0.f) {
-      // w <- clamp(w + g / N, w_min, w_max), one rounding per operation
-      const float2 q = make_float2(__fdiv_rn(g.x, c.N), __fdiv_rn(g.y, c.N));
-      wv = clamp_x2(add_x2(wv, q), ph.w_min, ph.w_max);
+    {
+      // w <- clamp(w + g / N, w_min, w_max), one rounding per operation, for
+      // N > 0; w unchanged otherwise (selected, not branched on: a branch
+      // per pair keeps the pairs of an iteration from interleaving)
+      const bool feed = c.N > 0.f;
+      const float Nd = feed ? c.N : 1.f;
+      const float2 q = make_float2(__fdiv_rn(g.x, Nd), __fdiv_rn(g.y, Nd));
+      const float2 wn = clamp_x2(add_x2(wv, q), ph.w_min, ph.w_max);
+      wv = feed ? wn : wv;
     }
     if (!two) wv.y = 0.f;  // a half pair's absent fish carries no weight
     acc_pair(acc, wv, xe, ye);

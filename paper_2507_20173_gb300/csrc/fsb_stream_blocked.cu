@@ -376,11 +376,16 @@ __global__ void __launch_bounds__(kBlkThreads, 2)
 #pragma unroll
     for (int t = 0; t < K; ++t) {
       if (static_cast<uint32_t>(t) < k) {
-        if (N[t] > 0.f) {
+        {
+          // eat for N > 0, else w unchanged: selected, not branched on
+          const bool feed = N[t] > 0.f;
+          const float Nd = feed ? N[t] : 1.f;
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
-            w[q] = eat(w[q], ph.feed_mode ? __fsub_rn(pv[q], cur[q]) : __fsub_rn(cur[q], pv[q]),
-                       N[t], ph);
+          for (int q = 0; q < 4; ++q) {
+            const float wn = eat(w[q], ph.feed_mode ? __fsub_rn(pv[q], cur[q])
+                                                    : __fsub_rn(cur[q], pv[q]), Nd, ph);
+            w[q] = feed ? wn : w[q];
+          }
         }
         acc[t].add4(w, x, y);
         if (STORE) {
