@@ -66,14 +66,16 @@ __device__ __forceinline__ void cp_async_wait() {
 
 // Pass index j of the pair and its step count k; false (status latched) if
 // they do not fit the call: the maxima pass writes records j .. j + k - 1,
-// the step pass reads records j - 1 .. j + k - 2.
-template <int K>
+// the step pass reads records j - 1 .. j + k - 2.  A copy for whole pairs
+// (FULL) takes k = K only.
+template <int K, bool FULL>
 __device__ __forceinline__ bool blocked_prologue(Ctl* ctl, uint32_t ring_cap, uint32_t k,
                                                  uint32_t& j, uint64_t& base) {
   if (__syncthreads_or(ld_relaxed_gpu(&ctl->status) != 0)) return false;
   j = ctl->pass;
   base = ctl->base_step;
-  if (j == 0 || k == 0 || k > static_cast<uint32_t>(K) || j + k > ring_cap) {
+  if (j == 0 || k == 0 || k > static_cast<uint32_t>(K) || (FULL && k != K) ||
+      j + k > ring_cap) {
     if (threadIdx.x == 0) atomicCAS(&ctl->status, 0, static_cast<int>(FSB_ERR_STATE));
     return false;
   }
@@ -133,13 +135,13 @@ __device__ __forceinline__ float* slot_y(float* slots, uint64_t ss, int t) {
   return slots + static_cast<uint64_t>(2 * t + 1) * ss;
 }
 
-template <int K, bool STORE>
+template <int K, bool STORE, bool FULL>
 __global__ void __launch_bounds__(kBlkThreads, 2)
     blocked_maxima_kernel(StreamArgs<float> a, uint32_t k, BlockPartial* bp, float* slots,
                           uint64_t ss) {
   uint32_t j;
   uint64_t base;
-  if (!blocked_prologue<K>(a.ctl, a.ring_cap, k, j, base)) return;
+  if (!blocked_prologue<K, FULL>(a.ctl, a.ring_cap, k, j, base)) return;
   const Physics<float> ph = a.ph;
   const float scaled = scaled_width(ph.step);
   const uint32_t t1 = static_cast<uint32_t>(base + j + 1);  // first step swum here
@@ -170,7 +172,7 @@ __global__ void __launch_bounds__(kBlkThreads, 2)
     for (int q = 0; q < 4; ++q) cur[q] = objective(x[q], y[q]);
 #pragma unroll
     for (int t = 0; t < K; ++t) {
-      if (static_cast<uint32_t>(t) < k) {
+      if (FULL || static_cast<uint32_t>(t) < k) {
         const Words4 r0 = pair_draw(a.key, a.school, 2 * g, t1 + t);
         const Words4 r1 = pair_draw(a.key, a.school, 2 * g + 1, t1 + t);
         swim_extremes(x[0], y[0], cur[0], r0.v[0], r0.v[1], scaled, ph, hi[t], lo[t]);
@@ -191,7 +193,7 @@ __global__ void __launch_bounds__(kBlkThreads, 2)
       float cur = objective(x, y);
 #pragma unroll
       for (int t = 0; t < K; ++t) {
-        if (static_cast<uint32_t>(t) < k) {
+        if (FULL || static_cast<uint32_t>(t) < k) {
           const Words2 r = fish_swim_words(a.key, a.school, i, t1 + t);
           swim_extremes(x, y, cur, r.r0, r.r1, scaled, ph, hi[t], lo[t]);
           if (STORE) {
@@ -226,7 +228,7 @@ __global__ void __launch_bounds__(kBlkThreads, 2)
   if (warp == 0) {
 #pragma unroll
     for (int t = 0; t < K; ++t) {
-      if (static_cast<uint32_t>(t) < k) {
+      if (FULL || static_cast<uint32_t>(t) < k) {
         const uint32_t m = warp_max(lane < kBlkWarps ? s_m[t][lane] : 0u);
         const uint32_t e = warp_max(lane < kBlkWarps ? s_e[t][lane] : 0u);
         if (lane == 0) {
@@ -241,7 +243,7 @@ __global__ void __launch_bounds__(kBlkThreads, 2)
   if (!arrive_last(a.ctl)) return;
 #pragma unroll
   for (int t = 0; t < K; ++t) {
-    if (static_cast<uint32_t>(t) >= k) continue;
+    if (!FULL && static_cast<uint32_t>(t) >= k) continue;
     uint32_t m = 0u, e = 0u;
     for (uint32_t b = threadIdx.x; b < gridDim.x; b += kBlkThreads) {
       const BlockPartial* p = bp + static_cast<uint64_t>(t) * gridDim.x + b;
@@ -261,7 +263,7 @@ __global__ void __launch_bounds__(kBlkThreads, 2)
   if (warp == 0) {
 #pragma unroll
     for (int t = 0; t < K; ++t) {
-      if (static_cast<uint32_t>(t) >= k) continue;
+      if (!FULL && static_cast<uint32_t>(t) >= k) continue;
       const uint32_t m = warp_max(lane < kBlkWarps ? s_m[t][lane] : 0u);
       const uint32_t e = warp_max(lane < kBlkWarps ? s_e[t][lane] : 0u);
       if (lane == 0) {
@@ -315,7 +317,7 @@ __global__ void __launch_bounds__(kBlkThreads, 2)
   using Sum = typename Acc::Sum;
   uint32_t j;
   uint64_t base;
-  if (!blocked_prologue<K>(a.ctl, a.ring_cap, k, j, base)) return;
+  if (!blocked_prologue<K, false>(a.ctl, a.ring_cap, k, j, base)) return;
   const Physics<float> ph = kernel_physics<VAR>(a.ph);
   const float scaled = scaled_width(ph.step);
   const uint32_t t1 = static_cast<uint32_t>(base + j + 1);
@@ -522,24 +524,31 @@ const void* pick_step(int acc, bool var) {
   }
 }
 
-template <int K, bool STORE>
+template <int K, bool STORE, bool FULL>
 void pick_k(int acc, bool var, const void** maxima, const void** step) {
-  *maxima = reinterpret_cast<const void*>(&blocked_maxima_kernel<K, STORE>);
+  *maxima = reinterpret_cast<const void*>(&blocked_maxima_kernel<K, STORE, FULL>);
   *step = pick_step<K, STORE>(acc, var);
 }
 
-// The kernels of a pair of k_max steps: the maxima pass and the step pass
-// (kernel 5 when the slots are set).
-bool pick_pair(const StreamLaunch& L, const void** maxima, const void** step) {
+// The kernels of a pair of up to k_max steps: the maxima pass and the step
+// pass (kernel 5 when the slots are set).  Kernel 5's maxima pass has a copy
+// for a whole pair (full: k = k_max) without the per-step test of k, which
+// the compiler does not take out of the unrolled step loop.  (The step pass
+// keeps one copy: knowing k = k_max there, the compiler holds more in
+// registers than it has, and spills.)
+bool pick_pair(const StreamLaunch& L, bool full, const void** maxima, const void** step) {
   const bool var = L.feed_mode != 0;
   const bool store = L.slots != nullptr;
   switch (L.blocked_k) {
-    case 2: store ? pick_k<2, true>(L.acc, var, maxima, step)
-                  : pick_k<2, false>(L.acc, var, maxima, step); break;
-    case 4: store ? pick_k<4, true>(L.acc, var, maxima, step)
-                  : pick_k<4, false>(L.acc, var, maxima, step); break;
-    case 8: store ? pick_k<8, true>(L.acc, var, maxima, step)
-                  : pick_k<8, false>(L.acc, var, maxima, step); break;
+    case 2: store ? (full ? pick_k<2, true, true>(L.acc, var, maxima, step)
+                          : pick_k<2, true, false>(L.acc, var, maxima, step))
+                  : pick_k<2, false, false>(L.acc, var, maxima, step); break;
+    case 4: store ? (full ? pick_k<4, true, true>(L.acc, var, maxima, step)
+                          : pick_k<4, true, false>(L.acc, var, maxima, step))
+                  : pick_k<4, false, false>(L.acc, var, maxima, step); break;
+    case 8: store ? (full ? pick_k<8, true, true>(L.acc, var, maxima, step)
+                          : pick_k<8, true, false>(L.acc, var, maxima, step))
+                  : pick_k<8, false, false>(L.acc, var, maxima, step); break;
     default: return false;
   }
   return *step != nullptr;
@@ -555,21 +564,26 @@ bool stream_blocked_supported(const StreamLaunch& L) {
 }
 
 int stream_blocked_blocks_per_sm(const StreamLaunch& L) {
-  const void* fa = nullptr;
-  const void* fb = nullptr;
-  if (!pick_pair(L, &fa, &fb)) return 0;
-  int na = 0, nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&na, fa, kBlkThreads, 0) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fb, kBlkThreads, 0) != cudaSuccess)
-    return 0;
-  return na < nb ? na : nb;
+  int best = 0;
+  for (bool full : {false, true}) {  // both copies of a pair run on the one grid
+    const void* fa = nullptr;
+    const void* fb = nullptr;
+    if (!pick_pair(L, full, &fa, &fb)) return 0;
+    int na = 0, nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&na, fa, kBlkThreads, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fb, kBlkThreads, 0) != cudaSuccess)
+      return 0;
+    const int m = na < nb ? na : nb;
+    best = full ? (m < best ? m : best) : m;
+  }
+  return best;
 }
 
 cudaError_t launch_blocked_pair(const StreamLaunch& L, uint32_t k, cudaStream_t s) {
   const void* fa = nullptr;
   const void* fb = nullptr;
-  if (!pick_pair(L, &fa, &fb) || L.bgrid <= 0 || !L.bpartials || k == 0 ||
-      k > static_cast<uint32_t>(L.blocked_k))
+  if (!pick_pair(L, k == static_cast<uint32_t>(L.blocked_k), &fa, &fb) || L.bgrid <= 0 ||
+      !L.bpartials || k == 0 || k > static_cast<uint32_t>(L.blocked_k))
     return cudaErrorInvalidValue;
   if (L.slots && L.slot_stride % 4 != 0) return cudaErrorInvalidValue;
   StreamArgs<float> a = make_stream_args<float>(L);
