@@ -40,7 +40,7 @@ typedef enum {
     FSB_ERR_INVALID_ARG = -1,  /* bad pointer, size, enum or config value   */
     FSB_ERR_CUDA = -2,         /* a CUDA runtime call failed                 */
     FSB_ERR_OOM = -3,          /* device or pinned allocation failed         */
-    FSB_ERR_UNSUPPORTED = -4,  /* valid request this build cannot serve      */
+    FSB_ERR_UNSUPPORTED = -4,  /* valid request this library cannot serve    */
     FSB_ERR_TIMEOUT = -5,      /* a bounded device-side wait gave up         */
     FSB_ERR_STATE = -6         /* device status word latched an error        */
 } fsb_status;

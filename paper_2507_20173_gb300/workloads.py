@@ -8,7 +8,7 @@ sizes, seeds and step counts, and the ragged school sizes of the batched
 ensemble (numpy's seeded generator, not the method's Philox).
 
 The paper states neither the fish population nor the iteration count; the
-sizes below are the ones this build measures (C1..C5).
+sizes below are the ones the benchmark measures (C1..C5).
 """
 from __future__ import annotations
 
