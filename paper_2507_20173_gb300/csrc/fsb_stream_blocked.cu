@@ -51,8 +51,11 @@ constexpr int kBlkWarps = kBlkThreads / 32;
 constexpr int kLead = 2;
 constexpr int kRing = kLead + 1;
 
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(src)
+// 16 bytes into shared memory, of which the first src_bytes (0 or 16) come
+// from src and the rest are zero.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(smem_dst)),
+               "l"(src), "r"(src_bytes)
                : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() {
@@ -339,15 +342,17 @@ __global__ void __launch_bounds__(kBlkThreads, 2)
   __shared__ __align__(16) float4 ring[STORE ? kRing : 1][2][kBlkThreads];
   uint64_t pg = tid;
   uint32_t pt = 0, pw = 0, rc = 0;
+  // (selects, not branches: past the last group a copy of 0 source bytes
+  // from the first group's address zero-fills an entry nobody reads)
   auto issue = [&]() {
-    if (pg < ngroups) {
-      cp_async16(&ring[pw][0][threadIdx.x], slot_x(slots, ss, static_cast<int>(pt)) + 4 * pg);
-      cp_async16(&ring[pw][1][threadIdx.x], slot_y(slots, ss, static_cast<int>(pt)) + 4 * pg);
-      if (++pt == k) {
-        pt = 0;
-        pg += stride;
-      }
-    }
+    const bool live = pg < ngroups;
+    const uint64_t gg = live ? pg : 0u;
+    const uint32_t bytes = live ? 16u : 0u;
+    cp_async16(&ring[pw][0][threadIdx.x], slot_x(slots, ss, static_cast<int>(pt)) + 4 * gg, bytes);
+    cp_async16(&ring[pw][1][threadIdx.x], slot_y(slots, ss, static_cast<int>(pt)) + 4 * gg, bytes);
+    const bool wrap = live && pt + 1 == k;
+    pg = wrap ? pg + stride : pg;
+    pt = wrap ? 0u : (live ? pt + 1 : pt);
     cp_async_commit();
     pw = pw + 1 == kRing ? 0u : pw + 1;
   };
