@@ -1,5 +1,6 @@
-// fsb_stream_blocked.cu -- the streaming step blocked over k steps by
-// recompute (stream kernel 4).
+// fsb_stream_blocked.cu -- the streaming step blocked over k steps (stream
+// kernels 4 and 5; kernel 5 with k = 8 is the library's streaming kernel for
+// a large school).
 //
 // A school's positions do not depend on its weights (the default swim), and
 // the draws are counter-based, so the steps j + 1 .. j + k of a school can be
@@ -11,7 +12,8 @@
 //   maxima pass  (state "swum j, not eaten"): reads x, y; swims steps
 //                j + 1 .. j + k in registers and reduces, per step, max |delta|
 //                and the paper's eat() value max(prev - cur) (Sec. 2.3.2) into
-//                the statistics records of those steps.  Writes no fish.
+//                the statistics records of those steps.  Writes no fish
+//                (kernel 4).
 //   step pass    reads x, y, w, prevObjective; for each of the k steps eats
 //                (normaliser from the statistics record: M_j from the pass
 //                before, the others from the maxima pass), adds the step's
@@ -21,7 +23,10 @@
 // Stream kernel 5 trades memory for instructions: its maxima pass also
 // stores the positions of steps j + 1 .. j + k (8 B per fish and step, in
 // slots beside the state), and its step pass loads them instead of drawing
-// and swimming again, so each fish-step's draw and swim run once.
+// and swimming again, so each fish-step's draw and swim run once (21 B of
+// traffic per fish-step at k = 8, against 32 for one pass per step).  Its
+// maxima pass has a second copy for whole pairs (k = K), without the
+// per-step test of k.
 //
 // Per fish the arithmetic is fsb_stream.cu's, operation for operation, so
 // the state is bit-identical to the one-pass-per-step kernels'; only the
